@@ -1,0 +1,409 @@
+"""Benchmark of the batched Rusanov patch update on GB300.
+
+Workload (default): 3D compressible Euler (s = 5, gamma = 1.4), FP64,
+262,144 patches of 5x5x5 interior cells + one halo cell, arranged as a
+64^3 periodic patch mesh (a 320^3-cell domain), every cell an i.i.d. random
+state (rho ~ U[0.5,1.5], u,v,w ~ U[-0.5,0.5], p ~ U[0.5,1.5]).
+
+One step = the whole hot path through the C ABI:
+  fv_halo_fill -> fv_max_eigenvalue_reduce (CFL 0.4, dt left on the device)
+  -> fv_patch_update_batch (dt read on the device), buffers ping-pong.
+
+Metric: patch cell-updates per second (interior cells advanced per second).
+The buffers (2 x 3.6 GB) are far larger than L2 (129 MB), so no flush is
+needed between steps.
+
+Arms:
+  default            the CUDA library (value: device-resident timing; e2e: the
+                     same step with the state copied host->device before and
+                     device->host after it, from/to pinned host memory)
+  --impl reference   the FP64 CPU oracle on the host cores (a bounded sample
+                     of the same workload per step)
+
+Multi-GPU (torchrun): every rank advances its own replica of the workload
+(independent patch meshes, no data-path collective; weak scaling); timing
+is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "patch cell-updates/s"
+UNIT = "cell-updates/s"
+
+WORKLOADS = {
+    # name: (d, p, n_patches, grid, precision)
+    "euler3d_fp64_262144x5": (3, 5, 262144, (64, 64, 64), "f64"),
+    "euler3d_fp32_262144x5": (3, 5, 262144, (64, 64, 64), "f32"),
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP64 pipe: 2 FP64 lanes per SM per clock (one DFMA/DADD/DMUL per lane per
+# clock) on GB300, 152 SMs.  The peak uses the maximum SM clock.
+FP64_LANES_PER_SM = 2
+NUM_SMS = 152
+
+
+def fp64_ops_per_patch(d: int, p: int) -> int:
+    """FP64 pipe operations one patch update needs (the algorithm's count,
+    with the reciprocal and square root counted as the FP64 operations of
+    their Newton refinements: 3 and 5).  Per cell with primitives: 3 (1/rho)
+    + d (u) + d (j.u) + 2 (p) + 1 (E+p) + 2 (c^2) + 5 (sqrt) = 13 + 2d;
+    per (cell, direction) flux: |u|+c (1) + f (d + 1); per face: 3 s; per
+    interior cell update: s (2d - 1) + s."""
+    s = d + 2
+    interior = p ** d
+    halo = 2 * d * p ** (d - 1)
+    faces = d * (p + 1) * p ** (d - 1)
+    prim = 13 + 2 * d
+    flux = 1 + (d + 1)
+    return (interior * (prim + d * flux) + halo * (prim + flux) + faces * 3 * s
+            + interior * (s * (2 * d - 1) + s))
+
+
+def alg_bytes_per_patch(d: int, p: int, itemsize: int) -> int:
+    """Algorithmic HBM bytes of one patch update: read the interior and the
+    face-halo cells, write the interior."""
+    s = d + 2
+    return ((p ** d + 2 * d * p ** (d - 1)) * s + p ** d * s) * itemsize
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(name: str, seed: int = 0):
+    from paper_2302_09005_gb300 import inputs
+    d, p, n, grid, prec = WORKLOADS[name]
+    dtype = np.float64 if prec == "f64" else np.float32
+    q, off, sz = inputs.random_batch(n, p, d, seed=seed, dtype=dtype)
+    nbr = inputs.grid_neighbours(grid)
+    return q, off, sz, nbr
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2302_09005_gb300 import _build, fv
+
+    _build.build()
+    torch.cuda.set_device(local)
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    d, p, n, grid, prec = WORKLOADS[args.workload]
+    s = d + 2
+    fvprec = fv.FV_FP64 if prec == "f64" else fv.FV_FP32
+    tdtype = torch.float64 if prec == "f64" else torch.float32
+    itemsize = 8 if prec == "f64" else 4
+    q, off, sz, nbr = make_workload(args.workload, seed=rank)
+    h_q = torch.from_numpy(q).pin_memory()
+    h_off = torch.from_numpy(off).pin_memory()
+    h_sz = torch.from_numpy(sz).pin_memory()
+    h_nbr = torch.from_numpy(nbr).pin_memory()
+    h_out = torch.empty_like(h_q).pin_memory()
+    del q
+    stream = torch.cuda.Stream()
+    qa = h_q.to("cuda", non_blocking=False)
+    qb = qa.clone()
+    toff, tsz, tnbr = h_off.cuda(), h_sz.cuda(), h_nbr.cuda()
+    b = fv.Batch(d, precision=fvprec, max_patch_size=p, stream=stream)
+    dx, cfl = 1.0 / (grid[0] * p), 0.4
+    torch.cuda.synchronize()
+
+    def step(src, dst):
+        b.halo_fill(src, toff, tsz, tnbr)
+        b.max_eigenvalue(src, toff, tsz, cfl, dx)
+        b.update(src, dst, toff, tsz, dx, -1.0)
+
+    # warm-up
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(qa, qb)
+            qa, qb = qb, qa
+    stream.synchronize()
+    if b.status() != fv.FV_OK:
+        raise RuntimeError("warm-up: " + fv.fv_last_error(b.h))
+
+    # ---- device-resident timed region ----------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for k in range(args.steps):
+            b.halo_fill(qa, toff, tsz, tnbr)
+            b.max_eigenvalue(qa, toff, tsz, cfl, dx)
+            ev[k][0].record(stream)
+            b.update(qa, qb, toff, tsz, dx, -1.0)
+            ev[k][1].record(stream)
+            qa, qb = qb, qa
+        t1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    upd_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    if b.status() != fv.FV_OK:
+        raise RuntimeError("timed region: " + fv.fv_last_error(b.h))
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    cells_per_step = n * p ** d
+    value = ws * cells_per_step * args.steps / (ms / 1e3)
+    upd_avg_ms = sum(upd_ms) / len(upd_ms)
+
+    # ---- end-to-end: host state in, host state out ----------------------
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        te0.record(stream)
+        for _ in range(e2e_steps):
+            qa.copy_(h_q, non_blocking=True)
+            toff.copy_(h_off, non_blocking=True)
+            tsz.copy_(h_sz, non_blocking=True)
+            tnbr.copy_(h_nbr, non_blocking=True)
+            step(qa, qb)
+            h_out.copy_(qb, non_blocking=True)
+        te1.record(stream)
+    stream.synchronize()
+    ems = te0.elapsed_time(te1)
+    if ws > 1:
+        tt = torch.tensor([ems], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ems = float(tt.item())
+    e2e_value = ws * cells_per_step * e2e_steps / (ems / 1e3)
+    h2d = h_q.numel() * itemsize + h_off.numel() * 8 + h_sz.numel() * 4 + h_nbr.numel() * 4
+    d2h = h_out.numel() * itemsize
+
+    peaks, peak_src = _peaks()
+    if prec == "f64":
+        ops = fp64_ops_per_patch(d, p) * n
+        peak_ops = FP64_LANES_PER_SM * NUM_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        achieved = ops / (upd_avg_ms / 1e3)
+        roof = {"bound": "alu", "kernel": "update_kernel<double,3>",
+                "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "T FP64-pipe ops/s", "frac": achieved / peak_ops,
+                "traffic": _traffic(args.workload),
+                "peak_source": "derived: 2 FP64 lanes/SM x 152 SMs x max SM clock "
+                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
+    else:
+        roof = None
+    alg_bytes = alg_bytes_per_patch(d, p, itemsize) * n
+    hbm = {"achieved": alg_bytes / (upd_avg_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+           "unit": "GB/s", "frac": alg_bytes / (upd_avg_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+           "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src}
+    if roof is None:
+        roof = {"bound": "hbm", "kernel": "update_kernel<float,3>", **hbm,
+                "traffic": _traffic(args.workload)}
+    b.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, args.cpu_sample)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": args.workload, "d": d, "s": s, "patch": p,
+                       "n_patches_per_gpu": n, "patch_grid": list(grid), "halo": 1,
+                       "cfl": 0.4, "gamma": 1.4,
+                       "step": "halo_fill+max_eigenvalue_reduce+patch_update",
+                       "l2": "inputs larger than L2 (2 x %.1f GB), no flush"
+                             % (h_q.numel() * itemsize / 1e9),
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": 4 * args.steps,
+            "update_kernel_ms": upd_avg_ms,
+            "roofline": roof,
+            "hbm": hbm,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _traffic(workload):
+    """DRAM bytes per update launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        from paper_2302_09005_gb300 import _build
+        ent = t.get(workload)
+        if ent and ent.get("source_hash") == _build.source_hash():
+            return ent["dram_bytes_per_launch"]
+    except Exception:
+        return None
+    return None
+
+
+def cpu_baseline(workload: str, sample: int):
+    """The oracle as it stands, single-threaded, on the first ``sample``
+    patches of the same workload: CFL reduce + update (Eq. 3-5)."""
+    import oracle
+    d, p, n, grid, prec = WORKLOADS[workload]
+    from paper_2302_09005_gb300 import inputs
+    q, off, sz = inputs.random_batch(sample, p, d, seed=0)
+    dx, cfl = 1.0 / (grid[0] * p), 0.4
+    t = time.perf_counter()
+    _, lam = oracle.max_eigenvalue(q, off, sz, d)
+    dt = oracle.cfl_dt(lam, cfl, dx, d)
+    oracle.patch_update(q, off, sz, d, dx, dt)
+    el = time.perf_counter() - t
+    return {"value": sample * p ** d / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample} of {n} patches ({p}^{d}, FP64): max-eigenvalue reduce + "
+                      f"update, one step, {el:.2f} s"}
+
+
+def run_reference(args, ws, rank):
+    """The oracle on the host cores, same metric and workload, each step a
+    bounded sample of the patches."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2302_09005_gb300 import inputs
+    oracle.build()
+    d, p, n, grid, prec = WORKLOADS[args.workload]
+    sample = args.cpu_sample
+    q, off, sz = inputs.random_batch(sample, p, d, seed=0)
+    dx, cfl = 1.0 / (grid[0] * p), 0.4
+
+    def one():
+        _, lam = oracle.max_eigenvalue(q, off, sz, d)
+        dt = oracle.cfl_dt(lam, cfl, dx, d)
+        oracle.patch_update(q, off, sz, d, dx, dt)
+
+    for _ in range(args.warmup):
+        one()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t
+    value = sample * p ** d * args.steps / el
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "d": d, "patch": p, "n_patches_per_gpu": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} of {n} patches per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="euler3d_fp64_262144x5")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=32768)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

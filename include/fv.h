@@ -1,0 +1,203 @@
+/*
+ * fv.h -- C ABI of the batched finite-volume patch library (libfv.so).
+ *
+ * The library advances many small Cartesian patches of a block-structured
+ * mesh by one explicit Euler step of a Rusanov finite-volume scheme for the
+ * compressible Euler equations, as in arXiv 2302.09005 ("GPU Offloading in
+ * ExaHyPE Through C++ Standard Algorithms"):
+ *   - PDE and flux f^j(q): Sec. 2, Eq. 1-2 (energy flux (E+p) j_j / rho);
+ *   - update Q^{n+1} = Q^n - dt/dx sum_j (F_{+1/2} - F_{-1/2}): Eq. 3,
+ *     Algorithm 1 step 7;
+ *   - Rusanov face flux F = 1/2 [f(Q_L) + f(Q_R) - a (Q_R - Q_L)]: Eq. 4;
+ *   - a = max over the two states of |u_j| + c: Eq. 5;
+ *   - per-patch maximum eigenvalue: Algorithm 1 step 10;
+ *   - a batch of N patches in one kernel invocation: Sec. 3 (batched kernel).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Device pointers.  Every array argument is a DEVICE pointer owned by the
+ * caller (for example the data pointer of a CUDA tensor), unless its
+ * description says "host".  The library never frees caller memory.
+ *
+ * Asynchrony.  Every call that launches work enqueues it on the handle's
+ * CUDA stream and returns without synchronising.  Arguments are validated on
+ * the host before anything is enqueued; an invalid call enqueues nothing and
+ * returns an error status.  Per-patch metadata lives on the device and is
+ * checked by the kernels: a patch with an invalid size or offset is skipped
+ * and flags the handle's device status word (read it with fv_get_status).
+ *
+ * Patch layout.  Patch i occupies the elements
+ *   [patch_offsets[i], patch_offsets[i] + (p_i + 2h)^d * s)
+ * of a flat buffer of doubles (FV_FP64 handles) or floats (FV_FP32 handles),
+ * with p_i = patch_sizes[i] interior cells per axis and halo width h.  Cells
+ * are ordered x fastest, then y, then z; the s unknowns of a cell are
+ * contiguous: (rho, j_1, .., j_d, E) with j = rho u the momentum and E the
+ * total energy.  Interior cells have every coordinate in [h, h+p_i).
+ * Every offset must be a multiple of 16 bytes (2 doubles / 4 floats).
+ *
+ * Errors.  Functions return fv_status.  FV_ERR_CUDA carries the CUDA error
+ * text in fv_last_error().  No entry point traps or aborts the process.
+ */
+#ifndef FV_H
+#define FV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FV_OK = 0,
+  FV_ERR_INVALID_ARG = 1, /* bad argument; nothing was enqueued            */
+  FV_ERR_ALIGNMENT = 2,   /* a pointer or patch offset is not 16-B aligned */
+  FV_ERR_UNSUPPORTED = 3, /* valid but not supported (d, s, p, halo)       */
+  FV_ERR_CUDA = 4,        /* a CUDA call failed; see fv_last_error         */
+  FV_ERR_NONPHYSICAL = 5, /* a kernel met rho <= 0, p <= 0 or a NaN        */
+  FV_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                 */
+  FV_ERR_BAD_PATCH = 7    /* a kernel skipped a patch with bad metadata    */
+} fv_status;
+
+typedef enum {
+  FV_FP64 = 0, /* buffers of double, all arithmetic in FP64 */
+  FV_FP32 = 1  /* buffers of float, flux and update arithmetic in FP32;
+                  maximum reductions, dt and conservation sums in FP64 */
+} fv_precision;
+
+typedef struct {
+  double gamma;           /* ratio of specific heats, > 1 (1.4 for air)      */
+  int halo;               /* halo width h; the Rusanov update needs 1        */
+  fv_precision precision; /* element type of every buffer of this handle    */
+  int max_patch_size;     /* largest p the handle will be given; bounds the
+                             shared memory of the update kernel.  0 selects
+                             8 for d = 3 and 17 for d = 1, 2.                 */
+} fv_options;
+
+/* Fills *o with gamma = 1.4, halo = 1, FV_FP64, max_patch_size = 0. */
+void fv_options_default(fv_options* o);
+
+typedef struct fv_batch fv_batch; /* opaque handle */
+
+/*
+ * fv_batch_create -- make a handle for d-dimensional patches with s unknowns
+ * per cell (the Euler system has s = d + 2, Sec. 2), options o (NULL for the
+ * defaults) and the CUDA stream cuda_stream (a cudaStream_t; NULL is the
+ * legacy default stream) on the current CUDA device.
+ * The handle allocates its own small device workspace (status word, time
+ * step slot, reduction partials).  d in {1, 2, 3}; s == d + 2.
+ * Returns FV_ERR_INVALID_ARG for a bad d, s or option, FV_ERR_CUDA if the
+ * workspace cannot be allocated.  *out is NULL on error.
+ */
+fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, void* cuda_stream);
+
+/* Releases the handle and its workspace (synchronises its stream first). */
+fv_status fv_batch_destroy(fv_batch* h);
+
+/* Makes later calls enqueue on cuda_stream. */
+fv_status fv_batch_set_stream(fv_batch* h, void* cuda_stream);
+
+/*
+ * fv_patch_update_batch -- one explicit Euler step (Eq. 3) of n_patches
+ * patches with Rusanov face fluxes (Eq. 4-5): Algorithm 1 with the outer
+ * loop over patches, every face flux computed once and used by both cells.
+ *   in_with_halo  device, patches at Q^n with filled halos; read only.
+ *   out           device, same layout; the interior cells of every patch are
+ *                 overwritten with Q^{n+1}; its halo cells are not written.
+ *                 Must not overlap in_with_halo.
+ *   patch_offsets device int64[n_patches], element offsets into both buffers.
+ *   patch_sizes   device int32[n_patches], p_i in [1, max_patch_size].
+ *   d, s          must equal the handle's.
+ *   dx            cell width (> 0), the same on every axis.
+ *   dt            time step; dt <= 0 uses the device time step written by
+ *                 the last fv_max_eigenvalue_reduce on this handle.
+ * n_patches == 0 enqueues nothing and returns FV_OK.
+ */
+fv_status fv_patch_update_batch(fv_batch* h, const void* in_with_halo, void* out,
+                                const int64_t* patch_offsets, const int32_t* patch_sizes,
+                                int64_t n_patches, int d, int s, double dx, double dt);
+
+/* Optional outputs and checks of fv_patch_update_batch_ex. */
+typedef struct {
+  double* lambda_patch; /* device double[n], per-patch max a over the faces
+                           used (Algorithm 1 step 10), or NULL              */
+  int64_t n_elems;      /* element count of both buffers; > 0 makes the
+                           kernels skip (and flag) patches that would run
+                           past it; 0 disables the check                    */
+} fv_update_extras;
+
+/* fv_patch_update_batch with optional outputs (extras may be NULL). */
+fv_status fv_patch_update_batch_ex(fv_batch* h, const void* in_with_halo, void* out,
+                                   const int64_t* patch_offsets, const int32_t* patch_sizes,
+                                   int64_t n_patches, int d, int s, double dx, double dt,
+                                   const fv_update_extras* extras);
+
+/*
+ * fv_halo_fill -- fills the face halo layers of every patch in place (the
+ * engine's job of keeping halo data consistent, Sec. 2).  Edge and corner
+ * halo cells are not touched; the Rusanov update does not read them.
+ *   neighbours  device int32[n_patches * 2d], per patch in the order
+ *               -x, +x, -y, +y, -z, +z:
+ *                 >= 0 : index of the neighbouring patch, which must have the
+ *                        same p; its h interior layers next to the shared
+ *                        face are copied (a patch may be its own neighbour:
+ *                        periodic);
+ *                 -1   : outflow, each halo cell repeats the nearest
+ *                        interior cell;
+ *                 -2   : reflecting wall, mirror image of the interior with
+ *                        the normal momentum negated.
+ * The kernel reads only interior cells and writes only halo cells.  Patches
+ * or neighbours with invalid metadata are skipped and flag the status word.
+ */
+fv_status fv_halo_fill(fv_batch* h, void* q_with_halo, const int64_t* patch_offsets,
+                       const int32_t* patch_sizes, const int32_t* neighbours, int64_t n_patches);
+
+/*
+ * fv_max_eigenvalue_reduce -- per-patch and batch maximum wave speed and the
+ * CFL time step (Eq. 5; Algorithm 1 step 10).
+ * The per-patch value is the largest a = max(|u_j|+c of the two cells) over
+ * the faces that bound interior cells -- the faces the update uses -- so it
+ * equals the update's lambda_patch output on the same state.
+ *   per_patch_max  device double[n_patches] or NULL.
+ *   global_max     device double[1] or NULL: maximum over the batch (0 for
+ *                  an empty batch).
+ *   cfl, dx        > 0; dt = cfl * dx / (d * global max) is written to the
+ *                  handle's device time step (read by an update with
+ *                  dt <= 0) and to dt_out (device double[1]) if not NULL.
+ * Maxima are exact, so the result does not depend on the order of work.
+ * Uses the handle's workspace for per-block partial maxima.
+ */
+fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
+                                   const int64_t* patch_offsets, const int32_t* patch_sizes,
+                                   int64_t n_patches, double* per_patch_max, double* global_max,
+                                   double cfl, double dx, double* dt_out);
+
+/*
+ * fv_conserved_totals -- FP64 sums over all interior cells of every unknown
+ * (mass, momentum, energy), for conservation checks.  Fixed-order two-stage
+ * reduction (per patch, then per block, then one block), so the result is
+ * bitwise reproducible.  FP32 handles accumulate in FP64.
+ *   totals  device double[s].
+ */
+fv_status fv_conserved_totals(fv_batch* h, const void* q_with_halo, const int64_t* patch_offsets,
+                              const int32_t* patch_sizes, int64_t n_patches, double* totals);
+
+/* Device address of the handle's time step slot (double[1]). */
+fv_status fv_get_dt_ptr(fv_batch* h, double** dt_device);
+
+/*
+ * fv_get_status -- synchronises the handle's stream, reads and clears the
+ * device status word and returns the first error it records (FV_ERR_BAD_PATCH,
+ * FV_ERR_NONPHYSICAL, FV_ERR_TIMEOUT), or the first CUDA error, else FV_OK.
+ */
+fv_status fv_get_status(fv_batch* h);
+
+/* Text of the last error on this handle ("" if none).  Owned by the handle. */
+const char* fv_last_error(const fv_batch* h);
+
+/* Static text naming a status code. */
+const char* fv_status_string(fv_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FV_H */

@@ -1,0 +1,174 @@
+// fv_device.cuh -- device-side building blocks of the Rusanov patch kernels:
+// Euler physics (Eq. 2, Eq. 5), bit-level helpers for exact maxima and
+// positivity checks, and the compile-time patch geometry.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fv {
+
+// Status bits of the handle's device status word.
+enum : unsigned int {
+  ST_BAD_PATCH = 1u,
+  ST_NONPHYSICAL = 2u,
+  ST_TIMEOUT = 4u,
+};
+
+// ---------------------------------------------------------------------------
+// Bit-level helpers.  A wave speed |u|+c is >= 0 or NaN.  With the sign bit
+// cleared, the IEEE bit pattern orders non-negative values like the values
+// themselves and puts every NaN above +inf, so maxima taken on the integer
+// patterns are exact, order independent, and propagate NaN.  They run on the
+// integer pipe, which keeps the FP64 pipe free.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long order_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long order_bits(float x) {
+  return (unsigned long long)(__float_as_uint(x) & 0x7FFFFFFFu);
+}
+// Value of a maximum taken on order_bits of type T, as a double.
+template <typename T>
+__device__ __forceinline__ double order_value(unsigned long long b);
+template <>
+__device__ __forceinline__ double order_value<double>(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+template <>
+__device__ __forceinline__ double order_value<float>(unsigned long long b) {
+  return (double)__uint_as_float((unsigned int)b);
+}
+template <typename T>
+__device__ __forceinline__ T max_by_bits(T a, T b);
+template <>
+__device__ __forceinline__ double max_by_bits<double>(double a, double b) {
+  return order_bits(a) >= order_bits(b) ? a : b;
+}
+template <>
+__device__ __forceinline__ float max_by_bits<float>(float a, float b) {
+  return order_bits(a) >= order_bits(b) ? a : b;
+}
+
+// 0 < x < +inf (not NaN), tested on the bit pattern with integer ops.
+__device__ __forceinline__ bool positive_finite(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b - 1ull) < 0x7FEFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ bool positive_finite(float x) {
+  unsigned int b = __float_as_uint(x);
+  return (b - 1u) < 0x7F7FFFFFu;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Reciprocal and square root.  The IEEE forms are correctly rounded; the
+// kernels use them on every cell of the interior and the face halo.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T recip(T x) {
+  return T(1) / x;
+}
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+
+template <typename T>
+__device__ __forceinline__ T abs_t(T x) {
+  return x < T(0) ? -x : x;
+}
+__device__ __forceinline__ double abs_t(double x) { return fabs(x); }
+__device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
+
+// ---------------------------------------------------------------------------
+// Euler physics of one cell, Eq. 2: q = (rho, j_1..j_D, E),
+// u = j / rho, p = (gamma - 1)(E - j.u / 2), c = sqrt(gamma p / rho).
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+struct Prim {
+  T u[D];
+  T p;
+  T c;
+};
+
+template <typename T, int D>
+__device__ __forceinline__ Prim<T, D> primitives(const T* q, T gm1, T gamma, bool& bad) {
+  Prim<T, D> w;
+  T inv = recip(q[0]);
+  T jj = T(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    w.u[k] = q[1 + k] * inv;
+    jj = k == 0 ? q[1] * w.u[0] : fma(q[1 + k], w.u[k], jj);
+  }
+  w.p = gm1 * fma(T(-0.5), jj, q[D + 1]);
+  T c2 = (gamma * w.p) * inv;
+  w.c = sqrt_t(c2);
+  bad |= !(positive_finite(q[0]) && positive_finite(w.p));
+  return w;
+}
+
+// Flux f^k (S = D + 2 values) and wave speed |u_k| + c of one cell (Eq. 2, 5).
+template <typename T, int D>
+__device__ __forceinline__ void flux_dir(const T* q, const Prim<T, D>& w, int k, T* f, T& lam) {
+  T uk = w.u[k];
+  f[0] = q[1 + k];
+#pragma unroll
+  for (int m = 0; m < D; ++m) f[1 + m] = (m == k) ? fma(q[1 + m], uk, w.p) : q[1 + m] * uk;
+  f[D + 1] = (q[D + 1] + w.p) * uk;
+  lam = abs_t(uk) + w.c;
+}
+
+// ---------------------------------------------------------------------------
+// Patch geometry with a one-cell halo.  P > 0: compile-time patch size;
+// P == 0: runtime size (generic path).
+// ---------------------------------------------------------------------------
+template <int D, int P>
+struct Geom {
+  int p;
+  __device__ __forceinline__ explicit Geom(int p_rt) : p(P > 0 ? P : p_rt) {}
+  __device__ __forceinline__ int ne() const { return p + 2; }
+  __device__ __forceinline__ int ncell() const {  // halo-inclusive cells
+    return D == 1 ? p + 2 : D == 2 ? (p + 2) * (p + 2) : (p + 2) * (p + 2) * (p + 2);
+  }
+  __device__ __forceinline__ int ptrans() const {  // p^(D-1)
+    return D == 1 ? 1 : D == 2 ? p : p * p;
+  }
+  __device__ __forceinline__ int nint() const { return ptrans() * p; }     // p^D
+  __device__ __forceinline__ int nbox() const { return (p + 2) * ptrans(); }  // cells per dir box
+  __device__ __forceinline__ int nface() const { return (p + 1) * ptrans(); }  // faces per dir
+  // linear cell index of halo-inclusive coordinates
+  __device__ __forceinline__ int cell(const int* c) const {
+    int idx = c[D - 1];
+#pragma unroll
+    for (int m = D - 2; m >= 0; --m) idx = idx * (p + 2) + c[m];
+    return idx;
+  }
+  // transverse index of coordinates c (each interior, 1..p) for direction k:
+  // the coordinates other than k, lowest axis fastest, shifted to 0..p-1.
+  __device__ __forceinline__ int trans(const int* c, int k) const {
+    int t = 0;
+#pragma unroll
+    for (int m = D - 1; m >= 0; --m)
+      if (m != k) t = t * p + (c[m] - 1);
+    return t;
+  }
+  // inverse of trans: fill the coordinates other than k from t
+  __device__ __forceinline__ void untrans(int t, int k, int* c) const {
+#pragma unroll
+    for (int m = 0; m < D; ++m)
+      if (m != k) {
+        c[m] = 1 + t % p;
+        t /= p;
+      }
+  }
+};
+
+}  // namespace fv

@@ -1,0 +1,97 @@
+// fv_internal.h -- the handle and the kernel launchers behind the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fv.h"
+
+// Threads per CTA of the patch kernels.
+#define FV_NT 128
+// Maximum number of CTAs of a grid-stride reduction kernel (partials slots).
+#define FV_MAX_RED_BLOCKS 4096
+
+struct fv_batch {
+  int d = 0, s = 0, halo = 1;
+  double gamma = 1.4;
+  fv_precision prec = FV_FP64;
+  int max_patch_size = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  // device workspace (one allocation)
+  void* ws = nullptr;
+  unsigned int* d_status = nullptr;        // status bits
+  double* d_dt = nullptr;                  // time step slot
+  double* d_lam = nullptr;                 // last global maximum
+  unsigned long long* d_partials = nullptr;  // FV_MAX_RED_BLOCKS slots
+  double* d_sum_partials = nullptr;        // FV_MAX_RED_BLOCKS * 8 slots
+  int update_blocks_per_sm = 0;            // occupancy cache
+  char last_error[512] = {0};
+};
+
+namespace fv {
+
+struct UpdateLaunch {
+  const void* in;
+  void* out;
+  const int64_t* off;
+  const int32_t* sizes;
+  int64_t n;
+  int64_t n_elems;
+  int pmax;
+  double gamma;
+  double dx, dt;
+  const double* dt_dev;
+  double* lam_patch;
+  unsigned int* status;
+};
+
+// Shared memory bytes of the update kernel for patches up to pmax.
+size_t update_smem_bytes(int d, fv_precision prec, int pmax);
+cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& a, int grid);
+cudaError_t update_occupancy(const fv_batch* h, int* blocks_per_sm);
+
+struct EigLaunch {
+  const void* q;
+  const int64_t* off;
+  const int32_t* sizes;
+  int64_t n;
+  int halo;
+  double gamma;
+  double* per_patch;
+  unsigned long long* partials;
+  unsigned int* status;
+};
+cudaError_t launch_eig(const fv_batch* h, const EigLaunch& a, int grid);
+cudaError_t launch_eig_finish(const fv_batch* h, const unsigned long long* partials, int nparts,
+                              double* global_out, double* lam_slot, double* dt_slot,
+                              double* dt_out, double cfl, double dx);
+
+struct HaloLaunch {
+  void* q;
+  const int64_t* off;
+  const int32_t* sizes;
+  const int32_t* nbr;
+  int64_t n;
+  int halo;
+  unsigned int* status;
+};
+cudaError_t launch_halo(const fv_batch* h, const HaloLaunch& a, int grid);
+
+struct SumLaunch {
+  const void* q;
+  const int64_t* off;
+  const int32_t* sizes;
+  int64_t n;
+  int halo;
+  double* partials;  // [nchunks][s]
+  unsigned int* status;
+};
+// Patches per chunk of the fixed-order conservation sum.
+#define FV_SUM_CHUNK 1024
+cudaError_t launch_sums(const fv_batch* h, const SumLaunch& a, int nchunks);
+cudaError_t launch_sums_finish(const fv_batch* h, const double* partials, int nchunks,
+                               double* totals);
+
+}  // namespace fv

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libfv (include/fv.h), with the C names.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels
+of libfv.so.  Buffers are CUDA tensors (or raw device addresses as ints);
+the library enqueues work on the handle's stream and returns a status that
+this module turns into an exception.  If the library cannot be loaded the
+import of this module fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+FV_OK = 0
+FV_ERR_INVALID_ARG = 1
+FV_ERR_ALIGNMENT = 2
+FV_ERR_UNSUPPORTED = 3
+FV_ERR_CUDA = 4
+FV_ERR_NONPHYSICAL = 5
+FV_ERR_TIMEOUT = 6
+FV_ERR_BAD_PATCH = 7
+
+FV_FP64 = 0
+FV_FP32 = 1
+
+
+class FvError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        name = _lib().fv_status_string(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else ""))
+
+
+class fv_options(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("halo", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_patch_size", ctypes.c_int)]
+
+
+class fv_update_extras(ctypes.Structure):
+    _fields_ = [("lambda_patch", ctypes.c_void_p), ("n_elems", ctypes.c_int64)]
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libfv.so is not built ({_build.LIB}); run "
+                              "paper_2302_09005_gb300._build.build() or __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        vp, i64, i32, dbl, c_int = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.c_double, ctypes.c_int)
+        L.fv_options_default.argtypes = [ctypes.POINTER(fv_options)]
+        L.fv_options_default.restype = None
+        L.fv_status_string.argtypes = [c_int]
+        L.fv_status_string.restype = ctypes.c_char_p
+        L.fv_batch_create.argtypes = [ctypes.POINTER(vp), c_int, c_int,
+                                      ctypes.POINTER(fv_options), vp]
+        L.fv_batch_destroy.argtypes = [vp]
+        L.fv_batch_set_stream.argtypes = [vp, vp]
+        L.fv_patch_update_batch.argtypes = [vp, vp, vp, vp, vp, i64, c_int, c_int, dbl, dbl]
+        L.fv_patch_update_batch_ex.argtypes = [vp, vp, vp, vp, vp, i64, c_int, c_int, dbl, dbl,
+                                               ctypes.POINTER(fv_update_extras)]
+        L.fv_halo_fill.argtypes = [vp, vp, vp, vp, vp, i64]
+        L.fv_max_eigenvalue_reduce.argtypes = [vp, vp, vp, vp, i64, vp, vp, dbl, dbl, vp]
+        L.fv_conserved_totals.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.fv_get_dt_ptr.argtypes = [vp, ctypes.POINTER(vp)]
+        L.fv_get_status.argtypes = [vp]
+        L.fv_last_error.argtypes = [vp]
+        L.fv_last_error.restype = ctypes.c_char_p
+        for name in ("fv_batch_create", "fv_batch_destroy", "fv_batch_set_stream",
+                     "fv_patch_update_batch", "fv_patch_update_batch_ex", "fv_halo_fill",
+                     "fv_max_eigenvalue_reduce", "fv_conserved_totals", "fv_get_dt_ptr",
+                     "fv_get_status"):
+            getattr(L, name).restype = c_int
+        _LIB = L
+    return _LIB
+
+
+def _ptr(x) -> int | None:
+    """Device address of a tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(h, status: int, where: str):
+    if status != FV_OK:
+        detail = ""
+        if h is not None:
+            detail = (_lib().fv_last_error(h) or b"").decode()
+        raise FvError(status, where, detail)
+
+
+def fv_options_default() -> fv_options:
+    o = fv_options()
+    _lib().fv_options_default(ctypes.byref(o))
+    return o
+
+
+def fv_batch_create(d: int, s: int, options: fv_options | None = None, stream=None) -> int:
+    """Create a handle; ``stream`` is a torch.cuda.Stream, a raw cudaStream_t
+    int or None (the current torch stream)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    sp = stream if isinstance(stream, int) else stream.cuda_stream
+    h = ctypes.c_void_p()
+    st = _lib().fv_batch_create(ctypes.byref(h), d, s,
+                                ctypes.byref(options) if options is not None else None, sp)
+    _check(None, st, "fv_batch_create")
+    return h.value
+
+
+def fv_batch_destroy(h: int):
+    _check(None, _lib().fv_batch_destroy(h), "fv_batch_destroy")
+
+
+def fv_batch_set_stream(h: int, stream):
+    sp = stream if isinstance(stream, int) else stream.cuda_stream
+    _check(h, _lib().fv_batch_set_stream(h, sp), "fv_batch_set_stream")
+
+
+def fv_patch_update_batch(h, in_with_halo, out, patch_offsets, patch_sizes, n_patches: int,
+                          d: int, s: int, dx: float, dt: float):
+    st = _lib().fv_patch_update_batch(h, _ptr(in_with_halo), _ptr(out), _ptr(patch_offsets),
+                                      _ptr(patch_sizes), n_patches, d, s, dx, dt)
+    _check(h, st, "fv_patch_update_batch")
+
+
+def fv_patch_update_batch_ex(h, in_with_halo, out, patch_offsets, patch_sizes, n_patches: int,
+                             d: int, s: int, dx: float, dt: float, lambda_patch=None,
+                             n_elems: int = 0):
+    ex = fv_update_extras(_ptr(lambda_patch), n_elems)
+    st = _lib().fv_patch_update_batch_ex(h, _ptr(in_with_halo), _ptr(out), _ptr(patch_offsets),
+                                         _ptr(patch_sizes), n_patches, d, s, dx, dt,
+                                         ctypes.byref(ex))
+    _check(h, st, "fv_patch_update_batch_ex")
+
+
+def fv_halo_fill(h, q_with_halo, patch_offsets, patch_sizes, neighbours, n_patches: int):
+    st = _lib().fv_halo_fill(h, _ptr(q_with_halo), _ptr(patch_offsets), _ptr(patch_sizes),
+                             _ptr(neighbours), n_patches)
+    _check(h, st, "fv_halo_fill")
+
+
+def fv_max_eigenvalue_reduce(h, q_with_halo, patch_offsets, patch_sizes, n_patches: int,
+                             per_patch_max=None, global_max=None, cfl: float = 0.4,
+                             dx: float = 1.0, dt_out=None):
+    st = _lib().fv_max_eigenvalue_reduce(h, _ptr(q_with_halo), _ptr(patch_offsets),
+                                         _ptr(patch_sizes), n_patches, _ptr(per_patch_max),
+                                         _ptr(global_max), cfl, dx, _ptr(dt_out))
+    _check(h, st, "fv_max_eigenvalue_reduce")
+
+
+def fv_conserved_totals(h, q_with_halo, patch_offsets, patch_sizes, n_patches: int, totals):
+    st = _lib().fv_conserved_totals(h, _ptr(q_with_halo), _ptr(patch_offsets),
+                                    _ptr(patch_sizes), n_patches, _ptr(totals))
+    _check(h, st, "fv_conserved_totals")
+
+
+def fv_get_dt_ptr(h) -> int:
+    p = ctypes.c_void_p()
+    _check(h, _lib().fv_get_dt_ptr(h, ctypes.byref(p)), "fv_get_dt_ptr")
+    return p.value
+
+
+def fv_get_status(h) -> int:
+    """Synchronise and return the device status (does not raise)."""
+    return _lib().fv_get_status(h)
+
+
+def fv_last_error(h) -> str:
+    return (_lib().fv_last_error(h) or b"").decode()
+
+
+class Batch:
+    """Owns one handle; methods forward to the C entry points."""
+
+    def __init__(self, d: int, *, precision: int = FV_FP64, gamma: float = 1.4,
+                 max_patch_size: int = 0, stream=None):
+        o = fv_options_default()
+        o.gamma = gamma
+        o.precision = precision
+        o.max_patch_size = max_patch_size
+        self.d, self.s = d, d + 2
+        self.precision = precision
+        self.h = fv_batch_create(d, d + 2, o, stream)
+
+    def close(self):
+        if self.h:
+            fv_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, q_in, q_out, off, sizes, dx, dt, lambda_patch=None, n_elems=None):
+        n = off.numel()
+        if lambda_patch is None and n_elems is None:
+            fv_patch_update_batch(self.h, q_in, q_out, off, sizes, n, self.d, self.s, dx, dt)
+        else:
+            fv_patch_update_batch_ex(self.h, q_in, q_out, off, sizes, n, self.d, self.s, dx, dt,
+                                     lambda_patch, n_elems or 0)
+
+    def halo_fill(self, q, off, sizes, nbr):
+        fv_halo_fill(self.h, q, off, sizes, nbr, off.numel())
+
+    def max_eigenvalue(self, q, off, sizes, cfl, dx, per_patch=None, global_max=None,
+                       dt_out=None):
+        fv_max_eigenvalue_reduce(self.h, q, off, sizes, off.numel(), per_patch, global_max, cfl,
+                                 dx, dt_out)
+
+    def totals(self, q, off, sizes, out):
+        fv_conserved_totals(self.h, q, off, sizes, off.numel(), out)
+
+    def status(self) -> int:
+        return fv_get_status(self.h)
+
+    def dt_ptr(self) -> int:
+        return fv_get_dt_ptr(self.h)

@@ -77,9 +77,13 @@ def random_batch(n: int, p, d: int, *, seed: int = 0, halo: int = 1, dtype=np.fl
     if n:
         if np.all(sizes == sizes[0]):
             ne = patch_elems(int(sizes[0]), d, s, halo)
-            cells = random_cells(rng, n * ne // s, d, gamma).reshape(n, ne)
-            idx = off[:, None] + np.arange(ne)[None, :]
-            q[idx] = cells
+            stride = int(off[1] - off[0]) if n > 1 else ne
+            view = q[:n * stride].reshape(n, stride)
+            chunk = 1 << 14
+            for c0 in range(0, n, chunk):
+                c1 = min(n, c0 + chunk)
+                view[c0:c1, :ne] = random_cells(rng, (c1 - c0) * ne // s, d,
+                                                gamma).reshape(c1 - c0, ne)
         else:
             for i in range(n):
                 ne = patch_elems(int(sizes[i]), d, s, halo)

@@ -1,0 +1,169 @@
+"""Edge cases of the C ABI on the GPU: empty batches, argument errors
+answered on the host, bad per-patch metadata and non-physical states
+reported through the device status word (never a trap), the largest patch
+size, and two handles on two streams at once."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_09005_gb300 import inputs
+from tests import fvtest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fv():
+    fvtest.ensure_built()
+    fvtest.torch_cuda()
+    from paper_2302_09005_gb300 import fv as fvmod
+    return fvmod
+
+
+def setup_batch(n=8, p=3, d=3, seed=0, dtype=np.float64):
+    q, off, sz = fvtest.random_batch(n, p, d, seed, dtype)
+    return q, off, sz, fvtest.to_dev(q), fvtest.to_dev(off), fvtest.to_dev(sz)
+
+
+def test_empty_batch_is_a_noop(fv):
+    torch = fvtest.torch_cuda()
+    b = fv.Batch(3, max_patch_size=5)
+    q = torch.ones(64, dtype=torch.float64, device="cuda")
+    o = q.clone()
+    off = torch.zeros(0, dtype=torch.int64, device="cuda")
+    sz = torch.zeros(0, dtype=torch.int32, device="cuda")
+    b.update(q, o, off, sz, 0.1, 0.01)
+    b.halo_fill(q, off, sz, torch.zeros(0, dtype=torch.int32, device="cuda"))
+    g = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    b.max_eigenvalue(q, off, sz, 0.4, 0.1, None, g)
+    tot = torch.full((5,), -1.0, dtype=torch.float64, device="cuda")
+    b.totals(q, off, sz, tot)
+    assert b.status() == fv.FV_OK
+    assert torch.equal(q, o)
+    assert g.item() == 0.0
+    assert torch.all(tot == 0.0)
+    b.close()
+
+
+def test_host_side_argument_errors(fv):
+    q, off, sz, tq, toff, tsz = setup_batch()
+    b = fv.Batch(3, max_patch_size=5)
+    out = tq.clone()
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_patch_update_batch(b.h, tq, out, toff, tsz, len(off), 2, 4, 0.1, 0.01)
+    assert e.value.status == fv.FV_ERR_INVALID_ARG
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_patch_update_batch(b.h, tq, None, toff, tsz, len(off), 3, 5, 0.1, 0.01)
+    assert e.value.status == fv.FV_ERR_INVALID_ARG
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_patch_update_batch(b.h, tq, tq, toff, tsz, len(off), 3, 5, 0.1, 0.01)
+    assert e.value.status == fv.FV_ERR_INVALID_ARG
+    with pytest.raises(fv.FvError) as e:  # 8-byte shifted buffer
+        fv.fv_patch_update_batch(b.h, tq[1:], out, toff, tsz, len(off) - 1, 3, 5, 0.1, 0.01)
+    assert e.value.status == fv.FV_ERR_ALIGNMENT
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_patch_update_batch(b.h, tq, out, toff, tsz, len(off), 3, 5, 0.0, 0.01)
+    assert e.value.status == fv.FV_ERR_INVALID_ARG
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_max_eigenvalue_reduce(b.h, tq, toff, tsz, len(off), cfl=-1.0, dx=0.1)
+    assert e.value.status == fv.FV_ERR_INVALID_ARG
+    with pytest.raises(fv.FvError):
+        fv.Batch(3, max_patch_size=40)  # does not fit in shared memory
+    assert b.status() == fv.FV_OK
+    b.close()
+
+
+def test_bad_patch_metadata_is_flagged_and_skipped(fv):
+    torch = fvtest.torch_cuda()
+    d, p, n = 3, 3, 10
+    q, off, sz = fvtest.random_batch(n, p, d, 1)
+    bad_sz = sz.copy()
+    bad_sz[2] = 0      # empty patch
+    bad_sz[5] = 9      # above max_patch_size
+    bad_off = off.copy()
+    bad_off[7] += 1    # not 16-byte aligned
+    tq = fvtest.to_dev(q)
+    out = tq.clone()
+    b = fv.Batch(d, max_patch_size=5)
+    b.update(tq, out, fvtest.to_dev(bad_off), fvtest.to_dev(bad_sz), 0.1, 0.01,
+             n_elems=tq.numel())
+    assert b.status() == fv.FV_ERR_BAD_PATCH
+    assert b.status() == fv.FV_OK  # reading clears the word
+    ref = oracle.patch_update(q, off, sz, d, 0.1, 0.01)
+    got = out.cpu().numpy()
+    s = d + 2
+    ne = (p + 2) ** d * s
+    for i in range(n):
+        blk = slice(off[i], off[i] + ne)
+        if i in (2, 5, 7):
+            assert np.array_equal(got[blk], q[blk])  # skipped, untouched
+        else:
+            assert np.allclose(got[blk], ref[blk], rtol=1e-12, atol=1e-12)
+    # a patch that would run past n_elems is skipped as well
+    out2 = tq.clone()
+    b.update(tq, out2, fvtest.to_dev(off), fvtest.to_dev(sz), 0.1, 0.01,
+             n_elems=int(off[-1]) + 10)
+    assert b.status() == fv.FV_ERR_BAD_PATCH
+    assert torch.equal(out2[off[-1]:], tq[off[-1]:])
+    # a neighbour index outside the batch
+    nbr = inputs.self_periodic_neighbours(n, d)
+    nbr[4, 1] = n + 3
+    b.halo_fill(tq, fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr))
+    assert b.status() == fv.FV_ERR_BAD_PATCH
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nonphysical_state_is_reported(fv, prec):
+    q, off, sz = fvtest.random_batch(6, 3, 2, 2)
+    q = q.copy()
+    q[off[3] + 4 * 5] = -1.0  # negative density in an interior cell
+    q[off[1] + 4 * 6 + 3] = np.nan  # NaN energy
+    if prec:
+        q = q.astype(np.float32)
+    tq = fvtest.to_dev(q)
+    b = fv.Batch(2, precision=prec, max_patch_size=3)
+    b.update(tq, tq.clone(), fvtest.to_dev(off), fvtest.to_dev(sz), 0.1, 0.01)
+    assert b.status() == fv.FV_ERR_NONPHYSICAL
+    b.max_eigenvalue(tq, fvtest.to_dev(off), fvtest.to_dev(sz), 0.4, 0.1)
+    assert b.status() == fv.FV_ERR_NONPHYSICAL
+    b.close()
+
+
+def test_largest_patch_size(fv):
+    """p = max_patch_size at its shared-memory limit (3D FP64 p = 8)."""
+    d, p, n = 3, 8, 30
+    q, off, sz = fvtest.random_batch(n, p, d, 3)
+    tq = fvtest.to_dev(q)
+    out = tq.clone()
+    b = fv.Batch(d, max_patch_size=8)
+    b.update(tq, out, fvtest.to_dev(off), fvtest.to_dev(sz), 0.02, 0.002)
+    assert b.status() == fv.FV_OK
+    ref = oracle.patch_update(q, off, sz, d, 0.02, 0.002)
+    mask = fvtest.interior_mask(off, sz, d, d + 2, len(q))
+    assert np.all(fvtest.per_unknown_rel_err(out.cpu().numpy(), ref, mask, d + 2) <= 1e-12)
+    b.close()
+
+
+def test_two_handles_two_streams(fv):
+    """Concurrent offload from two handles on two streams (each its own
+    workspace) gives the same results as one at a time."""
+    torch = fvtest.torch_cuda()
+    d, p, n = 3, 5, 500
+    q, off, sz = fvtest.random_batch(n, p, d, 4)
+    toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    b1 = fv.Batch(d, max_patch_size=5, stream=s1)
+    b2 = fv.Batch(d, max_patch_size=5, stream=s2)
+    qa, qb = fvtest.to_dev(q), fvtest.to_dev(q)
+    oa, ob = qa.clone(), qb.clone()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        b1.max_eigenvalue(qa, toff, tsz, 0.4, 0.02)
+        b1.update(qa, oa, toff, tsz, 0.02, -1.0)
+        b2.max_eigenvalue(qb, toff, tsz, 0.4, 0.02)
+        b2.update(qb, ob, toff, tsz, 0.02, -1.0)
+    assert b1.status() == fv.FV_OK and b2.status() == fv.FV_OK
+    assert torch.equal(oa, ob)
+    b1.close()
+    b2.close()

@@ -47,6 +47,9 @@ WORKLOADS = {
     # name: (d, p, n_patches, grid, precision)
     "euler3d_fp64_262144x5": (3, 5, 262144, (64, 64, 64), "f64"),
     "euler3d_fp32_262144x5": (3, 5, 262144, (64, 64, 64), "f32"),
+    # small cases of the same kernels (profiling captures, quick checks)
+    "euler3d_fp64_32768x5": (3, 5, 32768, (32, 32, 32), "f64"),
+    "euler3d_fp32_32768x5": (3, 5, 32768, (32, 32, 32), "f32"),
 }
 
 

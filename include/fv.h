@@ -197,6 +197,16 @@ const char* fv_last_error(const fv_batch* h);
 /* Static text naming a status code. */
 const char* fv_status_string(fv_status s);
 
+/*
+ * Diagnostics (no counterpart in the paper).
+ * fv_selftest_math -- evaluates, on the current device and the legacy
+ * default stream, the FP64 reciprocal (which == 0) or square root
+ * (which == 1) that the FP64 kernels use for 1/rho and the sound speed, on
+ * n device doubles x, into the device doubles out; synchronises.  Lets
+ * tests measure their error against the IEEE operations.
+ */
+fv_status fv_selftest_math(const double* x, double* out, int64_t n, int which);
+
 #ifdef __cplusplus
 }
 #endif

@@ -297,4 +297,12 @@ fv_status fv_get_status(fv_batch* h) {
 
 const char* fv_last_error(const fv_batch* h) { return h ? h->last_error : "null handle"; }
 
+fv_status fv_selftest_math(const double* x, double* out, int64_t n, int which) {
+  if (n < 0 || (n > 0 && (!x || !out)) || (which != 0 && which != 1)) return FV_ERR_INVALID_ARG;
+  if (n == 0) return FV_OK;
+  cudaError_t e = fv::launch_selftest_math(x, out, n, which);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? FV_OK : FV_ERR_CUDA;
+}
+
 }  // extern "C"

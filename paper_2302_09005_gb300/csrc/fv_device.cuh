@@ -70,14 +70,41 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 }
 
 // ---------------------------------------------------------------------------
-// Reciprocal and square root.  The IEEE forms are correctly rounded; the
-// kernels use them on every cell of the interior and the face halo.
+// Reciprocal and square root, once per cell of the interior and face halo.
+//
+// FP64 is the scarce unit on GB300 (two FP64 lanes per SM), so the FP64
+// forms take a hardware seed from the special-function unit and refine it
+// with FMAs instead of the full IEEE division and square root sequences:
+//   1/a     Newton-Raphson in its cubic form: with y0 ~ 1/a and
+//           e = 1 - a y0, 1/a = y0 / (1 - e) = y0 (1 + e + e^2 + ...), so
+//           y = y0 + y0 (e + e^2) leaves a relative error of order e^3;
+//   sqrt(x) with r0 ~ x^(-1/2), s0 = x r0 and e = 1 - s0 r0 = 1 - x r0^2,
+//           sqrt(x) = s0 (1 - e)^(-1/2) = s0 (1 + e/2 + 3e^2/8 + ...),
+//           truncated after the e^2 term (binomial series).
+// Both land within an ulp or two of the correctly rounded result (measured
+// by fv_selftest_math against the IEEE operations), far inside the 1e-12
+// tolerance of the update.  The FP32 path keeps the IEEE forms: it is
+// bound by memory traffic, not arithmetic.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T recip(T x) {
-  return T(1) / x;
+__device__ __forceinline__ double recip(double a) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  const double e = fma(-a, y, 1.0);
+  const double t = fma(e, e, e);
+  return fma(y, t, y);
 }
-__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float recip(float a) { return 1.0f / a; }
+
+__device__ __forceinline__ double sqrt_t(double x) {
+  double r;
+  asm("rsqrt.approx.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double s0 = x * r;
+  const double e = fma(-s0, r, 1.0);
+  const double t = e * fma(e, 0.375, 0.5);
+  const double s = fma(s0, t, s0);
+  // sqrt(+0) = +0 (the seed is +inf there); chosen on the bit pattern
+  return __double_as_longlong(x) == 0 ? 0.0 : s;
+}
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 
 template <typename T>

@@ -94,4 +94,6 @@ cudaError_t launch_sums(const fv_batch* h, const SumLaunch& a, int nchunks);
 cudaError_t launch_sums_finish(const fv_batch* h, const double* partials, int nchunks,
                                double* totals);
 
+cudaError_t launch_selftest_math(const double* x, double* out, int64_t n, int which);
+
 }  // namespace fv

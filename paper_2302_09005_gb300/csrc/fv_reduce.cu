@@ -316,4 +316,21 @@ cudaError_t launch_sums_finish(const fv_batch* h, const double* partials, int nc
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Self-test of the FP64 reciprocal and square root used by the kernels.
+// ---------------------------------------------------------------------------
+__global__ void selftest_math_kernel(const double* __restrict__ x, double* __restrict__ out,
+                                     int64_t n, int which) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = which == 0 ? recip(x[i]) : sqrt_t(x[i]);
+}
+
+cudaError_t launch_selftest_math(const double* x, double* out, int64_t n, int which) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  selftest_math_kernel<<<(int)blocks, 256>>>(x, out, n, which);
+  return cudaGetLastError();
+}
+
 }  // namespace fv

@@ -74,6 +74,8 @@ def _lib() -> ctypes.CDLL:
         L.fv_conserved_totals.argtypes = [vp, vp, vp, vp, i64, vp]
         L.fv_get_dt_ptr.argtypes = [vp, ctypes.POINTER(vp)]
         L.fv_get_status.argtypes = [vp]
+        L.fv_selftest_math.argtypes = [vp, vp, i64, c_int]
+        L.fv_selftest_math.restype = c_int
         L.fv_last_error.argtypes = [vp]
         L.fv_last_error.restype = ctypes.c_char_p
         for name in ("fv_batch_create", "fv_batch_destroy", "fv_batch_set_stream",
@@ -178,6 +180,12 @@ def fv_get_dt_ptr(h) -> int:
 def fv_get_status(h) -> int:
     """Synchronise and return the device status (does not raise)."""
     return _lib().fv_get_status(h)
+
+
+def fv_selftest_math(x, out, which: int):
+    """Device FP64 reciprocal (which=0) / square root (which=1) of x into out."""
+    _check(None, _lib().fv_selftest_math(_ptr(x), _ptr(out), x.numel(), which),
+           "fv_selftest_math")
 
 
 def fv_last_error(h) -> str:

@@ -115,12 +115,9 @@ def test_bad_patch_metadata_is_flagged_and_skipped(fv):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_nonphysical_state_is_reported(fv, prec):
-    q, off, sz = fvtest.random_batch(6, 3, 2, 2)
-    q = q.copy()
-    q[off[3] + 4 * 5] = -1.0  # negative density in an interior cell
-    q[off[1] + 4 * 6 + 3] = np.nan  # NaN energy
-    if prec:
-        q = q.astype(np.float32)
+    q, off, sz = fvtest.random_batch(6, 3, 2, 2, np.float32 if prec else np.float64)
+    q[off[3] + 4 * 5] = -1.0  # negative density in a face-halo cell
+    q[off[1] + 4 * 6 + 3] = np.nan  # NaN energy in an interior cell
     tq = fvtest.to_dev(q)
     b = fv.Batch(2, precision=prec, max_patch_size=3)
     b.update(tq, tq.clone(), fvtest.to_dev(off), fvtest.to_dev(sz), 0.1, 0.01)
@@ -167,3 +164,23 @@ def test_two_handles_two_streams(fv):
     assert torch.equal(oa, ob)
     b1.close()
     b2.close()
+
+
+def test_fp64_reciprocal_and_sqrt_within_two_ulp(fv):
+    """The FP64 kernels' Newton-refined reciprocal and square root stay
+    within 2 ulp of the IEEE results over the range of physical states."""
+    torch = fvtest.torch_cuda()
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.uniform(0.05, 20.0, 200000), np.exp(rng.uniform(-30, 30, 100000)),
+                        np.array([1.0, 2.0, 0.5, 1e-300, 1e300])])
+    tx = fvtest.to_dev(x)
+    out = torch.empty_like(tx)
+    for which, ref in ((0, 1.0 / x), (1, np.sqrt(x))):
+        fv.fv_selftest_math(tx, out, which)
+        got = out.cpu().numpy()
+        ulp = np.spacing(ref)
+        assert np.max(np.abs(got - ref) / ulp) <= 2.0, which
+    z = torch.zeros(4, dtype=torch.float64, device="cuda")
+    o = torch.empty_like(z)
+    fv.fv_selftest_math(z, o, 1)
+    assert torch.all(o == 0.0)

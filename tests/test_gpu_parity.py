@@ -86,13 +86,12 @@ def test_update_ragged_sizes_one_launch(fv):
 @pytest.mark.parametrize("d,p,n", [(2, 3, 64), (3, 5, 100), (2, 5, 80)])
 def test_update_fp32_within_1e5(fv, d, p, n):
     s = d + 2
-    q, off, sz = fvtest.random_batch(n, p, d, 13)
-    q32 = q.astype(np.float32)
+    q32, off, sz = fvtest.random_batch(n, p, d, 13, np.float32)
     dx, dt = 1.0 / 64, 0.002
     got, lam = run_update(fv, q32, off, sz, d, dx, dt, prec=1, want_lambda=True)
     ref, lam_ref = oracle.patch_update(q32.astype(np.float64), off, sz, d, dx, dt,
                                        want_lambda=True)
-    mask = fvtest.interior_mask(off, sz, d, s, len(q))
+    mask = fvtest.interior_mask(off, sz, d, s, len(q32))
     err = fvtest.per_unknown_rel_err(got, ref, mask, s)
     assert np.all(err <= TOL32), err
     assert np.allclose(lam, lam_ref, rtol=1e-6, atol=0)
@@ -109,6 +108,11 @@ def test_uniform_state_bitwise(fv, prec, d, p):
         ne = (p + 2) ** d
         q[off[i]:off[i] + ne * s] = np.tile(inputs.random_cells(rng, 1, d)[0], ne)
     qq = q if prec == 0 else q.astype(np.float32)
+    if prec:  # FP32 layout: offsets in multiples of 4 elements
+        qq, off, sz = fvtest.random_batch(n, p, d, 14, np.float32)
+        for i in range(n):
+            ne = (p + 2) ** d
+            qq[off[i]:off[i] + ne * s] = np.tile(q[0:s].astype(np.float32), ne)
     got, _ = run_update(fv, qq, off, sz, d, 0.01, 0.003, prec=prec)
     assert np.array_equal(got, qq)
 
@@ -142,7 +146,6 @@ def test_eigen_reduce_and_device_dt(fv):
     dt_ref = oracle.cfl_dt(glob.item(), cfl, dx, d)
     assert dt_out.item() == dt_ref  # same formula, same operand, correctly rounded
     assert torch.equal(q1, q2)
-    dev_dt = torch.empty(1, dtype=torch.float64, device="cuda")
     b.close()
 
 
@@ -154,9 +157,7 @@ def test_halo_fill_bitwise(fv, prec, d, p, grid, periodic, bnd):
     torch = fvtest.torch_cuda()
     s = d + 2
     n = int(np.prod(grid))
-    q, off, sz = fvtest.random_batch(n, p, d, 16)
-    if prec == 1:
-        q = q.astype(np.float32)
+    q, off, sz = fvtest.random_batch(n, p, d, 16, np.float32 if prec else np.float64)
     nbr = inputs.grid_neighbours(grid, periodic=periodic, boundary=bnd)
     ref = q.astype(np.float64).copy()
     oracle.halo_fill(ref, off, sz, nbr, d, s)
@@ -174,9 +175,7 @@ def test_conserved_totals_deterministic(fv, prec):
     torch = fvtest.torch_cuda()
     d, p, n = 3, 5, 2500  # spans three sum chunks, ragged last chunk
     s = d + 2
-    q, off, sz = fvtest.random_batch(n, p, d, 17)
-    if prec == 1:
-        q = q.astype(np.float32)
+    q, off, sz = fvtest.random_batch(n, p, d, 17, np.float32 if prec else np.float64)
     tq = fvtest.to_dev(q)
     toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
     b = fv.Batch(d, precision=prec, max_patch_size=5)

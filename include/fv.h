@@ -181,6 +181,41 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
 fv_status fv_conserved_totals(fv_batch* h, const void* q_with_halo, const int64_t* patch_offsets,
                               const int32_t* patch_sizes, int64_t n_patches, double* totals);
 
+/*
+ * fv_conserved_totals_noalloc -- the sums of fv_conserved_totals for callers
+ * that cannot allocate device memory (no counterpart in the paper).  Some
+ * callers own the whole GPU through their own memory pool and forbid any
+ * other allocation, or run latency-critical loops in which cudaMalloc or
+ * cudaFree would synchronise the device; they cannot create an fv_batch,
+ * whose workspace is allocated.  This entry point needs no handle and
+ * allocates nothing: it calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Its scratch (the per-chunk partial sums) is a static device
+ * array of 256 KiB inside libfv.so, held on every device that loads the
+ * library until the process exits.
+ *   d, s, precision  as for fv_batch_create (s == d + 2); halo width 1;
+ *                    patch sizes in [1, 64].
+ *   q_with_halo, patch_offsets, patch_sizes, n_patches  as for
+ *                    fv_conserved_totals; n_patches <= 4,194,304
+ *                    (4096 chunks of 1024 patches); larger batches return
+ *                    FV_ERR_UNSUPPORTED and enqueue nothing.
+ *   totals           device double[s], written.
+ *   status_word      device unsigned int or NULL; bad-patch (1) and
+ *                    non-physical (2) bits are OR-ed into it.
+ *   cuda_stream      cudaStream_t to enqueue on (NULL: legacy default stream).
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Every call on a device shares the one array;
+ * each call writes every partial slot it reads before reading it, so no
+ * slot needs clearing, but calls that overlap on the GPU (two streams, two
+ * threads) race on the array and give wrong totals: serialise them.
+ * Results are bitwise equal to fv_conserved_totals on the same input.
+ */
+fv_status fv_conserved_totals_noalloc(int d, int s, fv_precision precision,
+                                      const void* q_with_halo, const int64_t* patch_offsets,
+                                      const int32_t* patch_sizes, int64_t n_patches,
+                                      double* totals, unsigned int* status_word,
+                                      void* cuda_stream);
+
 /* Device address of the handle's time step slot (double[1]). */
 fv_status fv_get_dt_ptr(fv_batch* h, double** dt_device);
 

@@ -76,6 +76,9 @@ def _lib() -> ctypes.CDLL:
         L.fv_get_status.argtypes = [vp]
         L.fv_selftest_math.argtypes = [vp, vp, i64, c_int]
         L.fv_selftest_math.restype = c_int
+        L.fv_conserved_totals_noalloc.argtypes = [c_int, c_int, c_int, vp, vp, vp, i64, vp, vp,
+                                                  vp]
+        L.fv_conserved_totals_noalloc.restype = c_int
         L.fv_last_error.argtypes = [vp]
         L.fv_last_error.restype = ctypes.c_char_p
         for name in ("fv_batch_create", "fv_batch_destroy", "fv_batch_set_stream",
@@ -169,6 +172,21 @@ def fv_conserved_totals(h, q_with_halo, patch_offsets, patch_sizes, n_patches: i
     st = _lib().fv_conserved_totals(h, _ptr(q_with_halo), _ptr(patch_offsets),
                                     _ptr(patch_sizes), n_patches, _ptr(totals))
     _check(h, st, "fv_conserved_totals")
+
+
+def fv_conserved_totals_noalloc(d: int, s: int, precision: int, q_with_halo, patch_offsets,
+                                patch_sizes, n_patches: int, totals, status_word=None,
+                                stream=None):
+    """Conservation sums without a handle and without device allocation
+    (scratch in the library's static device memory); see include/fv.h."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    sp = stream if isinstance(stream, int) else stream.cuda_stream
+    st = _lib().fv_conserved_totals_noalloc(d, s, precision, _ptr(q_with_halo),
+                                            _ptr(patch_offsets), _ptr(patch_sizes), n_patches,
+                                            _ptr(totals), _ptr(status_word), sp)
+    _check(None, st, "fv_conserved_totals_noalloc")
 
 
 def fv_get_dt_ptr(h) -> int:

@@ -5,9 +5,13 @@ Workload (default): 3D compressible Euler (s = 5, gamma = 1.4), FP64,
 64^3 periodic patch mesh (a 320^3-cell domain), every cell an i.i.d. random
 state (rho ~ U[0.5,1.5], u,v,w ~ U[-0.5,0.5], p ~ U[0.5,1.5]).
 
-One step = the whole hot path through the C ABI:
-  fv_halo_fill -> fv_max_eigenvalue_reduce (CFL 0.4, dt left on the device)
-  -> fv_patch_update_batch (dt read on the device), buffers ping-pong.
+One step = the whole hot path through the C ABI, fv_time_step: halo cells
+gathered from the neighbours, Rusanov update with dt from the CFL condition
+(CFL 0.4) on the device, and the maximum wave speed of the new state reduced
+for the next step, in one kernel; buffers ping-pong.  The wave speed of the
+initial state is seeded once (fv_halo_fill + fv_max_eigenvalue_reduce).  The
+same step as three separate kernels (halo fill, reduce, update) and the FP32
+path are measured as variants.
 
 Metric: patch cell-updates per second (interior cells advanced per second).
 The buffers (2 x 3.6 GB) are far larger than L2 (129 MB), so no flush is
@@ -68,7 +72,7 @@ FP64_LANES_PER_SM = 2
 NUM_SMS = 152
 
 
-def fp64_ops_per_patch(d: int, p: int) -> int:
+def fp64_ops_per_patch(d: int, p: int, fused: bool = False) -> int:
     """FP64 pipe operations one patch update needs (the algorithm's count,
     with the reciprocal and square root counted as the FP64 operations of
     their Newton refinements: 3 and 5).  Per cell with primitives: 3 (1/rho)
@@ -81,8 +85,11 @@ def fp64_ops_per_patch(d: int, p: int) -> int:
     faces = d * (p + 1) * p ** (d - 1)
     prim = 13 + 2 * d
     flux = 1 + (d + 1)
-    return (interior * (prim + d * flux) + halo * (prim + flux) + faces * 3 * s
-            + interior * (s * (2 * d - 1) + s))
+    ops = (interior * (prim + d * flux) + halo * (prim + flux) + faces * 3 * s
+           + interior * (s * (2 * d - 1) + s))
+    if fused:  # wave speed of the new state for the next step: primitives + d adds
+        ops += interior * (prim - 1 + d)
+    return ops
 
 
 def alg_bytes_per_patch(d: int, p: int, itemsize: int) -> int:
@@ -158,6 +165,19 @@ def make_workload(name: str, seed: int = 0):
     return q, off, sz, nbr
 
 
+def _events(n):
+    import torch
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(n)]
+
+
+def _interior_view(t, n, stride, p, d, s):
+    """(n, p, .., p, s) view of the interior cells of a flat patch buffer."""
+    ne = p + 2
+    v = t[: n * stride].view(n, stride)[:, : ne ** d * s].reshape((n,) + (ne,) * d + (s,))
+    return v[(slice(None),) + (slice(1, 1 + p),) * d]
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import torch.distributed as dist
@@ -170,9 +190,9 @@ def run_ours(args, ws, rank, local):
     d, p, n, grid, prec = WORKLOADS[args.workload]
     s = d + 2
     fvprec = fv.FV_FP64 if prec == "f64" else fv.FV_FP32
-    tdtype = torch.float64 if prec == "f64" else torch.float32
     itemsize = 8 if prec == "f64" else 4
     q, off, sz, nbr = make_workload(args.workload, seed=rank)
+    stride = int(off[1] - off[0])
     h_q = torch.from_numpy(q).pin_memory()
     h_off = torch.from_numpy(off).pin_memory()
     h_sz = torch.from_numpy(sz).pin_memory()
@@ -180,31 +200,29 @@ def run_ours(args, ws, rank, local):
     h_out = torch.empty_like(h_q).pin_memory()
     del q
     stream = torch.cuda.Stream()
-    qa = h_q.to("cuda", non_blocking=False)
+    qa = h_q.to("cuda")
     qb = qa.clone()
     toff, tsz, tnbr = h_off.cuda(), h_sz.cuda(), h_nbr.cuda()
     b = fv.Batch(d, precision=fvprec, max_patch_size=p, stream=stream)
     dx, cfl = 1.0 / (grid[0] * p), 0.4
     torch.cuda.synchronize()
 
-    def step(src, dst):
-        b.halo_fill(src, toff, tsz, tnbr)
-        b.max_eigenvalue(src, toff, tsz, cfl, dx)
-        b.update(src, dst, toff, tsz, dx, -1.0)
+    def seed(x):  # lambda of the initial state: halo fill + reduce, once
+        b.halo_fill(x, toff, tsz, tnbr)
+        b.max_eigenvalue(x, toff, tsz, cfl, dx)
 
-    # warm-up
     with torch.cuda.stream(stream):
+        seed(qa)
         for _ in range(args.warmup):
-            step(qa, qb)
+            b.time_step(qa, qb, toff, tsz, tnbr, dx, cfl)
             qa, qb = qb, qa
     stream.synchronize()
     if b.status() != fv.FV_OK:
         raise RuntimeError("warm-up: " + fv.fv_last_error(b.h))
 
-    # ---- device-resident timed region ----------------------------------
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # ---- device-resident timed region: K fused time steps -----------------
+    ev = _events(args.steps)
+    t0, t1 = _events(1)[0]
     clocks = ClockSampler(local)
     if ws > 1:
         dist.barrier()
@@ -214,18 +232,15 @@ def run_ours(args, ws, rank, local):
     with torch.cuda.stream(stream):
         t0.record(stream)
         for k in range(args.steps):
-            b.halo_fill(qa, toff, tsz, tnbr)
-            b.max_eigenvalue(qa, toff, tsz, cfl, dx)
             ev[k][0].record(stream)
-            b.update(qa, qb, toff, tsz, dx, -1.0)
+            b.time_step(qa, qb, toff, tsz, tnbr, dx, cfl)
             ev[k][1].record(stream)
             qa, qb = qb, qa
         t1.record(stream)
     stream.synchronize()
     clk = clocks.stop()
-    torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
-    upd_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     if b.status() != fv.FV_OK:
         raise RuntimeError("timed region: " + fv.fv_last_error(b.h))
     if ws > 1:
@@ -235,11 +250,31 @@ def run_ours(args, ws, rank, local):
         dist.barrier()
     cells_per_step = n * p ** d
     value = ws * cells_per_step * args.steps / (ms / 1e3)
-    upd_avg_ms = sum(upd_ms) / len(upd_ms)
+    kern_ms = sum(step_ms) / len(step_ms)
 
-    # ---- end-to-end: host state in, host state out ----------------------
+    variants = {}
+    if not args.no_variants:
+        # the same step as three separate kernels (halo fill, reduce, update)
+        k2 = max(1, min(args.steps, 5))
+        ev2 = _events(k2)
+        with torch.cuda.stream(stream):
+            for k in range(k2):
+                ev2[k][0].record(stream)
+                b.halo_fill(qa, toff, tsz, tnbr)
+                b.max_eigenvalue(qa, toff, tsz, cfl, dx)
+                b.update(qa, qb, toff, tsz, dx, -1.0)
+                ev2[k][1].record(stream)
+                qa, qb = qb, qa
+        stream.synchronize()
+        sep_ms = sum(e[0].elapsed_time(e[1]) for e in ev2) / k2
+        variants["separate_kernels"] = {
+            "value": cells_per_step / (sep_ms / 1e3), "unit": UNIT, "ms_per_step": sep_ms,
+            "steps": k2, "what": "fv_halo_fill + fv_max_eigenvalue_reduce + "
+                                "fv_patch_update_batch per step"}
+
+    # ---- end-to-end through the C ABI with host buffers ----------------------
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    te0, te1 = _events(1)[0]
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -250,7 +285,8 @@ def run_ours(args, ws, rank, local):
             toff.copy_(h_off, non_blocking=True)
             tsz.copy_(h_sz, non_blocking=True)
             tnbr.copy_(h_nbr, non_blocking=True)
-            step(qa, qb)
+            seed(qa)
+            b.time_step(qa, qb, toff, tsz, tnbr, dx, cfl)
             h_out.copy_(qb, non_blocking=True)
         te1.record(stream)
     stream.synchronize()
@@ -263,25 +299,30 @@ def run_ours(args, ws, rank, local):
     h2d = h_q.numel() * itemsize + h_off.numel() * 8 + h_sz.numel() * 4 + h_nbr.numel() * 4
     d2h = h_out.numel() * itemsize
 
+    if prec == "f64" and not args.no_variants:
+        variants["fp32"] = fp32_variant(args, b, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx,
+                                        cfl, stream)
+
     peaks, peak_src = _peaks()
     if prec == "f64":
-        ops = fp64_ops_per_patch(d, p) * n
+        ops = fp64_ops_per_patch(d, p, fused=True) * n
         peak_ops = FP64_LANES_PER_SM * NUM_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6
-        achieved = ops / (upd_avg_ms / 1e3)
-        roof = {"bound": "alu", "kernel": "update_kernel<double,3>",
+        achieved = ops / (kern_ms / 1e3)
+        roof = {"bound": "alu", "kernel": "step_kernel<double,3,gather,fused>",
                 "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "T FP64-pipe ops/s", "frac": achieved / peak_ops,
                 "traffic": _traffic(args.workload),
+                "ops_per_launch": ops,
                 "peak_source": "derived: 2 FP64 lanes/SM x 152 SMs x max SM clock "
                                f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
     else:
         roof = None
     alg_bytes = alg_bytes_per_patch(d, p, itemsize) * n
-    hbm = {"achieved": alg_bytes / (upd_avg_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
-           "unit": "GB/s", "frac": alg_bytes / (upd_avg_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+    hbm = {"achieved": alg_bytes / (kern_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+           "unit": "GB/s", "frac": alg_bytes / (kern_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
            "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src}
     if roof is None:
-        roof = {"bound": "hbm", "kernel": "update_kernel<float,3>", **hbm,
+        roof = {"bound": "hbm", "kernel": "step_kernel<float,3,gather,fused>", **hbm,
                 "traffic": _traffic(args.workload)}
     b.close()
 
@@ -296,16 +337,20 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": args.workload, "d": d, "s": s, "patch": p,
                        "n_patches_per_gpu": n, "patch_grid": list(grid), "halo": 1,
                        "cfl": 0.4, "gamma": 1.4,
-                       "step": "halo_fill+max_eigenvalue_reduce+patch_update",
+                       "step": "fv_time_step: halo gather + Rusanov update + next-step "
+                               "CFL max in one kernel (initial CFL max seeded once)",
                        "l2": "inputs larger than L2 (2 x %.1f GB), no flush"
                              % (h_q.numel() * itemsize / 1e9),
                        "parallelism": f"replicas x{ws}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-            "gpu_launches": 4 * args.steps,
-            "update_kernel_ms": upd_avg_ms,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                    "what": "state + metadata host->device, halo fill + reduce + time step, "
+                            "state device->host, pinned host buffers"},
+            "gpu_launches": args.steps,
+            "step_kernel_ms": kern_ms,
             "roofline": roof,
             "hbm": hbm,
+            "variants": variants,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -313,6 +358,60 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, stream):
+    """FP32 arithmetic on the same workload (FP32-rounded initial state): timed
+    fused steps, and the relative L1 distance to the FP64 path after one
+    step from the same initial state."""
+    import torch
+    from paper_2302_09005_gb300 import fv
+    b = fv.Batch(d, precision=fv.FV_FP32, max_patch_size=p, stream=stream)
+    x64 = h_q.to("cuda")
+    y64 = x64.clone()
+    x = x64.float()
+    y = x.clone()
+    with torch.cuda.stream(stream):
+        b64.halo_fill(x64, toff, tsz, tnbr)
+        b64.max_eigenvalue(x64, toff, tsz, cfl, dx)
+        b64.time_step(x64, y64, toff, tsz, tnbr, dx, cfl)
+        b.halo_fill(x, toff, tsz, tnbr)
+        b.max_eigenvalue(x, toff, tsz, cfl, dx)
+        b.time_step(x, y, toff, tsz, tnbr, dx, cfl)
+    stream.synchronize()
+    i64 = _interior_view(y64, n, stride, p, d, s)
+    i32 = _interior_view(y, n, stride, p, d, s).double()
+    diff = (i32 - i64).abs().reshape(-1, s).sum(0)
+    norm = i64.abs().reshape(-1, s).sum(0)
+    rel_l1 = (diff / norm).tolist()
+    max_rel = ((i32 - i64).abs().reshape(-1, s).amax(0) / i64.abs().reshape(-1, s).amax(0))
+    del i64, i32, diff
+    # timing
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            b.time_step(x, y, toff, tsz, tnbr, dx, cfl)
+        x, y = y, x
+    ev = _events(args.steps)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            b.time_step(x, y, toff, tsz, tnbr, dx, cfl)
+            ev[k][1].record(stream)
+            x, y = y, x
+    stream.synchronize()
+    ok = b.status() == fv.FV_OK
+    ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    peaks, peak_src = _peaks()
+    alg = alg_bytes_per_patch(d, p, 4) * n
+    b.close()
+    return {"value": n * p ** d / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "status_ok": ok,
+            "rel_l1_vs_fp64_one_step": rel_l1, "max_rel_err_vs_fp64_one_step":
+                max_rel.tolist(),
+            "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                         "peak_source": peak_src}}
 
 
 def _traffic(workload):
@@ -398,6 +497,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

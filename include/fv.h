@@ -172,6 +172,43 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
                                    double cfl, double dx, double* dt_out);
 
 /*
+ * fv_time_step -- one full explicit time step of a patch mesh in one kernel
+ * launch: the update of fv_patch_update_batch (Eq. 3-5) with
+ *   - dt = cfl * dx / (d * lambda) from the CFL condition on the current
+ *     state's maximum wave speed lambda, which the handle holds on the
+ *     device (left there by the previous fv_time_step, or by
+ *     fv_max_eigenvalue_reduce on the initial state after its halo fill);
+ *   - the face-halo cells read straight from the neighbours' interiors of
+ *     in_with_halo by the rules of fv_halo_fill (neighbours as there), so
+ *     the halo cells of both buffers are neither read nor written;
+ *   - the maximum wave speed of Q^{n+1} (all interior cells, all directions)
+ *     reduced on the device for the next step.
+ * For a mesh closed by neighbours, outflow and walls this equals, bitwise,
+ * fv_halo_fill + fv_max_eigenvalue_reduce + fv_patch_update_batch with
+ * dt <= 0.  dt is also written to the handle's time step slot.
+ * lambda_patch (nullable): per-patch max a over the faces used.
+ */
+fv_status fv_time_step(fv_batch* h, const void* in_with_halo, void* out,
+                       const int64_t* patch_offsets, const int32_t* patch_sizes,
+                       const int32_t* neighbours, int64_t n_patches, double dx, double cfl,
+                       double* lambda_patch);
+
+/*
+ * fv_run_steps -- n_steps time steps from q0: fv_halo_fill and
+ * fv_max_eigenvalue_reduce on q0, then fv_time_step ping-ponging between q0
+ * and q1.  The result is in q0 if n_steps is even, else in q1.
+ * use_graph != 0 captures the whole sequence into a CUDA graph the first
+ * time a given set of arguments is seen, caches the instantiated graph in
+ * the handle (keyed by every pointer and value argument) and replays it;
+ * it needs a handle created on a non-default stream.  Buffers must not be
+ * freed and reallocated at the same addresses while cached graphs refer to
+ * them (fv_batch_destroy drops the cache).
+ */
+fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* patch_offsets,
+                       const int32_t* patch_sizes, const int32_t* neighbours, int64_t n_patches,
+                       double dx, double cfl, int n_steps, int use_graph);
+
+/*
  * fv_conserved_totals -- FP64 sums over all interior cells of every unknown
  * (mass, momentum, energy), for conservation checks.  Fixed-order two-stage
  * reduction (per patch, then per block, then one block), so the result is
@@ -218,6 +255,10 @@ fv_status fv_conserved_totals_noalloc(int d, int s, fv_precision precision,
 
 /* Device address of the handle's time step slot (double[1]). */
 fv_status fv_get_dt_ptr(fv_batch* h, double** dt_device);
+
+/* Synchronises the handle's stream and copies its time step slot (the dt of
+ * the last reduce or time step) to *dt_host. */
+fv_status fv_read_dt(fv_batch* h, double* dt_host);
 
 /*
  * fv_get_status -- synchronises the handle's stream, reads and clears the

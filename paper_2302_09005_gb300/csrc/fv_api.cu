@@ -4,12 +4,31 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <new>
+#include <tuple>
+#include <utility>
 
 #include "fv_device.cuh"
 #include "fv_internal.h"
 
 namespace {
+
+// Instantiated CUDA graphs of fv_run_steps, keyed by every argument that is
+// baked into the captured launches.
+using GraphKey = std::tuple<const void*, const void*, const void*, const void*, const void*,
+                            int64_t, double, double, int, int>;
+struct GraphCache {
+  std::map<GraphKey, cudaGraphExec_t> exec;
+};
+
+void graph_cache_clear(fv_batch* h) {
+  auto* gc = static_cast<GraphCache*>(h->graph_cache);
+  if (!gc) return;
+  for (auto& kv : gc->exec) cudaGraphExecDestroy(kv.second);
+  delete gc;
+  h->graph_cache = nullptr;
+}
 
 fv_status set_err(fv_batch* h, fv_status st, const char* fmt, ...) {
   if (h) {
@@ -118,10 +137,11 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
   char* w = static_cast<char*>(h->ws);
   h->d_status = reinterpret_cast<unsigned int*>(w);
   h->d_dt = reinterpret_cast<double*>(w + 64);
-  h->d_lam = reinterpret_cast<double*>(w + 128);
+  h->d_lam = reinterpret_cast<unsigned long long*>(w + 128);
   h->d_partials = reinterpret_cast<unsigned long long*>(w + 256);
   h->d_sum_partials = reinterpret_cast<double*>(w + 256 + 8ull * FV_MAX_RED_BLOCKS);
-  e = fv::update_occupancy(h, &h->update_blocks_per_sm);
+  e = fv::update_occupancy(h, false, &h->update_blocks_per_sm);
+  if (e == cudaSuccess) e = fv::update_occupancy(h, true, &h->step_blocks_per_sm);
   if (e != cudaSuccess) {
     cudaFree(h->ws);
     delete h;
@@ -134,6 +154,7 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
 fv_status fv_batch_destroy(fv_batch* h) {
   if (!h) return FV_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(h->stream);
+  graph_cache_clear(h);
   cudaError_t e2 = cudaFree(h->ws);
   delete h;
   return (e == cudaSuccess && e2 == cudaSuccess) ? FV_OK : FV_ERR_CUDA;
@@ -182,6 +203,7 @@ fv_status fv_patch_update_batch_ex(fv_batch* h, const void* in, void* out, const
   l.dt_dev = h->d_dt;
   l.lam_patch = ex ? ex->lambda_patch : nullptr;
   l.status = h->d_status;
+  l.fused = false;
   cudaError_t e = fv::launch_update(h, l, patch_grid(h, n, h->update_blocks_per_sm));
   if (e != cudaSuccess) return cuda_err(h, e, "update kernel");
   return FV_OK;
@@ -239,8 +261,8 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q, const int64_t* of
     e = fv::launch_eig(h, l, grid);
     if (e != cudaSuccess) return cuda_err(h, e, "eigenvalue kernel");
   }
-  e = fv::launch_eig_finish(h, h->d_partials, grid, global_max, h->d_lam, h->d_dt, dt_out, cfl,
-                            dx);
+  e = fv::launch_eig_finish(h, h->d_partials, grid, global_max, &h->d_lam[h->lam_cur], h->d_dt,
+                            dt_out, cfl, dx);
   if (e != cudaSuccess) return cuda_err(h, e, "eigenvalue finish kernel");
   return FV_OK;
 }
@@ -271,6 +293,106 @@ fv_status fv_conserved_totals(fv_batch* h, const void* q, const int64_t* off,
   e = fv::launch_sums_finish(h, h->d_sum_partials, (int)nchunks, totals);
   if (e != cudaSuccess) return cuda_err(h, e, "sums finish kernel");
   return FV_OK;
+}
+
+fv_status fv_time_step(fv_batch* h, const void* in, void* out, const int64_t* off,
+                       const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
+                       double cfl, double* lambda_patch) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  h->last_error[0] = 0;
+  if (!(dx > 0.0) || !(cfl > 0.0)) return set_err(h, FV_ERR_INVALID_ARG, "dx, cfl must be > 0");
+  fv_status st = check_meta(h, in, off, sizes, n);
+  if (st != FV_OK) return st;
+  if (n == 0) return FV_OK;
+  if (!out || !nbr) return set_err(h, FV_ERR_INVALID_ARG, "null output or neighbour table");
+  if (!aligned16(out)) return set_err(h, FV_ERR_ALIGNMENT, "output not 16-byte aligned");
+  if (in == out) return set_err(h, FV_ERR_INVALID_ARG, "in and out alias");
+  const int nxt = h->lam_cur ^ 1;
+  cudaError_t e = cudaMemsetAsync(&h->d_lam[nxt], 0, sizeof(unsigned long long), h->stream);
+  if (e != cudaSuccess) return cuda_err(h, e, "time step: reset wave speed");
+  fv::UpdateLaunch l;
+  l.in = in;
+  l.out = out;
+  l.off = off;
+  l.sizes = sizes;
+  l.nbr = nbr;
+  l.n = n;
+  l.pmax = h->max_patch_size;
+  l.gamma = h->gamma;
+  l.dx = dx;
+  l.cfl = cfl;
+  l.lam_in = &h->d_lam[h->lam_cur];
+  l.lam_next = &h->d_lam[nxt];
+  l.dt_slot = h->d_dt;
+  l.lam_patch = lambda_patch;
+  l.status = h->d_status;
+  l.fused = true;
+  e = fv::launch_update(h, l, patch_grid(h, n, h->step_blocks_per_sm));
+  if (e != cudaSuccess) return cuda_err(h, e, "time step kernel");
+  h->lam_cur = nxt;
+  return FV_OK;
+}
+
+fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* off, const int32_t* sizes,
+                       const int32_t* nbr, int64_t n, double dx, double cfl, int n_steps,
+                       int use_graph) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  h->last_error[0] = 0;
+  if (n_steps < 0) return set_err(h, FV_ERR_INVALID_ARG, "n_steps < 0");
+  if (q0 == q1) return set_err(h, FV_ERR_INVALID_ARG, "q0 and q1 alias");
+  auto enqueue = [&]() -> fv_status {
+    fv_status s = fv_halo_fill(h, q0, off, sizes, nbr, n);
+    if (s == FV_OK) s = fv_max_eigenvalue_reduce(h, q0, off, sizes, n, nullptr, nullptr, cfl, dx,
+                                                 nullptr);
+    void* a = q0;
+    void* b = q1;
+    for (int k = 0; k < n_steps && s == FV_OK; ++k) {
+      s = fv_time_step(h, a, b, off, sizes, nbr, n, dx, cfl, nullptr);
+      std::swap(a, b);
+    }
+    return s;
+  };
+  if (!use_graph) return enqueue();
+  if (h->stream == nullptr)
+    return set_err(h, FV_ERR_UNSUPPORTED, "graph capture needs a non-default stream");
+  const int lam_start = h->lam_cur;
+  const GraphKey key{q0, q1, off, sizes, nbr, n, dx, cfl, n_steps, lam_start};
+  if (!h->graph_cache) h->graph_cache = new (std::nothrow) GraphCache();
+  auto* gc = static_cast<GraphCache*>(h->graph_cache);
+  if (!gc) return set_err(h, FV_ERR_CUDA, "out of host memory");
+  auto it = gc->exec.find(key);
+  if (it == gc->exec.end()) {
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_err(h, e, "begin capture");
+    fv_status s = enqueue();
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (s != FV_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      h->lam_cur = lam_start;
+      return s != FV_OK ? s : cuda_err(h, e, "end capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->lam_cur = lam_start;
+      return cuda_err(h, e, "graph instantiate");
+    }
+    it = gc->exec.emplace(key, exec).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second, h->stream);
+  if (e != cudaSuccess) return cuda_err(h, e, "graph launch");
+  h->lam_cur = lam_start ^ (n_steps & 1);
+  return FV_OK;
+}
+
+fv_status fv_read_dt(fv_batch* h, double* dt_host) {
+  if (!h || !dt_host) return FV_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(dt_host, h->d_dt, sizeof(double), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? FV_OK : cuda_err(h, e, "read dt");
 }
 
 fv_status fv_get_dt_ptr(fv_batch* h, double** dt_device) {

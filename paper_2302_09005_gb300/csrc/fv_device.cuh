@@ -123,6 +123,7 @@ struct Prim {
   T u[D];
   T p;
   T c;
+  T ep;  // E + p, shared by the energy flux of every direction
 };
 
 template <typename T, int D>
@@ -136,6 +137,7 @@ __device__ __forceinline__ Prim<T, D> primitives(const T* q, T gm1, T gamma, boo
     jj = k == 0 ? q[1] * w.u[0] : fma(q[1 + k], w.u[k], jj);
   }
   w.p = gm1 * fma(T(-0.5), jj, q[D + 1]);
+  w.ep = q[D + 1] + w.p;
   T c2 = (gamma * w.p) * inv;
   w.c = sqrt_t(c2);
   bad |= !(positive_finite(q[0]) && positive_finite(w.p));
@@ -149,7 +151,7 @@ __device__ __forceinline__ void flux_dir(const T* q, const Prim<T, D>& w, int k,
   f[0] = q[1 + k];
 #pragma unroll
   for (int m = 0; m < D; ++m) f[1 + m] = (m == k) ? fma(q[1 + m], uk, w.p) : q[1 + m] * uk;
-  f[D + 1] = (q[D + 1] + w.p) * uk;
+  f[D + 1] = w.ep * uk;
   lam = abs_t(uk) + w.c;
 }
 
@@ -195,6 +197,30 @@ struct Geom {
         c[m] = 1 + t % p;
         t /= p;
       }
+  }
+  // Cell index of the cell with coordinate ck along a runtime direction k and
+  // transverse index t, built with selects (no dynamically indexed arrays,
+  // which would live in local memory).
+  __device__ __forceinline__ int cell_kt(int k, int ck, int t) const {
+    const int ne = p + 2;
+    if constexpr (D == 1) {
+      return ck;
+    } else if constexpr (D == 2) {
+      const int a = 1 + t;
+      const int c0 = k == 0 ? ck : a;
+      const int c1 = k == 0 ? a : ck;
+      return c0 + ne * c1;
+    } else {
+      const int a = 1 + t % p, b = 1 + t / p;
+      const int c0 = k == 0 ? ck : a;
+      const int c1 = k == 0 ? a : (k == 1 ? ck : b);
+      const int c2 = k == 2 ? ck : b;
+      return c0 + ne * (c1 + ne * c2);
+    }
+  }
+  // Stride of the cell index along direction k.
+  __device__ __forceinline__ int stride(int k) const {
+    return k == 0 ? 1 : k == 1 ? (p + 2) : (p + 2) * (p + 2);
   }
 };
 

@@ -21,36 +21,44 @@ struct fv_batch {
   int num_sms = 0;
   // device workspace (one allocation)
   void* ws = nullptr;
-  unsigned int* d_status = nullptr;        // status bits
-  double* d_dt = nullptr;                  // time step slot
-  double* d_lam = nullptr;                 // last global maximum
+  unsigned int* d_status = nullptr;          // status bits
+  double* d_dt = nullptr;                    // time step slot
+  unsigned long long* d_lam = nullptr;       // two slots: bits of the global max wave speed
+  int lam_cur = 0;                           // slot holding lambda of the current state
   unsigned long long* d_partials = nullptr;  // FV_MAX_RED_BLOCKS slots
-  double* d_sum_partials = nullptr;        // FV_MAX_RED_BLOCKS * 8 slots
-  int update_blocks_per_sm = 0;            // occupancy cache
+  double* d_sum_partials = nullptr;          // FV_MAX_RED_BLOCKS * 8 slots
+  int update_blocks_per_sm = 0;              // occupancy cache, update mode
+  int step_blocks_per_sm = 0;                // occupancy cache, time-step mode
+  void* graph_cache = nullptr;               // captured multi-step graphs (fv_graph.cu)
   char last_error[512] = {0};
 };
 
 namespace fv {
 
 struct UpdateLaunch {
-  const void* in;
-  void* out;
-  const int64_t* off;
-  const int32_t* sizes;
-  int64_t n;
-  int64_t n_elems;
-  int pmax;
-  double gamma;
-  double dx, dt;
-  const double* dt_dev;
-  double* lam_patch;
-  unsigned int* status;
+  const void* in = nullptr;
+  void* out = nullptr;
+  const int64_t* off = nullptr;
+  const int32_t* sizes = nullptr;
+  const int32_t* nbr = nullptr;  // time-step mode
+  int64_t n = 0;
+  int64_t n_elems = 0;
+  int pmax = 0;
+  double gamma = 1.4;
+  double dx = 0, dt = 0, cfl = 0;
+  const double* dt_dev = nullptr;
+  const unsigned long long* lam_in = nullptr;  // time-step mode
+  unsigned long long* lam_next = nullptr;      // time-step mode
+  double* dt_slot = nullptr;                   // time-step mode
+  double* lam_patch = nullptr;
+  unsigned int* status = nullptr;
+  bool fused = false;  // time-step mode: gather halos, dt from lam_in, reduce lam_next
 };
 
 // Shared memory bytes of the update kernel for patches up to pmax.
 size_t update_smem_bytes(int d, fv_precision prec, int pmax);
 cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& a, int grid);
-cudaError_t update_occupancy(const fv_batch* h, int* blocks_per_sm);
+cudaError_t update_occupancy(const fv_batch* h, bool fused, int* blocks_per_sm);
 
 struct EigLaunch {
   const void* q;
@@ -65,7 +73,7 @@ struct EigLaunch {
 };
 cudaError_t launch_eig(const fv_batch* h, const EigLaunch& a, int grid);
 cudaError_t launch_eig_finish(const fv_batch* h, const unsigned long long* partials, int nparts,
-                              double* global_out, double* lam_slot, double* dt_slot,
+                              double* global_out, unsigned long long* lam_slot, double* dt_slot,
                               double* dt_out, double cfl, double dx);
 
 struct HaloLaunch {

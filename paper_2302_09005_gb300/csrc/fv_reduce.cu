@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(FV_NT) eig_kernel(EigParams<T> a) {
 // maximum and dt = cfl dx / (d lambda_max).
 template <typename T, int D>
 __global__ void eig_finish_kernel(const unsigned long long* __restrict__ partials, int nparts,
-                                  double* global_out, double* lam_slot, double* dt_slot,
-                                  double* dt_out, double cfl, double dx) {
+                                  double* global_out, unsigned long long* lam_slot,
+                                  double* dt_slot, double* dt_out, double cfl, double dx) {
   __shared__ unsigned long long red[32];
   unsigned long long m = 0ull;
   for (int j = threadIdx.x; j < nparts; j += blockDim.x) m = partials[j] > m ? partials[j] : m;
@@ -125,7 +125,7 @@ __global__ void eig_finish_kernel(const unsigned long long* __restrict__ partial
     m = red[0] > m ? red[0] : m;
     const double lam = order_value<T>(m);
     if (global_out) *global_out = lam;
-    *lam_slot = lam;
+    *lam_slot = m;  // bits, read by the next time step
     const double dt = (cfl * dx) / ((double)D * lam);
     *dt_slot = dt;
     if (dt_out) *dt_out = dt;
@@ -162,7 +162,7 @@ cudaError_t launch_eig(const fv_batch* h, const EigLaunch& l, int grid) {
 }
 
 cudaError_t launch_eig_finish(const fv_batch* h, const unsigned long long* partials, int nparts,
-                              double* global_out, double* lam_slot, double* dt_slot,
+                              double* global_out, unsigned long long* lam_slot, double* dt_slot,
                               double* dt_out, double cfl, double dx) {
 #define FV_EIG_FIN(T, D)                                                                    \
   eig_finish_kernel<T, D><<<1, 256, 0, h->stream>>>(partials, nparts, global_out, lam_slot, \

@@ -1,37 +1,55 @@
 // fv_update.cu -- the batched Rusanov patch update (Eq. 3-5, Algorithm 1 with
-// the outer loop over patches).
+// the outer loop over patches), in two modes sharing one kernel:
 //
-// One CTA advances one patch at a time and walks the batch with a grid
-// stride.  Per patch:
-//   stage   the halo-inclusive patch is read from HBM with 16-byte loads and
-//           transposed into shared memory, one array per unknown (SoA), so
-//           consecutive threads read consecutive cells without bank conflicts;
-//   cells   every interior and face-halo cell converts to primitives once and
-//           writes, for each direction whose faces it touches, its flux f^k
-//           and wave speed |u_k| + c (Eq. 2, 5) into a per-direction box;
-//   faces   every face flux G = f_L + f_R - a (Q_R - Q_L) = 2 F (Eq. 4) is
-//           computed exactly once and kept in shared memory;
-//   update  every interior cell sums G_+ - G_- over the directions (x, then
-//           y, then z) and writes Q - (dt / 2dx) sum to HBM (Eq. 3).
-// The per-patch maximum of a over the faces (Algorithm 1 step 10) is reduced
-// with warp shuffles on the integer bit patterns (exact, order free).
+//   update     (fv_patch_update_batch) the halo cells are read from the input
+//              patch, as filled by fv_halo_fill;
+//   time step  (fv_time_step) the face-halo cells are gathered straight from
+//              the neighbours' interiors (periodic / outflow / wall as in
+//              fv_halo_fill), dt comes from the CFL condition on the maximum
+//              wave speed the previous step left on the device, and the
+//              kernel reduces the maximum wave speed of the new state for the
+//              next step.  One launch replaces halo fill + reduce + update
+//              and gives bitwise the same result.
+//
+// Each CTA is persistent and walks its patches i = blockIdx.x + k*gridDim.x.
+// While it computes patch i, the TMA engine copies patch i+1 into the other
+// of two shared-memory stages (cp.async.bulk, completion on an mbarrier), and
+// the halo cells of patch i+1 that live elsewhere are gathered with cp.async.
+// Per patch:
+//   cells   every interior cell converts to primitives once and writes, per
+//           direction, its flux f^k and wave speed |u_k| + c (Eq. 2, 5) into
+//           a per-direction box; then every face-halo cell does the same for
+//           its normal direction only.  The two groups start on warp
+//           boundaries, and halo lanes select their direction without
+//           branching, so warps never diverge.
+//   faces   every face flux G = f_L + f_R - a (Q_R - Q_L) = 2F (Eq. 4) is
+//           computed exactly once and shared by its two cells;
+//   update  every interior cell sums G_+ - G_- over x, then y, then z and
+//           writes Q - (dt / 2dx) sum (Eq. 3).
+// Maxima (per-patch a of Algorithm 1 step 10, next-step wave speed) are taken
+// on integer bit patterns: exact and independent of the order of work.
 #include "fv_device.cuh"
 #include "fv_internal.h"
+#include "fv_ptx.cuh"
 
 namespace fv {
 
 template <typename T>
-struct UpdateParams {
+struct StepParams {
   const T* __restrict__ in;
   T* __restrict__ out;
   const int64_t* __restrict__ off;
   const int32_t* __restrict__ sizes;
+  const int32_t* __restrict__ nbr;  // time-step mode
   int64_t n;
   int64_t n_elems;
   int pmax;
   T gamma, gm1;
-  double dx, dt;
-  const double* dt_dev;
+  double dx, dt, cfl;
+  const double* dt_dev;               // update mode with dt <= 0
+  const unsigned long long* lam_in;   // time-step mode: bits of lambda(Q^n)
+  unsigned long long* lam_next;       // time-step mode: bits of lambda(Q^n+1)
+  double* dt_slot;                    // time-step mode: dt used, written once
   double* lam_patch;
   unsigned int* status;
 };
@@ -40,167 +58,308 @@ template <int D>
 __host__ __device__ inline int ipow_d(int b) {
   return D == 1 ? b : D == 2 ? b * b : b * b * b;
 }
-
-// Elements of shared memory (in units of T) for one patch of size p.
 template <int D>
-__host__ __device__ inline int update_smem_elems(int p) {
-  constexpr int S = D + 2;
-  int ncell = ipow_d<D>(p + 2);
-  int ptr = ipow_d<D>(p) / p;
-  int nbox = (p + 2) * ptr, nface = (p + 1) * ptr;
-  return S * ncell + D * (S + 1) * nbox + D * S * nface;
+__host__ __device__ inline int stage_elems(int p) {
+  return ipow_d<D>(p + 2) * (D + 2);
+}
+template <int D>
+__host__ __device__ inline int fbox_elems(int p) {
+  return D * (D + 3) * (p + 2) * (ipow_d<D>(p) / p);
+}
+template <int D>
+__host__ __device__ inline int gface_elems(int p) {
+  return D * (D + 2) * (p + 1) * (ipow_d<D>(p) / p);
+}
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+constexpr int kHdrBytes = 64;  // two mbarriers + per-warp reduction slots
+static_assert(16 + 8 * (FV_NT / 32) <= kHdrBytes, "header too small");
+
+// Shared-memory carve-up for patches up to pmax (element counts of T).
+template <int D>
+struct Carve {
+  int stage, fbox, gface;
+  __host__ __device__ explicit Carve(int pmax, int vec)
+      : stage(round_up(stage_elems<D>(pmax), vec)),
+        fbox(round_up(fbox_elems<D>(pmax), vec)),
+        gface(round_up(gface_elems<D>(pmax), vec)) {}
+  __host__ __device__ int total() const { return 2 * stage + fbox + gface; }
+};
+
+// Clock cycles a CTA waits for a copy before it reports FV_ERR_TIMEOUT
+// (about one second at 2 GHz).
+constexpr long long kWaitLimit = 2000000000ll;
+
+// ---------------------------------------------------------------------------
+// Copies into a stage
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__device__ __forceinline__ bool patch_ok(const StepParams<T>& a, int64_t j, int& pj,
+                                         int64_t& offj) {
+  constexpr int VEC = 16 / sizeof(T);
+  pj = a.sizes[j];
+  offj = a.off[j];
+  bool ok = pj >= 1 && pj <= a.pmax && offj >= 0 && (offj % VEC) == 0;
+  if (ok && a.n_elems > 0) ok = offj + (int64_t)stage_elems<D>(pj) <= a.n_elems;
+  if (!ok && threadIdx.x == 0) atomicOr(a.status, ST_BAD_PATCH);
+  return ok;
 }
 
-constexpr int kRedBytes = 8 * (FV_NT / 32);
+// Thread 0: bulk copy of the 16-byte-aligned body of patch j into a stage.
+// The ragged tail (< 16 bytes) lies in the last cell of the patch, a corner
+// (d >= 2, never read) or the +x halo cell (d = 1, gathered separately).
+template <typename T, int D>
+__device__ __forceinline__ void issue_stage(const StepParams<T>& a, int pj, int64_t offj, T* st,
+                                            uint64_t* bar) {
+  const uint32_t bytes = (uint32_t)(stage_elems<D>(pj) * sizeof(T)) & ~15u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_expect_tx(bar, bytes);
+  bulk_copy_g2s(st, a.in + offj, bytes, bar);
+}
 
-template <typename T, int D, int P>
-__device__ __forceinline__ void update_patch(const UpdateParams<T>& a, int p_rt, int64_t i,
-                                             int64_t off, T hr, T* smem,
-                                             unsigned long long* red) {
+// All threads: fetch the face-halo cells of patch j that do not come with its
+// bulk copy -- from the neighbours (time-step mode) or the patch's own halo
+// (d = 1, whose +x halo cell may sit in the uncopied tail).  Issued as
+// cp.async element copies; a wall's negated normal momentum is written with a
+// plain load and store.
+template <typename T, int D, bool GATHER>
+__device__ __forceinline__ void gather_halo(const StepParams<T>& a, int64_t j, int pj,
+                                            int64_t offj, T* st) {
+  if constexpr (!GATHER && D != 1) return;
+  constexpr int S = D + 2;
+  constexpr int VEC = 16 / sizeof(T);
+  const Geom<D, 0> g(pj);
+  const int ptr = g.ptrans();
+  const int ntot = 2 * D * ptr * S;
+  const T* own = a.in + offj;
+  for (int e = threadIdx.x; e < ntot; e += FV_NT) {
+    const int hc = e / S;
+    const int v = e - hc * S;
+    const int f = hc / ptr;
+    const int r = hc - f * ptr;
+    const int k = f >> 1, side = f & 1;
+    const int ck = side ? pj + 1 : 0;  // halo layer along k
+    int ck_src = ck;                   // d = 1 update mode: the own halo cell
+    const T* src_patch = own;
+    bool neg = false;
+    if constexpr (GATHER) {
+      const int32_t nb = a.nbr[j * 2 * D + f];
+      bool outflow = true;
+      if (nb >= 0) {
+        bool ok = nb < a.n;
+        int64_t onb = 0;
+        if (ok) {
+          onb = a.off[nb];
+          ok = a.sizes[nb] == pj && onb >= 0 && (onb % VEC) == 0 &&
+               (a.n_elems <= 0 || onb + (int64_t)stage_elems<D>(pj) <= a.n_elems);
+        }
+        if (ok) {
+          src_patch = a.in + onb;
+          ck_src = side ? 1 : pj;  // the neighbour's interior layer next to the face
+          outflow = false;
+        } else {
+          atomicOr(a.status, ST_BAD_PATCH);
+        }
+      } else if (nb == -2) {
+        neg = (v == 1 + k);
+      } else if (nb != -1) {
+        atomicOr(a.status, ST_BAD_PATCH);
+      }
+      if (outflow) ck_src = side ? pj : 1;  // the own interior layer next to the face
+    }
+    const int cd = g.cell_kt(k, ck, r);
+    const int csrc = g.cell_kt(k, ck_src, r);
+    T* dst = st + cd * S + v;
+    const T* src = src_patch + (int64_t)csrc * S + v;
+    if (neg)
+      *dst = -__ldg(src);
+    else
+      cp_async_elem(dst, src);
+  }
+  cp_async_commit();
+}
+
+// State of the copy pipeline of one CTA.
+struct Pipe {
+  uint64_t* bar;
+  uint32_t parity;   // bit s: parity of the next completion of bar[s]
+  uint32_t pending;  // bit s: a bulk copy into stage s is in flight
+  bool timeout;
+};
+
+template <typename T>
+struct NextPatch {
+  int64_t j;  // >= n: none
+  int p;
+  int64_t off;
+  T* st;
+  int slot;
+};
+
+// Between the cell and face phases: wait for the bulk copy of the next patch
+// and start its halo gather, so both overlap the rest of this patch.
+template <typename T, int D, bool GATHER>
+__device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
+                                         const NextPatch<T>& nx) {
+  if (nx.j >= a.n) return;
+  const bool ok = mbar_wait_bounded(&pp.bar[nx.slot], (pp.parity >> nx.slot) & 1u, kWaitLimit);
+  if (ok) {
+    pp.parity ^= 1u << nx.slot;
+    pp.pending &= ~(1u << nx.slot);
+  }
+  if (!ok) {
+    pp.timeout = true;
+    return;
+  }
+  gather_halo<T, D, GATHER>(a, nx.j, nx.p, nx.off, nx.st);
+}
+
+// ---------------------------------------------------------------------------
+// One patch: cells, faces, update.
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__device__ __forceinline__ void flux_dir_sel(const T* q, const Prim<T, D>& w, int k, T* f,
+                                             T& lam) {
+  // direction chosen per lane with selects; fma(x, y, -0) == x * y bitwise
+  T uk = w.u[0], jk = q[1];
+#pragma unroll
+  for (int m = 1; m < D; ++m) {
+    uk = (k == m) ? w.u[m] : uk;
+    jk = (k == m) ? q[1 + m] : jk;
+  }
+  f[0] = jk;
+#pragma unroll
+  for (int m = 0; m < D; ++m) f[1 + m] = fma(q[1 + m], uk, (m == k) ? w.p : T(-0.0));
+  f[D + 1] = w.ep * uk;
+  lam = abs_t(uk) + w.c;
+}
+
+template <typename T, int D, int P, bool GATHER, bool FUSED>
+__device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, int64_t i,
+                                              int64_t off, const T* __restrict__ st, T* F, T* G,
+                                              T hr, unsigned long long* red,
+                                              unsigned long long& lam_next, Pipe& pp,
+                                              const NextPatch<T>& nx) {
   constexpr int S = D + 2;
   constexpr int NT = FV_NT;
   const Geom<D, P> g(p_rt);
   const int p = g.p;
-  const int ncell = g.ncell(), nbox = g.nbox(), nface = g.nface(), nint = g.nint();
-  const int ptr = g.ptrans();
-  T* Qs = smem;                    // [S][ncell]
-  T* Fb = Qs + S * ncell;          // [D][S+1][nbox]: f^k then |u_k|+c
-  T* Gb = Fb + D * (S + 1) * nbox;  // [D][S][nface]
+  const int nbox = g.nbox(), nface = g.nface(), nint = g.nint(), ptr = g.ptrans();
   const int tid = threadIdx.x;
-
-  // ---- stage: HBM -> shared memory, AoS -> SoA --------------------------
-  {
-    const T* src = a.in + off;
-    const int nel = ncell * S;
-    constexpr int VEC = 16 / sizeof(T);
-    const int nvec = nel / VEC;
-    for (int v = tid; v < nvec; v += NT) {
-      T x[VEC];
-      if constexpr (sizeof(T) == 8) {
-        double2 w = __ldg(reinterpret_cast<const double2*>(src) + v);
-        x[0] = w.x;
-        x[1] = w.y;
-      } else {
-        float4 w = __ldg(reinterpret_cast<const float4*>(src) + v);
-        x[0] = w.x;
-        x[1] = w.y;
-        x[2] = w.z;
-        x[3] = w.w;
-      }
-#pragma unroll
-      for (int u = 0; u < VEC; ++u) {
-        int e = v * VEC + u;
-        int c = e / S;
-        Qs[(e - c * S) * ncell + c] = x[u];
-      }
-    }
-    for (int e = nvec * VEC + tid; e < nel; e += NT) {
-      int c = e / S;
-      Qs[(e - c * S) * ncell + c] = __ldg(src + e);
-    }
-  }
-  __syncthreads();
-
-  // ---- cells: primitives once, flux and wave speed per needed direction --
   bool bad = false;
+
+  // ---- cells ----------------------------------------------------------------
   {
-    const int n1 = nint + 2 * D * ptr;
-    for (int t = tid; t < n1; t += NT) {
-      int c[3] = {0, 0, 0};
-      int kdir;
+    const int nint_pad = (nint + 31) & ~31;
+    const int nA = nint_pad + 2 * D * ptr;
+    for (int t = tid; t < nA; t += NT) {
       if (t < nint) {
+        int c[3] = {0, 0, 0};
         int r = t;
 #pragma unroll
         for (int m = 0; m < D; ++m) {
           c[m] = 1 + r % p;
           r /= p;
         }
-        kdir = -1;
-      } else {
-        int j = t - nint;
-        int f = j / ptr;
-        int r = j - f * ptr;
-        kdir = f >> 1;
-        g.untrans(r, kdir, c);
-        c[kdir] = (f & 1) ? p + 1 : 0;
-      }
-      const int cid = g.cell(c);
-      T q[S];
+        const int cid = g.cell(c);
+        T q[S];
 #pragma unroll
-      for (int v = 0; v < S; ++v) q[v] = Qs[v * ncell + cid];
-      Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
+        for (int v = 0; v < S; ++v) q[v] = st[cid * S + v];
+        const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        if (kdir < 0 || kdir == k) {
+        for (int k = 0; k < D; ++k) {
           T f[S], lam;
           flux_dir<T, D>(q, w, k, f, lam);
           const int b = c[k] + (p + 2) * g.trans(c, k);
-          T* F = Fb + k * (S + 1) * nbox;
+          T* Fk = F + k * (S + 1) * nbox;
 #pragma unroll
-          for (int v = 0; v < S; ++v) F[v * nbox + b] = f[v];
-          F[S * nbox + b] = lam;
+          for (int v = 0; v < S; ++v) Fk[v * nbox + b] = f[v];
+          Fk[S * nbox + b] = lam;
         }
+      } else if (t >= nint_pad) {
+        const int hc = t - nint_pad;
+        const int f = hc / ptr;
+        const int r = hc - f * ptr;
+        const int k = f >> 1;
+        const int ck = (f & 1) ? p + 1 : 0;
+        const int cid = g.cell_kt(k, ck, r);
+        T q[S];
+#pragma unroll
+        for (int v = 0; v < S; ++v) q[v] = st[cid * S + v];
+        const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
+        T fl[S], lam;
+        flux_dir_sel<T, D>(q, w, k, fl, lam);
+        const int b = ck + (p + 2) * r;
+        T* Fk = F + k * (S + 1) * nbox;
+#pragma unroll
+        for (int v = 0; v < S; ++v) Fk[v * nbox + b] = fl[v];
+        Fk[S * nbox + b] = lam;
       }
     }
   }
   __syncthreads();
+  mid_hook<T, D, GATHER>(a, pp, nx);
 
-  // ---- faces: G = f_L + f_R - a (Q_R - Q_L), once per face ---------------
+  // ---- faces: G = f_L + f_R - a (Q_R - Q_L), once per face -------------------
   unsigned long long lmax = 0ull;
-  {
-    for (int t = tid; t < D * nface; t += NT) {
-      const int k = t / nface;
-      const int j = t - k * nface;
-      const int tr = j / (p + 1);
-      const int b = j - tr * (p + 1);
-      int c[3] = {0, 0, 0};
-      g.untrans(tr, k, c);
-      c[k] = b;
-      const int cl = g.cell(c);
-      const int stride = k == 0 ? 1 : k == 1 ? (p + 2) : (p + 2) * (p + 2);
-      const int cr = cl + stride;
-      const T* F = Fb + k * (S + 1) * nbox;
-      const int bl = b + (p + 2) * tr;
-      const T am = max_by_bits(F[S * nbox + bl], F[S * nbox + bl + 1]);
-      const unsigned long long ab = order_bits(am);
-      lmax = ab > lmax ? ab : lmax;
-      T* G = Gb + k * S * nface;
+  for (int t = tid; t < D * nface; t += NT) {
+    const int k = t / nface;
+    const int j = t - k * nface;
+    const int tr = j / (p + 1);
+    const int b = j - tr * (p + 1);
+    const int cl = g.cell_kt(k, b, tr);
+    const int cr = cl + g.stride(k);
+    const T* Fk = F + k * (S + 1) * nbox;
+    const int bl = b + (p + 2) * tr;
+    const T am = max_by_bits(Fk[S * nbox + bl], Fk[S * nbox + bl + 1]);
+    const unsigned long long ab = order_bits(am);
+    lmax = ab > lmax ? ab : lmax;
+    T* Gk = G + k * S * nface;
+#pragma unroll
+    for (int v = 0; v < S; ++v) {
+      const T dq = st[cr * S + v] - st[cl * S + v];
+      const T fs = Fk[v * nbox + bl] + Fk[v * nbox + bl + 1];
+      Gk[v * nface + j] = fma(-am, dq, fs);
+    }
+  }
+  __syncthreads();
+
+  // ---- update: Q - (dt/2dx) sum_k (G_+ - G_-) -----------------------------------
+  T* dst_base = a.out + off;
+  for (int t = tid; t < nint; t += NT) {
+    int c[3] = {0, 0, 0};
+    int r = t;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      c[m] = 1 + r % p;
+      r /= p;
+    }
+    const int cid = g.cell(c);
+    T acc[S];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int jm = (c[k] - 1) + (p + 1) * g.trans(c, k);
+      const T* Gk = G + k * S * nface;
 #pragma unroll
       for (int v = 0; v < S; ++v) {
-        const T dq = Qs[v * ncell + cr] - Qs[v * ncell + cl];
-        const T fs = F[v * nbox + bl] + F[v * nbox + bl + 1];
-        G[v * nface + j] = fma(-am, dq, fs);
+        const T dG = Gk[v * nface + jm + 1] - Gk[v * nface + jm];
+        acc[v] = k == 0 ? dG : acc[v] + dG;
       }
     }
-  }
-  __syncthreads();
-
-  // ---- update: Q - (dt/2dx) sum_k (G_+ - G_-), interior cells -------------
-  {
-    T* dst_base = a.out + off;
-    for (int t = tid; t < nint; t += NT) {
-      int c[3] = {0, 0, 0};
-      int r = t;
+    T qn[S];
 #pragma unroll
-      for (int m = 0; m < D; ++m) {
-        c[m] = 1 + r % p;
-        r /= p;
-      }
-      const int cid = g.cell(c);
-      T acc[S];
+    for (int v = 0; v < S; ++v) qn[v] = fma(-hr, acc[v], st[cid * S + v]);
+    T* dst = dst_base + (int64_t)cid * S;
+#pragma unroll
+    for (int v = 0; v < S; ++v) dst[v] = qn[v];
+    if constexpr (FUSED) {
+      // wave speed of the new state for the next step's CFL condition
+      const Prim<T, D> w = primitives<T, D>(qn, a.gm1, a.gamma, bad);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const int jm = (c[k] - 1) + (p + 1) * g.trans(c, k);
-        const T* G = Gb + k * S * nface;
-#pragma unroll
-        for (int v = 0; v < S; ++v) {
-          const T dG = G[v * nface + jm + 1] - G[v * nface + jm];
-          acc[v] = k == 0 ? dG : acc[v] + dG;
-        }
+        const unsigned long long lb = order_bits(abs_t(w.u[k]) + w.c);
+        lam_next = lb > lam_next ? lb : lam_next;
       }
-      T* dst = dst_base + (int64_t)cid * S;
-#pragma unroll
-      for (int v = 0; v < S; ++v) dst[v] = fma(-hr, acc[v], Qs[v * ncell + cid]);
     }
   }
 
@@ -216,70 +375,165 @@ __device__ __forceinline__ void update_patch(const UpdateParams<T>& a, int p_rt,
       a.lam_patch[i] = order_value<T>(m);
     }
   }
-  __syncthreads();  // shared memory is reused by the next patch
 }
 
-template <typename T, int D>
-__device__ __forceinline__ void update_dispatch(const UpdateParams<T>& a, int p, int64_t i,
-                                                int64_t off, T hr, T* smem,
-                                                unsigned long long* red) {
+template <typename T, int D, bool GATHER, bool FUSED>
+__device__ __forceinline__ void patch_dispatch(const StepParams<T>& a, int p, int64_t i,
+                                               int64_t off, const T* st, T* F, T* G, T hr,
+                                               unsigned long long* red,
+                                               unsigned long long& lam_next, Pipe& pp,
+                                               const NextPatch<T>& nx) {
+#define FV_PC(PP) \
+  patch_compute<T, D, PP, GATHER, FUSED>(a, p, i, off, st, F, G, hr, red, lam_next, pp, nx)
   if constexpr (D == 3) {
     switch (p) {
-      case 3: update_patch<T, 3, 3>(a, p, i, off, hr, smem, red); return;
-      case 5: update_patch<T, 3, 5>(a, p, i, off, hr, smem, red); return;
-      case 7: update_patch<T, 3, 7>(a, p, i, off, hr, smem, red); return;
-      default: update_patch<T, 3, 0>(a, p, i, off, hr, smem, red); return;
+      case 3: FV_PC(3); return;
+      case 5: FV_PC(5); return;
+      case 7: FV_PC(7); return;
+      default: FV_PC(0); return;
     }
   } else if constexpr (D == 2) {
     switch (p) {
-      case 3: update_patch<T, 2, 3>(a, p, i, off, hr, smem, red); return;
-      case 5: update_patch<T, 2, 5>(a, p, i, off, hr, smem, red); return;
-      case 8: update_patch<T, 2, 8>(a, p, i, off, hr, smem, red); return;
-      case 17: update_patch<T, 2, 17>(a, p, i, off, hr, smem, red); return;
-      default: update_patch<T, 2, 0>(a, p, i, off, hr, smem, red); return;
+      case 3: FV_PC(3); return;
+      case 5: FV_PC(5); return;
+      case 8: FV_PC(8); return;
+      case 17: FV_PC(17); return;
+      default: FV_PC(0); return;
     }
   } else {
-    update_patch<T, 1, 0>(a, p, i, off, hr, smem, red);
+    FV_PC(0);
   }
+#undef FV_PC
 }
 
-template <typename T, int D>
-__global__ void __launch_bounds__(FV_NT) update_kernel(UpdateParams<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned long long* red = reinterpret_cast<unsigned long long*>(smem_raw);
-  T* smem = reinterpret_cast<T*>(smem_raw + kRedBytes);
-  constexpr int S = D + 2;
+template <typename T, int D, bool GATHER, bool FUSED>
+__global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? 3 : 4) step_kernel(StepParams<T> a) {
   constexpr int VEC = 16 / sizeof(T);
-  const double dtv = a.dt > 0.0 ? a.dt : *a.dt_dev;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(smem_raw + 16);
+  const Carve<D> cv(a.pmax, VEC);
+  T* stage[2];
+  stage[0] = reinterpret_cast<T*>(smem_raw + kHdrBytes);
+  stage[1] = stage[0] + cv.stage;
+  T* F = stage[1] + cv.stage;
+  T* G = F + cv.fbox;
+  const int tid = threadIdx.x;
+
+  double dtv;
+  if constexpr (FUSED) {
+    const double lam = order_value<T>(*a.lam_in);
+    dtv = (a.cfl * a.dx) / ((double)D * lam);
+    if (blockIdx.x == 0 && tid == 0) *a.dt_slot = dtv;
+  } else {
+    dtv = a.dt > 0.0 ? a.dt : *a.dt_dev;
+  }
   const T hr = (T)(0.5 * (dtv / a.dx));
-  for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x) {
-    const int p = a.sizes[i];
-    const int64_t off = a.off[i];
-    bool ok = p >= 1 && p <= a.pmax && off >= 0 && (off % VEC) == 0;
-    if (ok && a.n_elems > 0) ok = off + (int64_t)ipow_d<D>(p + 2) * S <= a.n_elems;
-    if (!ok) {
-      if (threadIdx.x == 0) atomicOr(a.status, ST_BAD_PATCH);
-      continue;
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  Pipe pp{bar, 0u, 0u, false};
+  unsigned long long lam_next = 0ull;
+
+  // first valid patch of this CTA, staged before the loop
+  int64_t cur = blockIdx.x;
+  int pc = 0;
+  int64_t oc = 0;
+  while (cur < a.n && !patch_ok<T, D>(a, cur, pc, oc)) cur += gridDim.x;
+  int s = 0;
+  if (cur < a.n) {
+    if (tid == 0) issue_stage<T, D>(a, pc, oc, stage[0], &bar[0]);
+    pp.pending = 1u;
+    const bool ok = mbar_wait_bounded(&bar[0], 0u, kWaitLimit);
+    if (ok) {
+      pp.parity ^= 1u;
+      pp.pending = 0u;
+      gather_halo<T, D, GATHER>(a, cur, pc, oc, stage[0]);
+    } else {
+      pp.timeout = true;
     }
-    update_dispatch<T, D>(a, p, i, off, hr, smem, red);
+    cp_async_wait_all();
+  }
+  if (__syncthreads_or(pp.timeout)) cur = a.n;
+
+  while (cur < a.n) {
+    NextPatch<T> nx;
+    nx.j = cur + gridDim.x;
+    while (nx.j < a.n && !patch_ok<T, D>(a, nx.j, nx.p, nx.off)) nx.j += gridDim.x;
+    nx.slot = s ^ 1;
+    nx.st = stage[s ^ 1];
+    if (nx.j < a.n) {
+      if (tid == 0) issue_stage<T, D>(a, nx.p, nx.off, nx.st, &bar[s ^ 1]);
+      pp.pending |= 1u << (s ^ 1);
+    }
+    patch_dispatch<T, D, GATHER, FUSED>(a, pc, cur, oc, stage[s], F, G, hr, red, lam_next, pp,
+                                        nx);
+    cp_async_wait_all();
+    if (__syncthreads_or(pp.timeout)) break;
+    cur = nx.j;
+    pc = nx.p;
+    oc = nx.off;
+    s ^= 1;
+  }
+  if (pp.timeout) {
+    // a copy did not complete in time: report, give the copies in flight a
+    // second bounded wait, and leave
+    if (tid == 0) atomicOr(a.status, ST_TIMEOUT);
+    if (pp.pending & 1u) mbar_wait_bounded(&bar[0], pp.parity & 1u, kWaitLimit);
+    if (pp.pending & 2u) mbar_wait_bounded(&bar[1], (pp.parity >> 1) & 1u, kWaitLimit);
+    cp_async_wait_all();
+    return;
+  }
+  if constexpr (FUSED) {
+    lam_next = warp_max_u64(lam_next);
+    if ((tid & 31) == 0) red[tid >> 5] = lam_next;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long m = red[0];
+#pragma unroll
+      for (int w = 1; w < FV_NT / 32; ++w) m = red[w] > m ? red[w] : m;
+      atomicMax(a.lam_next, m);
+    }
   }
 }
 
 size_t update_smem_bytes(int d, fv_precision prec, int pmax) {
-  size_t es = prec == FV_FP64 ? 8 : 4;
-  int elems = d == 1 ? update_smem_elems<1>(pmax)
-              : d == 2 ? update_smem_elems<2>(pmax)
-                       : update_smem_elems<3>(pmax);
-  return kRedBytes + es * (size_t)elems;
+  const int es = prec == FV_FP64 ? 8 : 4;
+  const int vec = 16 / es;
+  const int elems = d == 1   ? Carve<1>(pmax, vec).total()
+                    : d == 2 ? Carve<2>(pmax, vec).total()
+                             : Carve<3>(pmax, vec).total();
+  return kHdrBytes + (size_t)es * elems;
 }
 
-template <typename T, int D>
-static cudaError_t launch_update_t(const fv_batch* h, const UpdateLaunch& l, int grid) {
-  UpdateParams<T> a;
+// Raises the kernel's dynamic shared-memory limit on the current device once
+// (not per launch, so launches can be captured into CUDA graphs).
+template <typename T, int D, bool GATHER, bool FUSED>
+static cudaError_t ensure_smem(size_t smem) {
+  static int set_bytes[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && set_bytes[dev] >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(step_kernel<T, D, GATHER, FUSED>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) set_bytes[dev] = (int)smem;
+  return e;
+}
+
+template <typename T, int D, bool GATHER, bool FUSED>
+static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int grid) {
+  StepParams<T> a;
   a.in = static_cast<const T*>(l.in);
   a.out = static_cast<T*>(l.out);
   a.off = l.off;
   a.sizes = l.sizes;
+  a.nbr = l.nbr;
   a.n = l.n;
   a.n_elems = l.n_elems;
   a.pmax = l.pmax;
@@ -287,46 +541,58 @@ static cudaError_t launch_update_t(const fv_batch* h, const UpdateLaunch& l, int
   a.gm1 = (T)(l.gamma - 1.0);
   a.dx = l.dx;
   a.dt = l.dt;
+  a.cfl = l.cfl;
   a.dt_dev = l.dt_dev;
+  a.lam_in = l.lam_in;
+  a.lam_next = l.lam_next;
+  a.dt_slot = l.dt_slot;
   a.lam_patch = l.lam_patch;
   a.status = l.status;
-  size_t smem = update_smem_bytes(D, h->prec, l.pmax);
-  cudaError_t e = cudaFuncSetAttribute(update_kernel<T, D>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = update_smem_bytes(D, h->prec, l.pmax);
+  cudaError_t e = ensure_smem<T, D, GATHER, FUSED>(smem);
   if (e != cudaSuccess) return e;
-  update_kernel<T, D><<<grid, FV_NT, smem, h->stream>>>(a);
+  step_kernel<T, D, GATHER, FUSED><<<grid, FV_NT, smem, h->stream>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int D>
-static cudaError_t occupancy_t(const fv_batch* h, int* bps) {
-  size_t smem = update_smem_bytes(D, h->prec, h->max_patch_size);
-  cudaError_t e = cudaFuncSetAttribute(update_kernel<T, D>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, update_kernel<T, D>, FV_NT, smem);
+template <typename T, bool GATHER, bool FUSED>
+static cudaError_t launch_by_d(const fv_batch* h, const UpdateLaunch& l, int grid) {
+  if (h->d == 1) return launch_step_t<T, 1, GATHER, FUSED>(h, l, grid);
+  if (h->d == 2) return launch_step_t<T, 2, GATHER, FUSED>(h, l, grid);
+  return launch_step_t<T, 3, GATHER, FUSED>(h, l, grid);
 }
 
 cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& l, int grid) {
-  if (h->prec == FV_FP64) {
-    if (h->d == 1) return launch_update_t<double, 1>(h, l, grid);
-    if (h->d == 2) return launch_update_t<double, 2>(h, l, grid);
-    return launch_update_t<double, 3>(h, l, grid);
+  if (l.fused) {
+    return h->prec == FV_FP64 ? launch_by_d<double, true, true>(h, l, grid)
+                              : launch_by_d<float, true, true>(h, l, grid);
   }
-  if (h->d == 1) return launch_update_t<float, 1>(h, l, grid);
-  if (h->d == 2) return launch_update_t<float, 2>(h, l, grid);
-  return launch_update_t<float, 3>(h, l, grid);
+  return h->prec == FV_FP64 ? launch_by_d<double, false, false>(h, l, grid)
+                            : launch_by_d<float, false, false>(h, l, grid);
 }
 
-cudaError_t update_occupancy(const fv_batch* h, int* bps) {
-  if (h->prec == FV_FP64) {
-    if (h->d == 1) return occupancy_t<double, 1>(h, bps);
-    if (h->d == 2) return occupancy_t<double, 2>(h, bps);
-    return occupancy_t<double, 3>(h, bps);
-  }
-  if (h->d == 1) return occupancy_t<float, 1>(h, bps);
-  if (h->d == 2) return occupancy_t<float, 2>(h, bps);
-  return occupancy_t<float, 3>(h, bps);
+template <typename T, int D, bool GATHER, bool FUSED>
+static cudaError_t occupancy_t(const fv_batch* h, int* bps) {
+  const size_t smem = update_smem_bytes(D, h->prec, h->max_patch_size);
+  cudaError_t e = ensure_smem<T, D, GATHER, FUSED>(smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, step_kernel<T, D, GATHER, FUSED>,
+                                                       FV_NT, smem);
+}
+
+template <typename T, bool GATHER, bool FUSED>
+static cudaError_t occ_by_d(const fv_batch* h, int* bps) {
+  if (h->d == 1) return occupancy_t<T, 1, GATHER, FUSED>(h, bps);
+  if (h->d == 2) return occupancy_t<T, 2, GATHER, FUSED>(h, bps);
+  return occupancy_t<T, 3, GATHER, FUSED>(h, bps);
+}
+
+cudaError_t update_occupancy(const fv_batch* h, bool fused, int* bps) {
+  if (fused)
+    return h->prec == FV_FP64 ? occ_by_d<double, true, true>(h, bps)
+                              : occ_by_d<float, true, true>(h, bps);
+  return h->prec == FV_FP64 ? occ_by_d<double, false, false>(h, bps)
+                            : occ_by_d<float, false, false>(h, bps);
 }
 
 }  // namespace fv

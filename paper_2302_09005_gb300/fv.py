@@ -79,6 +79,12 @@ def _lib() -> ctypes.CDLL:
         L.fv_conserved_totals_noalloc.argtypes = [c_int, c_int, c_int, vp, vp, vp, i64, vp, vp,
                                                   vp]
         L.fv_conserved_totals_noalloc.restype = c_int
+        L.fv_time_step.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, vp]
+        L.fv_time_step.restype = c_int
+        L.fv_run_steps.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, c_int, c_int]
+        L.fv_run_steps.restype = c_int
+        L.fv_read_dt.argtypes = [vp, ctypes.POINTER(dbl)]
+        L.fv_read_dt.restype = c_int
         L.fv_last_error.argtypes = [vp]
         L.fv_last_error.restype = ctypes.c_char_p
         for name in ("fv_batch_create", "fv_batch_destroy", "fv_batch_set_stream",
@@ -168,6 +174,21 @@ def fv_max_eigenvalue_reduce(h, q_with_halo, patch_offsets, patch_sizes, n_patch
     _check(h, st, "fv_max_eigenvalue_reduce")
 
 
+def fv_time_step(h, in_with_halo, out, patch_offsets, patch_sizes, neighbours, n_patches: int,
+                 dx: float, cfl: float, lambda_patch=None):
+    st = _lib().fv_time_step(h, _ptr(in_with_halo), _ptr(out), _ptr(patch_offsets),
+                             _ptr(patch_sizes), _ptr(neighbours), n_patches, dx, cfl,
+                             _ptr(lambda_patch))
+    _check(h, st, "fv_time_step")
+
+
+def fv_run_steps(h, q0, q1, patch_offsets, patch_sizes, neighbours, n_patches: int, dx: float,
+                 cfl: float, n_steps: int, use_graph: bool = False):
+    st = _lib().fv_run_steps(h, _ptr(q0), _ptr(q1), _ptr(patch_offsets), _ptr(patch_sizes),
+                             _ptr(neighbours), n_patches, dx, cfl, n_steps, int(use_graph))
+    _check(h, st, "fv_run_steps")
+
+
 def fv_conserved_totals(h, q_with_halo, patch_offsets, patch_sizes, n_patches: int, totals):
     st = _lib().fv_conserved_totals(h, _ptr(q_with_halo), _ptr(patch_offsets),
                                     _ptr(patch_sizes), n_patches, _ptr(totals))
@@ -193,6 +214,13 @@ def fv_get_dt_ptr(h) -> int:
     p = ctypes.c_void_p()
     _check(h, _lib().fv_get_dt_ptr(h, ctypes.byref(p)), "fv_get_dt_ptr")
     return p.value
+
+
+def fv_read_dt(h) -> float:
+    """Synchronise and return the handle's device time step."""
+    x = ctypes.c_double()
+    _check(h, _lib().fv_read_dt(h, ctypes.byref(x)), "fv_read_dt")
+    return x.value
 
 
 def fv_get_status(h) -> int:
@@ -244,6 +272,12 @@ class Batch:
 
     def halo_fill(self, q, off, sizes, nbr):
         fv_halo_fill(self.h, q, off, sizes, nbr, off.numel())
+
+    def time_step(self, q_in, q_out, off, sizes, nbr, dx, cfl, lambda_patch=None):
+        fv_time_step(self.h, q_in, q_out, off, sizes, nbr, off.numel(), dx, cfl, lambda_patch)
+
+    def run_steps(self, q0, q1, off, sizes, nbr, dx, cfl, n_steps, use_graph=False):
+        fv_run_steps(self.h, q0, q1, off, sizes, nbr, off.numel(), dx, cfl, n_steps, use_graph)
 
     def max_eigenvalue(self, q, off, sizes, cfl, dx, per_patch=None, global_max=None,
                        dt_out=None):

@@ -116,11 +116,15 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-  size_t smem = fv::update_smem_bytes(d, h->prec, h->max_patch_size);
   int smem_optin = 0;
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  if (e == cudaSuccess && smem > (size_t)smem_optin) {
+  h->nstage = 2;
+  if (e == cudaSuccess &&
+      fv::update_smem_bytes(d, h->prec, h->max_patch_size, 2) > (size_t)smem_optin)
+    h->nstage = 1;
+  if (e == cudaSuccess &&
+      fv::update_smem_bytes(d, h->prec, h->max_patch_size, 1) > (size_t)smem_optin) {
     delete h;
     return FV_ERR_UNSUPPORTED;  // max_patch_size too large for shared memory
   }

@@ -16,6 +16,7 @@ struct fv_batch {
   double gamma = 1.4;
   fv_precision prec = FV_FP64;
   int max_patch_size = 0;
+  int nstage = 2;  // shared-memory stages of the update kernel
   cudaStream_t stream = nullptr;
   int device = 0;
   int num_sms = 0;
@@ -56,7 +57,7 @@ struct UpdateLaunch {
 };
 
 // Shared memory bytes of the update kernel for patches up to pmax.
-size_t update_smem_bytes(int d, fv_precision prec, int pmax);
+size_t update_smem_bytes(int d, fv_precision prec, int pmax, int nstage);
 cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& a, int grid);
 cudaError_t update_occupancy(const fv_batch* h, bool fused, int* blocks_per_sm);
 

@@ -44,6 +44,7 @@ struct StepParams {
   int64_t n;
   int64_t n_elems;
   int pmax;
+  int nstage;  // shared-memory stages: 2 (copy overlaps compute) or 1
   T gamma, gm1;
   double dx, dt, cfl;
   const double* dt_dev;               // update mode with dt <= 0
@@ -75,15 +76,19 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 constexpr int kHdrBytes = 64;  // two mbarriers + per-warp reduction slots
 static_assert(16 + 8 * (FV_NT / 32) <= kHdrBytes, "header too small");
 
-// Shared-memory carve-up for patches up to pmax (element counts of T).
+// Shared-memory carve-up for patches up to pmax (element counts of T).  Two
+// stages let the copy of the next patch overlap the current one; when two do
+// not fit in shared memory (large patches) one stage is used and the copy of
+// the next patch starts after the current patch is done.
 template <int D>
 struct Carve {
-  int stage, fbox, gface;
-  __host__ __device__ explicit Carve(int pmax, int vec)
-      : stage(round_up(stage_elems<D>(pmax), vec)),
+  int nstage, stage, fbox, gface;
+  __host__ __device__ Carve(int pmax, int vec, int nstage_)
+      : nstage(nstage_),
+        stage(round_up(stage_elems<D>(pmax), vec)),
         fbox(round_up(fbox_elems<D>(pmax), vec)),
         gface(round_up(gface_elems<D>(pmax), vec)) {}
-  __host__ __device__ int total() const { return 2 * stage + fbox + gface; }
+  __host__ __device__ int total() const { return nstage * stage + fbox + gface; }
 };
 
 // Clock cycles a CTA waits for a copy before it reports FV_ERR_TIMEOUT
@@ -412,11 +417,12 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? 3 : 4) step_kernel(Ste
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   unsigned long long* red = reinterpret_cast<unsigned long long*>(smem_raw + 16);
-  const Carve<D> cv(a.pmax, VEC);
+  const Carve<D> cv(a.pmax, VEC, a.nstage);
+  const bool single = a.nstage == 1;
   T* stage[2];
   stage[0] = reinterpret_cast<T*>(smem_raw + kHdrBytes);
-  stage[1] = stage[0] + cv.stage;
-  T* F = stage[1] + cv.stage;
+  stage[1] = single ? stage[0] : stage[0] + cv.stage;
+  T* F = stage[0] + cv.nstage * cv.stage;
   T* G = F + cv.fbox;
   const int tid = threadIdx.x;
 
@@ -465,20 +471,30 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? 3 : 4) step_kernel(Ste
     NextPatch<T> nx;
     nx.j = cur + gridDim.x;
     while (nx.j < a.n && !patch_ok<T, D>(a, nx.j, nx.p, nx.off)) nx.j += gridDim.x;
-    nx.slot = s ^ 1;
-    nx.st = stage[s ^ 1];
-    if (nx.j < a.n) {
-      if (tid == 0) issue_stage<T, D>(a, nx.p, nx.off, nx.st, &bar[s ^ 1]);
-      pp.pending |= 1u << (s ^ 1);
+    nx.slot = single ? 0 : s ^ 1;
+    nx.st = stage[nx.slot];
+    NextPatch<T> nx_mid = nx;  // what the mid-patch hook waits for and gathers
+    if (single) {
+      nx_mid.j = a.n;  // the one stage is busy until this patch is done
+    } else if (nx.j < a.n) {
+      if (tid == 0) issue_stage<T, D>(a, nx.p, nx.off, nx.st, &bar[nx.slot]);
+      pp.pending |= 1u << nx.slot;
     }
     patch_dispatch<T, D, GATHER, FUSED>(a, pc, cur, oc, stage[s], F, G, hr, red, lam_next, pp,
-                                        nx);
+                                        nx_mid);
     cp_async_wait_all();
     if (__syncthreads_or(pp.timeout)) break;
+    if (single && nx.j < a.n) {
+      if (tid == 0) issue_stage<T, D>(a, nx.p, nx.off, nx.st, &bar[0]);
+      pp.pending |= 1u;
+      mid_hook<T, D, GATHER>(a, pp, nx);
+      cp_async_wait_all();
+      if (__syncthreads_or(pp.timeout)) break;
+    }
     cur = nx.j;
     pc = nx.p;
     oc = nx.off;
-    s ^= 1;
+    if (!single) s ^= 1;
   }
   if (pp.timeout) {
     // a copy did not complete in time: report, give the copies in flight a
@@ -502,12 +518,12 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? 3 : 4) step_kernel(Ste
   }
 }
 
-size_t update_smem_bytes(int d, fv_precision prec, int pmax) {
+size_t update_smem_bytes(int d, fv_precision prec, int pmax, int nstage) {
   const int es = prec == FV_FP64 ? 8 : 4;
   const int vec = 16 / es;
-  const int elems = d == 1   ? Carve<1>(pmax, vec).total()
-                    : d == 2 ? Carve<2>(pmax, vec).total()
-                             : Carve<3>(pmax, vec).total();
+  const int elems = d == 1   ? Carve<1>(pmax, vec, nstage).total()
+                    : d == 2 ? Carve<2>(pmax, vec, nstage).total()
+                             : Carve<3>(pmax, vec, nstage).total();
   return kHdrBytes + (size_t)es * elems;
 }
 
@@ -537,6 +553,7 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.n = l.n;
   a.n_elems = l.n_elems;
   a.pmax = l.pmax;
+  a.nstage = h->nstage;
   a.gamma = (T)l.gamma;
   a.gm1 = (T)(l.gamma - 1.0);
   a.dx = l.dx;
@@ -548,7 +565,7 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.dt_slot = l.dt_slot;
   a.lam_patch = l.lam_patch;
   a.status = l.status;
-  const size_t smem = update_smem_bytes(D, h->prec, l.pmax);
+  const size_t smem = update_smem_bytes(D, h->prec, l.pmax, h->nstage);
   cudaError_t e = ensure_smem<T, D, GATHER, FUSED>(smem);
   if (e != cudaSuccess) return e;
   step_kernel<T, D, GATHER, FUSED><<<grid, FV_NT, smem, h->stream>>>(a);
@@ -573,7 +590,7 @@ cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& l, int grid) {
 
 template <typename T, int D, bool GATHER, bool FUSED>
 static cudaError_t occupancy_t(const fv_batch* h, int* bps) {
-  const size_t smem = update_smem_bytes(D, h->prec, h->max_patch_size);
+  const size_t smem = update_smem_bytes(D, h->prec, h->max_patch_size, h->nstage);
   cudaError_t e = ensure_smem<T, D, GATHER, FUSED>(smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, step_kernel<T, D, GATHER, FUSED>,

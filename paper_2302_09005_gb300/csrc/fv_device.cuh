@@ -86,9 +86,38 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // tolerance of the update.  The FP32 path keeps the IEEE forms: it is
 // bound by memory traffic, not arithmetic.
 // ---------------------------------------------------------------------------
+//
+// The seeds come from the FP32 special-function unit, not from the f64
+// approximation instructions (which spend FP64 operations of their own): the
+// double's sign, exponent and leading 20 fraction bits are repacked as a
+// float with integer operations, the float reciprocal / reciprocal square
+// root is taken, and the result is repacked as a double.  The seed is good
+// to about 2^-20, so one cubic step leaves ~2^-60 for 1/a and the two-term
+// series ~2^-62 for sqrt.  Arguments outside the float exponent range (and
+// zero, negative, non-finite values) take the IEEE operation instead.
+
+// Double -> float carrying the double's leading 20 fraction bits (truncated);
+// false if the exponent does not fit a normal float with margin.
+__device__ __forceinline__ bool f64_seed_as_f32(double x, float& f) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const int ef = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if ((hi >> 31) != 0u || ef < 4 || ef > 250) return false;
+  f = __uint_as_float(((unsigned)ef << 23) | ((hi & 0xFFFFFu) << 3));
+  return true;
+}
+// Exact float -> double by repacking the fields (positive normal floats).
+__device__ __forceinline__ double f32_as_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = ((b >> 23) & 0xFFu) - 127u + 1023u;
+  return __hiloint2double((int)((e << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
+}
+
 __device__ __forceinline__ double recip(double a) {
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  float f;
+  if (!f64_seed_as_f32(a, f)) return 1.0 / a;
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
+  const double y = f32_as_f64(rf);
   const double e = fma(-a, y, 1.0);
   const double t = fma(e, e, e);
   return fma(y, t, y);
@@ -96,14 +125,15 @@ __device__ __forceinline__ double recip(double a) {
 __device__ __forceinline__ float recip(float a) { return 1.0f / a; }
 
 __device__ __forceinline__ double sqrt_t(double x) {
-  double r;
-  asm("rsqrt.approx.f64 %0, %1;" : "=d"(r) : "d"(x));
+  float f;
+  if (!f64_seed_as_f32(x, f)) return sqrt(x);
+  float rf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
+  const double r = f32_as_f64(rf);
   const double s0 = x * r;
   const double e = fma(-s0, r, 1.0);
   const double t = e * fma(e, 0.375, 0.5);
-  const double s = fma(s0, t, s0);
-  // sqrt(+0) = +0 (the seed is +inf there); chosen on the bit pattern
-  return __double_as_longlong(x) == 0 ? 0.0 : s;
+  return fma(s0, t, s0);
 }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 

@@ -275,7 +275,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
         for (int k = 0; k < D; ++k) {
           T f[S], lam;
           flux_dir<T, D>(q, w, k, f, lam);
-          const int b = c[k] + (p + 2) * g.trans(c, k);
+          const int b = g.trans(c, k) + ptr * c[k];
           T* Fk = F + k * (S + 1) * nbox;
 #pragma unroll
           for (int v = 0; v < S; ++v) Fk[v * nbox + b] = f[v];
@@ -294,7 +294,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
         const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
         T fl[S], lam;
         flux_dir_sel<T, D>(q, w, k, fl, lam);
-        const int b = ck + (p + 2) * r;
+        const int b = r + ptr * ck;
         T* Fk = F + k * (S + 1) * nbox;
 #pragma unroll
         for (int v = 0; v < S; ++v) Fk[v * nbox + b] = fl[v];
@@ -310,20 +310,20 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
   for (int t = tid; t < D * nface; t += NT) {
     const int k = t / nface;
     const int j = t - k * nface;
-    const int tr = j / (p + 1);
-    const int b = j - tr * (p + 1);
+    const int b = j / ptr;
+    const int tr = j - b * ptr;
     const int cl = g.cell_kt(k, b, tr);
     const int cr = cl + g.stride(k);
     const T* Fk = F + k * (S + 1) * nbox;
-    const int bl = b + (p + 2) * tr;
-    const T am = max_by_bits(Fk[S * nbox + bl], Fk[S * nbox + bl + 1]);
+    const int bl = tr + ptr * b;  // box index of the left cell; right: bl + ptr
+    const T am = max_by_bits(Fk[S * nbox + bl], Fk[S * nbox + bl + ptr]);
     const unsigned long long ab = order_bits(am);
     lmax = ab > lmax ? ab : lmax;
     T* Gk = G + k * S * nface;
 #pragma unroll
     for (int v = 0; v < S; ++v) {
       const T dq = st[cr * S + v] - st[cl * S + v];
-      const T fs = Fk[v * nbox + bl] + Fk[v * nbox + bl + 1];
+      const T fs = Fk[v * nbox + bl] + Fk[v * nbox + bl + ptr];
       Gk[v * nface + j] = fma(-am, dq, fs);
     }
   }
@@ -343,11 +343,11 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
     T acc[S];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const int jm = (c[k] - 1) + (p + 1) * g.trans(c, k);
+      const int jm = g.trans(c, k) + ptr * (c[k] - 1);
       const T* Gk = G + k * S * nface;
 #pragma unroll
       for (int v = 0; v < S; ++v) {
-        const T dG = Gk[v * nface + jm + 1] - Gk[v * nface + jm];
+        const T dG = Gk[v * nface + jm + ptr] - Gk[v * nface + jm];
         acc[v] = k == 0 ? dG : acc[v] + dG;
       }
     }

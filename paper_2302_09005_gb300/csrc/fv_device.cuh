@@ -70,31 +70,44 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 }
 
 // ---------------------------------------------------------------------------
+// |x| and -x on the sign bit with integer operations: exact, and they keep
+// the scarce FP64 pipe out of sign manipulations the compiler does not fold
+// into a neighbouring instruction.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double abs_t(double x) {
+  return __hiloint2double(__double2hiint(x) & 0x7FFFFFFF, __double2loint(x));
+}
+__device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
+__device__ __forceinline__ double neg_t(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ float neg_t(float x) { return -x; }
+
+// ---------------------------------------------------------------------------
 // Reciprocal and square root, once per cell of the interior and face halo.
 //
 // FP64 is the scarce unit on GB300 (two FP64 lanes per SM), so the FP64
-// forms take a hardware seed from the special-function unit and refine it
-// with FMAs instead of the full IEEE division and square root sequences:
+// forms refine a cheap seed with FMAs instead of running the full IEEE
+// division and square root sequences:
 //   1/a     Newton-Raphson in its cubic form: with y0 ~ 1/a and
 //           e = 1 - a y0, 1/a = y0 / (1 - e) = y0 (1 + e + e^2 + ...), so
 //           y = y0 + y0 (e + e^2) leaves a relative error of order e^3;
 //   sqrt(x) with r0 ~ x^(-1/2), s0 = x r0 and e = 1 - s0 r0 = 1 - x r0^2,
 //           sqrt(x) = s0 (1 - e)^(-1/2) = s0 (1 + e/2 + 3e^2/8 + ...),
 //           truncated after the e^2 term (binomial series).
-// Both land within an ulp or two of the correctly rounded result (measured
-// by fv_selftest_math against the IEEE operations), far inside the 1e-12
-// tolerance of the update.  The FP32 path keeps the IEEE forms: it is
-// bound by memory traffic, not arithmetic.
-// ---------------------------------------------------------------------------
-//
 // The seeds come from the FP32 special-function unit, not from the f64
 // approximation instructions (which spend FP64 operations of their own): the
 // double's sign, exponent and leading 20 fraction bits are repacked as a
 // float with integer operations, the float reciprocal / reciprocal square
 // root is taken, and the result is repacked as a double.  The seed is good
-// to about 2^-20, so one cubic step leaves ~2^-60 for 1/a and the two-term
-// series ~2^-62 for sqrt.  Arguments outside the float exponent range (and
-// zero, negative, non-finite values) take the IEEE operation instead.
+// to about 2^-20, so the cubic step leaves ~2^-60 for 1/a and the two-term
+// series ~2^-62 for sqrt: within an ulp or two of the correctly rounded
+// result (measured by fv_selftest_math against the IEEE operations), far
+// inside the 1e-12 tolerance of the update.  Arguments outside the float
+// exponent range (and zero, negative, non-finite values) take the IEEE
+// operation.  The FP32 path keeps the IEEE forms: it is bound by memory
+// traffic and instruction issue, not by FP32 arithmetic.
+// ---------------------------------------------------------------------------
 
 // Double -> float carrying the double's leading 20 fraction bits (truncated);
 // false if the exponent does not fit a normal float with margin.
@@ -118,7 +131,7 @@ __device__ __forceinline__ double recip(double a) {
   float rf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
   const double y = f32_as_f64(rf);
-  const double e = fma(-a, y, 1.0);
+  const double e = fma(neg_t(a), y, 1.0);
   const double t = fma(e, e, e);
   return fma(y, t, y);
 }
@@ -131,18 +144,11 @@ __device__ __forceinline__ double sqrt_t(double x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
   const double r = f32_as_f64(rf);
   const double s0 = x * r;
-  const double e = fma(-s0, r, 1.0);
+  const double e = fma(neg_t(s0), r, 1.0);
   const double t = e * fma(e, 0.375, 0.5);
   return fma(s0, t, s0);
 }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
-
-template <typename T>
-__device__ __forceinline__ T abs_t(T x) {
-  return x < T(0) ? -x : x;
-}
-__device__ __forceinline__ double abs_t(double x) { return fabs(x); }
-__device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
 
 // ---------------------------------------------------------------------------
 // Euler physics of one cell, Eq. 2: q = (rho, j_1..j_D, E),

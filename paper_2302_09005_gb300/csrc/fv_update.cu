@@ -73,6 +73,17 @@ __host__ __device__ inline int gface_elems(int p) {
 }
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Unroll factors of the cell and face loops (two independent work items per
+// thread let the FP64 chains of one interleave with the other's latency).
+#ifndef FV_UNROLL_CELLS
+#define FV_UNROLL_CELLS 1
+#endif
+#ifndef FV_UNROLL_FACES
+#define FV_UNROLL_FACES 1
+#endif
+#define FV_STR_(x) #x
+#define FV_PRAGMA_UNROLL(n) _Pragma(FV_STR_(unroll n))
+
 constexpr int kHdrBytes = 64;  // two mbarriers + per-warp reduction slots
 static_assert(16 + 8 * (FV_NT / 32) <= kHdrBytes, "header too small");
 
@@ -242,7 +253,7 @@ __device__ __forceinline__ void flux_dir_sel(const T* q, const Prim<T, D>& w, in
 template <typename T, int D, int P, bool GATHER, bool FUSED>
 __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, int64_t i,
                                               int64_t off, const T* __restrict__ st, T* F, T* G,
-                                              T hr, unsigned long long* red,
+                                              T mhr, unsigned long long* red,
                                               unsigned long long& lam_next, Pipe& pp,
                                               const NextPatch<T>& nx) {
   constexpr int S = D + 2;
@@ -257,6 +268,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
   {
     const int nint_pad = (nint + 31) & ~31;
     const int nA = nint_pad + 2 * D * ptr;
+    FV_PRAGMA_UNROLL(FV_UNROLL_CELLS)
     for (int t = tid; t < nA; t += NT) {
       if (t < nint) {
         int c[3] = {0, 0, 0};
@@ -307,6 +319,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
 
   // ---- faces: G = f_L + f_R - a (Q_R - Q_L), once per face -------------------
   unsigned long long lmax = 0ull;
+  FV_PRAGMA_UNROLL(FV_UNROLL_FACES)
   for (int t = tid; t < D * nface; t += NT) {
     const int k = t / nface;
     const int j = t - k * nface;
@@ -322,9 +335,10 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
     T* Gk = G + k * S * nface;
 #pragma unroll
     for (int v = 0; v < S; ++v) {
-      const T dq = st[cr * S + v] - st[cl * S + v];
+      // f_L + f_R - a (Q_R - Q_L), with the sign folded into the difference
+      const T dqn = st[cl * S + v] - st[cr * S + v];
       const T fs = Fk[v * nbox + bl] + Fk[v * nbox + bl + ptr];
-      Gk[v * nface + j] = fma(-am, dq, fs);
+      Gk[v * nface + j] = fma(am, dqn, fs);
     }
   }
   __syncthreads();
@@ -353,7 +367,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
     }
     T qn[S];
 #pragma unroll
-    for (int v = 0; v < S; ++v) qn[v] = fma(-hr, acc[v], st[cid * S + v]);
+    for (int v = 0; v < S; ++v) qn[v] = fma(mhr, acc[v], st[cid * S + v]);
     T* dst = dst_base + (int64_t)cid * S;
 #pragma unroll
     for (int v = 0; v < S; ++v) dst[v] = qn[v];
@@ -434,7 +448,7 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? 3 : 4) step_kernel(Ste
   } else {
     dtv = a.dt > 0.0 ? a.dt : *a.dt_dev;
   }
-  const T hr = (T)(0.5 * (dtv / a.dx));
+  const T hr = neg_t((T)(0.5 * (dtv / a.dx)));  // -dt / (2 dx), passed as mhr
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);

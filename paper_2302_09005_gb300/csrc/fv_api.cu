@@ -119,7 +119,11 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
   int smem_optin = 0;
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+#ifdef FV_FORCE_SINGLE_STAGE
+  h->nstage = 1;
+#else
   h->nstage = 2;
+#endif
   if (e == cudaSuccess &&
       fv::update_smem_bytes(d, h->prec, h->max_patch_size, 2) > (size_t)smem_optin)
     h->nstage = 1;

@@ -84,8 +84,13 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 #define FV_STR_(x) #x
 #define FV_PRAGMA_UNROLL(n) _Pragma(FV_STR_(unroll n))
 
-constexpr int kHdrBytes = 64;  // two mbarriers + per-warp reduction slots
-static_assert(16 + 8 * (FV_NT / 32) <= kHdrBytes, "header too small");
+// Shared-memory header: two mbarriers (16 B), per-warp reduction slots, and
+// the face sources of the two stages (2 x 6 x 16 B).
+constexpr int kRedOff = 16;
+constexpr int kFaceSrcOff = 64;
+constexpr int kHdrBytes = 256;
+static_assert(kRedOff + 8 * (FV_NT / 32) <= kFaceSrcOff, "header too small");
+static_assert(kFaceSrcOff + 2 * 6 * 16 <= kHdrBytes, "header too small");
 
 // Shared-memory carve-up for patches up to pmax (element counts of T).  Two
 // stages let the copy of the next patch overlap the current one; when two do
@@ -133,66 +138,110 @@ __device__ __forceinline__ void issue_stage(const StepParams<T>& a, int pj, int6
   bulk_copy_g2s(st, a.in + offj, bytes, bar);
 }
 
-// All threads: fetch the face-halo cells of patch j that do not come with its
-// bulk copy -- from the neighbours (time-step mode) or the patch's own halo
-// (d = 1, whose +x halo cell may sit in the uncopied tail).  Issued as
-// cp.async element copies; a wall's negated normal momentum is written with a
-// plain load and store.
+// Where the face-halo cells of one face come from: a patch (element offset),
+// the layer along the face normal in that patch, and whether the normal
+// momentum is negated (wall).
+struct FaceSrc {
+  long long off;
+  int ck;
+  int neg;
+};
+
+// Threads 0 .. 2d-1: resolve the sources of the 2d faces of patch j once (the
+// neighbour table and the neighbour's metadata are read and checked here, not
+// per halo element).  Time-step mode follows the rules of fv_halo_fill;
+// update mode with d = 1 re-reads the patch's own halo cells.
 template <typename T, int D, bool GATHER>
-__device__ __forceinline__ void gather_halo(const StepParams<T>& a, int64_t j, int pj,
-                                            int64_t offj, T* st) {
+__device__ __forceinline__ void face_sources(const StepParams<T>& a, int64_t j, int pj,
+                                             int64_t offj, FaceSrc* fs) {
   if constexpr (!GATHER && D != 1) return;
-  constexpr int S = D + 2;
   constexpr int VEC = 16 / sizeof(T);
-  const Geom<D, 0> g(pj);
-  const int ptr = g.ptrans();
-  const int ntot = 2 * D * ptr * S;
-  const T* own = a.in + offj;
-  for (int e = threadIdx.x; e < ntot; e += FV_NT) {
-    const int hc = e / S;
-    const int v = e - hc * S;
-    const int f = hc / ptr;
-    const int r = hc - f * ptr;
-    const int k = f >> 1, side = f & 1;
-    const int ck = side ? pj + 1 : 0;  // halo layer along k
-    int ck_src = ck;                   // d = 1 update mode: the own halo cell
-    const T* src_patch = own;
-    bool neg = false;
-    if constexpr (GATHER) {
-      const int32_t nb = a.nbr[j * 2 * D + f];
-      bool outflow = true;
-      if (nb >= 0) {
-        bool ok = nb < a.n;
-        int64_t onb = 0;
-        if (ok) {
-          onb = a.off[nb];
-          ok = a.sizes[nb] == pj && onb >= 0 && (onb % VEC) == 0 &&
-               (a.n_elems <= 0 || onb + (int64_t)stage_elems<D>(pj) <= a.n_elems);
-        }
-        if (ok) {
-          src_patch = a.in + onb;
-          ck_src = side ? 1 : pj;  // the neighbour's interior layer next to the face
-          outflow = false;
-        } else {
-          atomicOr(a.status, ST_BAD_PATCH);
-        }
-      } else if (nb == -2) {
-        neg = (v == 1 + k);
-      } else if (nb != -1) {
+  const int f = threadIdx.x;
+  if (f >= 2 * D) return;
+  const int side = f & 1;
+  FaceSrc r;
+  r.off = offj;
+  r.neg = 0;
+  if constexpr (!GATHER) {
+    r.ck = side ? pj + 1 : 0;  // the own halo layer
+  } else {
+    r.ck = side ? pj : 1;  // outflow: the own interior layer next to the face
+    const int32_t nb = a.nbr[j * 2 * D + f];
+    if (nb >= 0) {
+      bool ok = nb < a.n;
+      int64_t onb = 0;
+      if (ok) {
+        onb = a.off[nb];
+        ok = a.sizes[nb] == pj && onb >= 0 && (onb % VEC) == 0 &&
+             (a.n_elems <= 0 || onb + (int64_t)stage_elems<D>(pj) <= a.n_elems);
+      }
+      if (ok) {
+        r.off = onb;
+        r.ck = side ? 1 : pj;  // the neighbour's interior layer next to the face
+      } else {
         atomicOr(a.status, ST_BAD_PATCH);
       }
-      if (outflow) ck_src = side ? pj : 1;  // the own interior layer next to the face
+    } else if (nb == -2) {
+      r.neg = 1;  // wall: mirror of the own interior layer
+    } else if (nb != -1) {
+      atomicOr(a.status, ST_BAD_PATCH);
     }
-    const int cd = g.cell_kt(k, ck, r);
-    const int csrc = g.cell_kt(k, ck_src, r);
-    T* dst = st + cd * S + v;
-    const T* src = src_patch + (int64_t)csrc * S + v;
-    if (neg)
-      *dst = -__ldg(src);
-    else
-      cp_async_elem(dst, src);
+  }
+  fs[f] = r;
+}
+
+// All threads: fetch the face-halo cells of a patch that do not come with its
+// bulk copy, from the sources resolved by face_sources, as cp.async element
+// copies (a wall's negated normal momentum with a plain load and store).
+template <typename T, int D, int P, bool GATHER>
+__device__ __forceinline__ void gather_halo(const StepParams<T>& a, int pj, T* st,
+                                            const FaceSrc* fs) {
+  if constexpr (!GATHER && D != 1) return;
+  constexpr int S = D + 2;
+  const Geom<D, P> g(pj);
+  const int p = g.p;
+  const int ptr = g.ptrans();
+  for (int hc = threadIdx.x; hc < 2 * D * ptr; hc += FV_NT) {
+    const int f = hc / ptr;
+    const int r = hc - f * ptr;
+    const int k = f >> 1;
+    const FaceSrc m = fs[f];
+    const int cd = g.cell_kt(k, (f & 1) ? p + 1 : 0, r);
+    const int cs = g.cell_kt(k, m.ck, r);
+    T* dst = st + cd * S;
+    const T* src = a.in + m.off + (int64_t)cs * S;
+#pragma unroll
+    for (int v = 0; v < S; ++v) {
+      if (m.neg && v == 1 + k)
+        dst[v] = neg_t(__ldg(src + v));
+      else
+        cp_async_elem(dst + v, src + v);
+    }
   }
   cp_async_commit();
+}
+
+template <typename T, int D, bool GATHER>
+__device__ __forceinline__ void gather_dispatch(const StepParams<T>& a, int pj, T* st,
+                                                const FaceSrc* fs) {
+  if constexpr (!GATHER && D != 1) return;
+  if constexpr (D == 3) {
+    switch (pj) {
+      case 3: gather_halo<T, D, 3, GATHER>(a, pj, st, fs); return;
+      case 5: gather_halo<T, D, 5, GATHER>(a, pj, st, fs); return;
+      case 7: gather_halo<T, D, 7, GATHER>(a, pj, st, fs); return;
+      default: gather_halo<T, D, 0, GATHER>(a, pj, st, fs); return;
+    }
+  } else if constexpr (D == 2) {
+    switch (pj) {
+      case 3: gather_halo<T, D, 3, GATHER>(a, pj, st, fs); return;
+      case 5: gather_halo<T, D, 5, GATHER>(a, pj, st, fs); return;
+      case 8: gather_halo<T, D, 8, GATHER>(a, pj, st, fs); return;
+      default: gather_halo<T, D, 0, GATHER>(a, pj, st, fs); return;
+    }
+  } else {
+    gather_halo<T, D, 0, GATHER>(a, pj, st, fs);
+  }
 }
 
 // State of the copy pipeline of one CTA.
@@ -209,6 +258,7 @@ struct NextPatch {
   int p;
   int64_t off;
   T* st;
+  FaceSrc* fs;
   int slot;
 };
 
@@ -227,7 +277,7 @@ __device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
     pp.timeout = true;
     return;
   }
-  gather_halo<T, D, GATHER>(a, nx.j, nx.p, nx.off, nx.st);
+  gather_dispatch<T, D, GATHER>(a, nx.p, nx.st, nx.fs);
 }
 
 // ---------------------------------------------------------------------------
@@ -425,12 +475,22 @@ __device__ __forceinline__ void patch_dispatch(const StepParams<T>& a, int p, in
 #undef FV_PC
 }
 
+// Resident CTAs per SM the register allocation is sized for.
+#ifndef FV_MINBLOCKS_FP64
+#define FV_MINBLOCKS_FP64 3
+#endif
+#ifndef FV_MINBLOCKS_FP32
+#define FV_MINBLOCKS_FP32 4
+#endif
+
 template <typename T, int D, bool GATHER, bool FUSED>
-__global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? 3 : 4) step_kernel(StepParams<T> a) {
+__global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV_MINBLOCKS_FP32)
+    step_kernel(StepParams<T> a) {
   constexpr int VEC = 16 / sizeof(T);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  unsigned long long* red = reinterpret_cast<unsigned long long*>(smem_raw + 16);
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(smem_raw + kRedOff);
+  FaceSrc* fsrc = reinterpret_cast<FaceSrc*>(smem_raw + kFaceSrcOff);  // [stage][face]
   const Carve<D> cv(a.pmax, VEC, a.nstage);
   const bool single = a.nstage == 1;
   T* stage[2];
@@ -467,13 +527,15 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? 3 : 4) step_kernel(Ste
   while (cur < a.n && !patch_ok<T, D>(a, cur, pc, oc)) cur += gridDim.x;
   int s = 0;
   if (cur < a.n) {
+    face_sources<T, D, GATHER>(a, cur, pc, oc, fsrc);
     if (tid == 0) issue_stage<T, D>(a, pc, oc, stage[0], &bar[0]);
     pp.pending = 1u;
+    __syncthreads();  // face sources visible
     const bool ok = mbar_wait_bounded(&bar[0], 0u, kWaitLimit);
     if (ok) {
       pp.parity ^= 1u;
       pp.pending = 0u;
-      gather_halo<T, D, GATHER>(a, cur, pc, oc, stage[0]);
+      gather_dispatch<T, D, GATHER>(a, pc, stage[0], fsrc);
     } else {
       pp.timeout = true;
     }
@@ -487,6 +549,9 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? 3 : 4) step_kernel(Ste
     while (nx.j < a.n && !patch_ok<T, D>(a, nx.j, nx.p, nx.off)) nx.j += gridDim.x;
     nx.slot = single ? 0 : s ^ 1;
     nx.st = stage[nx.slot];
+    nx.fs = fsrc + 6 * nx.slot;
+    // visible to all threads after the barrier that ends the cell phase
+    if (nx.j < a.n) face_sources<T, D, GATHER>(a, nx.j, nx.p, nx.off, nx.fs);
     NextPatch<T> nx_mid = nx;  // what the mid-patch hook waits for and gathers
     if (single) {
       nx_mid.j = a.n;  // the one stage is busy until this patch is done

@@ -302,6 +302,9 @@ def run_ours(args, ws, rank, local):
     if prec == "f64" and not args.no_variants:
         variants["fp32"] = fp32_variant(args, b, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx,
                                         cfl, stream)
+        del h_out
+        variants["batching_uneven_fp64"] = batching_variant(args, "f64")
+        variants["batching_uneven_fp32"] = batching_variant(args, "f32")
 
     peaks, peak_src = _peaks()
     if prec == "f64":
@@ -358,6 +361,70 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def batching_variant(args, prec: str, n: int = 200000, steps_per_graph: int = 20,
+                     replays: int = 3):
+    """Uneven patch sizes (50% 3^3, 30% 5^3, 20% 7^3, shuffled; self-periodic
+    halos): plan + autotune of the schedule, then CUDA graphs of
+    `steps_per_graph` fused time steps (plus the halo fill and CFL reduce that
+    seed the first step) replayed; cell-updates/s over the replays."""
+    import torch
+    from paper_2302_09005_gb300 import fv, inputs
+    d = 3
+    sizes = inputs.uneven_sizes(n, seed=0)
+    dtype = np.float64 if prec == "f64" else np.float32
+    q, off, sz = inputs.random_batch(n, sizes, d, seed=0, dtype=dtype)
+    nbr = inputs.self_periodic_neighbours(n, d)
+    cells = int(np.sum(sizes.astype(np.int64) ** 3))
+    stream = torch.cuda.Stream()
+    b = fv.Batch(d, precision=fv.FV_FP64 if prec == "f64" else fv.FV_FP32, max_patch_size=7,
+                 stream=stream)
+    x = torch.from_numpy(q).cuda()
+    y = x.clone()
+    toff, tsz, tnbr = (torch.from_numpy(a).cuda() for a in (off, sz, nbr))
+    dx, cfl = 1.0 / 64, 0.4
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        b.halo_fill(x, toff, tsz, tnbr)
+        b.max_eigenvalue(x, toff, tsz, cfl, dx)
+    chosen, ms_sched = fv.fv_batch_autotune(b.h, x, y, toff, tsz, tnbr, n, dx, cfl)
+    x0 = x.clone()
+    with torch.cuda.stream(stream):  # capture + first run
+        b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps_per_graph, use_graph=True)
+    stream.synchronize()
+    e0, e1 = _events(1)[0]
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(replays):
+            b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps_per_graph, use_graph=True)
+        e1.record(stream)
+    stream.synchronize()
+    ok = b.status() == fv.FV_OK
+    ms = e0.elapsed_time(e1) / replays
+    # end to end: state host -> device, one graph replay, state device -> host
+    hq = torch.from_numpy(q).pin_memory()
+    hout = torch.empty_like(hq).pin_memory()
+    e2, e3 = _events(1)[0]
+    with torch.cuda.stream(stream):
+        e2.record(stream)
+        x.copy_(hq, non_blocking=True)
+        b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps_per_graph, use_graph=True)
+        hout.copy_(x if steps_per_graph % 2 == 0 else y, non_blocking=True)
+        e3.record(stream)
+    stream.synchronize()
+    ems = e2.elapsed_time(e3)
+    b.close()
+    del x0
+    names = ["stride (persistent, index order)", "lpt (persistent, largest first)",
+             "classes (one launch per size)"]
+    return {"value": steps_per_graph * cells / (ms / 1e3), "unit": UNIT,
+            "ms_per_graph": ms, "steps_per_graph": steps_per_graph, "status_ok": ok,
+            "n_patches": n, "cells_per_step": cells, "dtype": prec,
+            "schedule_chosen": names[chosen],
+            "ms_per_step_by_schedule": dict(zip(names, ms_sched)),
+            "e2e": {"value": steps_per_graph * cells / (ems / 1e3), "unit": UNIT,
+                    "h2d_bytes": q.nbytes, "d2h_bytes": q.nbytes}}
 
 
 def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, stream):

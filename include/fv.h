@@ -209,6 +209,47 @@ fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* patch_off
                        double dx, double cfl, int n_steps, int use_graph);
 
 /*
+ * Scheduling of batches with uneven patch sizes (the batched kernel of
+ * Sec. 3 takes N patches of any sizes in one invocation).
+ *   FV_SCHED_STRIDE   one persistent launch; CTA b takes patches b, b+G, ...
+ *                     in index order; shared memory sized for the largest p.
+ *                     The default, and the only one without a plan.
+ *   FV_SCHED_LPT      one persistent launch over the patches sorted by size,
+ *                     largest first (longest-processing-time-first order).
+ *   FV_SCHED_CLASSES  one launch per patch size, each with the shared memory,
+ *                     pipeline depth and occupancy of its own size.
+ * All three give bitwise identical results.
+ */
+typedef enum { FV_SCHED_STRIDE = 0, FV_SCHED_LPT = 1, FV_SCHED_CLASSES = 2 } fv_schedule;
+
+/*
+ * fv_batch_plan -- sorts the patches of a batch by size on the device
+ * (counting sort; patch_sizes: device int32[n_patches]) for the LPT and
+ * CLASSES schedules, and keeps the plan in the handle.  Synchronises the
+ * handle's stream (call it outside stream capture).  A later update or time
+ * step uses the plan when it is given the same patch_sizes pointer and
+ * n_patches; the caller re-plans if the sizes change.
+ */
+fv_status fv_batch_plan(fv_batch* h, const int32_t* patch_sizes, int64_t n_patches);
+
+/* Selects the schedule of later updates and time steps. */
+fv_status fv_batch_set_schedule(fv_batch* h, fv_schedule schedule);
+
+/*
+ * fv_batch_autotune -- times the three schedules on the caller's batch (one
+ * warm-up and three timed fv_time_step calls each, or fv_patch_update_batch
+ * calls with dt = cfl * dx when neighbours is NULL), keeps the fastest in
+ * the handle and returns it in *chosen (nullable); ms_per_schedule (host
+ * double[3], nullable) receives the average milliseconds of each.
+ * Plans the batch first if needed.  scratch_out is overwritten; the
+ * handle's wave speed and time step are restored afterwards.  Synchronises.
+ */
+fv_status fv_batch_autotune(fv_batch* h, const void* in_with_halo, void* scratch_out,
+                            const int64_t* patch_offsets, const int32_t* patch_sizes,
+                            const int32_t* neighbours, int64_t n_patches, double dx, double cfl,
+                            fv_schedule* chosen, double* ms_per_schedule);
+
+/*
  * fv_conserved_totals -- FP64 sums over all interior cells of every unknown
  * (mass, momentum, energy), for conservation checks.  Fixed-order two-stage
  * reduction (per patch, then per block, then one block), so the result is

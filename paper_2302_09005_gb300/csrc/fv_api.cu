@@ -119,6 +119,7 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
   int smem_optin = 0;
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  h->smem_optin = smem_optin;
 #ifdef FV_FORCE_SINGLE_STAGE
   h->nstage = 1;
 #else
@@ -163,6 +164,7 @@ fv_status fv_batch_destroy(fv_batch* h) {
   if (!h) return FV_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   graph_cache_clear(h);
+  fv::plan_free(h);
   cudaError_t e2 = cudaFree(h->ws);
   delete h;
   return (e == cudaSuccess && e2 == cudaSuccess) ? FV_OK : FV_ERR_CUDA;
@@ -212,7 +214,7 @@ fv_status fv_patch_update_batch_ex(fv_batch* h, const void* in, void* out, const
   l.lam_patch = ex ? ex->lambda_patch : nullptr;
   l.status = h->d_status;
   l.fused = false;
-  cudaError_t e = fv::launch_update(h, l, patch_grid(h, n, h->update_blocks_per_sm));
+  cudaError_t e = fv::launch_scheduled(h, l);
   if (e != cudaSuccess) return cuda_err(h, e, "update kernel");
   return FV_OK;
 }
@@ -335,7 +337,7 @@ fv_status fv_time_step(fv_batch* h, const void* in, void* out, const int64_t* of
   l.lam_patch = lambda_patch;
   l.status = h->d_status;
   l.fused = true;
-  e = fv::launch_update(h, l, patch_grid(h, n, h->step_blocks_per_sm));
+  e = fv::launch_scheduled(h, l);
   if (e != cudaSuccess) return cuda_err(h, e, "time step kernel");
   h->lam_cur = nxt;
   return FV_OK;

@@ -30,7 +30,17 @@ struct fv_batch {
   double* d_sum_partials = nullptr;          // FV_MAX_RED_BLOCKS * 8 slots
   int update_blocks_per_sm = 0;              // occupancy cache, update mode
   int step_blocks_per_sm = 0;                // occupancy cache, time-step mode
-  void* graph_cache = nullptr;               // captured multi-step graphs (fv_graph.cu)
+  void* graph_cache = nullptr;               // captured multi-step graphs
+  // schedule (fv_sched.cu): processing order sorted by size, size classes
+  int sched = 0;                             // fv_schedule
+  int32_t* d_order = nullptr;                // device int32[plan_cap]
+  int64_t plan_cap = 0, plan_n = -1;
+  const int32_t* plan_sizes = nullptr;       // the sizes array the plan was built from
+  int ncls = 0;
+  int cls_p[64] = {0};
+  int64_t cls_begin[64] = {0}, cls_end[64] = {0};
+  int occ_cache[2][64] = {{0}};              // CTAs per SM by (time-step mode, p)
+  int smem_optin = 0;                        // opt-in shared memory per CTA
   char last_error[512] = {0};
 };
 
@@ -41,7 +51,9 @@ struct UpdateLaunch {
   void* out = nullptr;
   const int64_t* off = nullptr;
   const int32_t* sizes = nullptr;
-  const int32_t* nbr = nullptr;  // time-step mode
+  const int32_t* nbr = nullptr;    // time-step mode
+  const int32_t* order = nullptr;  // processing order, or null for 0..n-1
+  int64_t i_begin = 0, i_end = -1;  // positions to run (-1: n)
   int64_t n = 0;
   int64_t n_elems = 0;
   int pmax = 0;
@@ -54,12 +66,19 @@ struct UpdateLaunch {
   double* lam_patch = nullptr;
   unsigned int* status = nullptr;
   bool fused = false;  // time-step mode: gather halos, dt from lam_in, reduce lam_next
+  int nstage = 0;      // shared-memory stages (0: the handle's)
 };
 
 // Shared memory bytes of the update kernel for patches up to pmax.
 size_t update_smem_bytes(int d, fv_precision prec, int pmax, int nstage);
 cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& a, int grid);
 cudaError_t update_occupancy(const fv_batch* h, bool fused, int* blocks_per_sm);
+cudaError_t step_occupancy(const fv_batch* h, bool fused, int pmax, int nstage,
+                           int* blocks_per_sm);
+// Launches the update / time-step kernel(s) under the handle's schedule.
+cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l);
+// Frees the schedule plan of a handle.
+void plan_free(fv_batch* h);
 
 struct EigLaunch {
   const void* q;

@@ -1,0 +1,242 @@
+// fv_sched.cu -- scheduling of the patch kernels over a batch of uneven
+// patch sizes (the batched kernel of Sec. 3 with N patches of any size per
+// launch):
+//   FV_SCHED_STRIDE   one persistent launch, CTA b takes patches b, b+G, ...
+//                     in index order; shared memory sized for the largest p;
+//   FV_SCHED_LPT      one persistent launch over the patches sorted by size,
+//                     largest first (longest-processing-time-first list
+//                     scheduling: the big patches start early, the small ones
+//                     fill the tail);
+//   FV_SCHED_CLASSES  one launch per patch size, each with the shared memory,
+//                     pipeline depth and occupancy of its own size.
+// fv_batch_plan sorts the patches on the device (counting sort by size);
+// fv_batch_autotune times the three on the caller's batch and keeps the
+// fastest.
+#include <stdio.h>
+
+#include "fv_device.cuh"
+#include "fv_internal.h"
+
+namespace fv {
+
+// bucket of a patch size: 1..pmax, or pmax+1 for sizes the kernels reject
+__device__ __forceinline__ int size_bucket(int p, int pmax) {
+  return (p >= 1 && p <= pmax) ? p : pmax + 1;
+}
+
+__global__ void plan_hist_kernel(const int32_t* __restrict__ sizes, int64_t n, int pmax,
+                                 unsigned long long* counts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&counts[size_bucket(sizes[i], pmax)], 1ull);
+}
+
+__global__ void plan_scatter_kernel(const int32_t* __restrict__ sizes, int64_t n, int pmax,
+                                    unsigned long long* cursor, int32_t* order) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long pos = atomicAdd(&cursor[size_bucket(sizes[i], pmax)], 1ull);
+    order[pos] = (int32_t)i;
+  }
+}
+
+void plan_free(fv_batch* h) {
+  if (h->d_order) cudaFree(h->d_order);
+  h->d_order = nullptr;
+  h->plan_cap = 0;
+  h->plan_n = -1;
+  h->plan_sizes = nullptr;
+  h->ncls = 0;
+}
+
+static int stages_for(const fv_batch* h, int p) {
+  return update_smem_bytes(h->d, h->prec, p, 2) <= (size_t)h->smem_optin ? 2 : 1;
+}
+
+static int grid_for(const fv_batch* h, int64_t count, int bps) {
+  int64_t g = (int64_t)h->num_sms * (bps > 0 ? bps : 1);
+  if (g > count) g = count;
+  if (g > FV_MAX_RED_BLOCKS) g = FV_MAX_RED_BLOCKS;
+  return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
+  const bool plan_ok = h->d_order != nullptr && h->plan_n == l.n && h->plan_sizes == l.sizes;
+  const int f = l.fused ? 1 : 0;
+  if (h->sched == FV_SCHED_CLASSES && plan_ok) {
+    for (int c = 0; c < h->ncls; ++c) {
+      const int64_t cnt = h->cls_end[c] - h->cls_begin[c];
+      if (cnt <= 0) continue;
+      UpdateLaunch lc = l;
+      lc.order = h->d_order;
+      lc.i_begin = h->cls_begin[c];
+      lc.i_end = h->cls_end[c];
+      lc.pmax = h->cls_p[c];
+      lc.nstage = stages_for(h, lc.pmax);
+      int& bps = h->occ_cache[f][lc.pmax < 64 ? lc.pmax : 63];
+      if (bps == 0) {
+        cudaError_t e = step_occupancy(h, l.fused, lc.pmax, lc.nstage, &bps);
+        if (e != cudaSuccess) return e;
+      }
+      cudaError_t e = launch_update(h, lc, grid_for(h, cnt, bps));
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  const int bps = l.fused ? h->step_blocks_per_sm : h->update_blocks_per_sm;
+  if (h->sched == FV_SCHED_LPT && plan_ok) {
+    l.order = h->d_order;
+    l.i_begin = 0;
+    l.i_end = l.n;
+  }
+  return launch_update(h, l, grid_for(h, l.n, bps));
+}
+
+}  // namespace fv
+
+namespace {
+fv_status sched_err(fv_batch* h, fv_status st, const char* msg) {
+  snprintf(h->last_error, sizeof(h->last_error), "%s", msg);
+  return st;
+}
+}  // namespace
+
+extern "C" {
+
+fv_status fv_batch_plan(fv_batch* h, const int32_t* sizes, int64_t n) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  h->last_error[0] = 0;
+  if (n < 0 || (n > 0 && !sizes)) return sched_err(h, FV_ERR_INVALID_ARG, "bad sizes / n");
+  if (n > 0x7FFFFFFFll) return sched_err(h, FV_ERR_UNSUPPORTED, "more than 2^31-1 patches");
+  cudaError_t e = cudaSuccess;
+  if (n > h->plan_cap) {
+    if (h->d_order) cudaFree(h->d_order);
+    h->d_order = nullptr;
+    h->plan_cap = 0;
+    e = cudaMalloc(&h->d_order, sizeof(int32_t) * (size_t)n);
+    if (e != cudaSuccess) return sched_err(h, FV_ERR_CUDA, "plan: out of device memory");
+    h->plan_cap = n;
+  }
+  const int pmax = h->max_patch_size;
+  const int nb = pmax + 2;  // buckets 0..pmax+1 (0 unused)
+  unsigned long long* counts = h->d_partials;  // workspace slots, stream ordered
+  unsigned long long host[80] = {0};
+  if (nb > 80) return sched_err(h, FV_ERR_UNSUPPORTED, "max_patch_size too large to plan");
+  e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * nb, h->stream);
+  const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  if (e == cudaSuccess && n > 0) {
+    fv::plan_hist_kernel<<<grid, 256, 0, h->stream>>>(sizes, n, pmax, counts);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host, counts, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
+  // positions: largest size first, rejected sizes last
+  unsigned long long start[80] = {0};
+  unsigned long long pos = 0;
+  h->ncls = 0;
+  for (int p = pmax; p >= 1; --p) {
+    start[p] = pos;
+    if (host[p] > 0) {
+      h->cls_p[h->ncls] = p;
+      h->cls_begin[h->ncls] = (int64_t)pos;
+      h->cls_end[h->ncls] = (int64_t)(pos + host[p]);
+      ++h->ncls;
+    }
+    pos += host[p];
+  }
+  start[pmax + 1] = pos;
+  if (host[pmax + 1] > 0) {  // rejected sizes: the kernels flag and skip them
+    h->cls_p[h->ncls] = pmax;
+    h->cls_begin[h->ncls] = (int64_t)pos;
+    h->cls_end[h->ncls] = (int64_t)(pos + host[pmax + 1]);
+    ++h->ncls;
+  }
+  e = cudaMemcpyAsync(counts, start, sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice,
+                      h->stream);
+  if (e == cudaSuccess && n > 0) {
+    fv::plan_scatter_kernel<<<grid, 256, 0, h->stream>>>(sizes, n, pmax, counts, h->d_order);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // `start` lives on this stack
+  if (e != cudaSuccess) return sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
+  h->plan_n = n;
+  h->plan_sizes = sizes;
+  return FV_OK;
+}
+
+fv_status fv_batch_set_schedule(fv_batch* h, fv_schedule s) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  if (s != FV_SCHED_STRIDE && s != FV_SCHED_LPT && s != FV_SCHED_CLASSES)
+    return FV_ERR_INVALID_ARG;
+  h->sched = (int)s;
+  return FV_OK;
+}
+
+fv_status fv_batch_autotune(fv_batch* h, const void* in, void* scratch_out, const int64_t* off,
+                            const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
+                            double cfl, fv_schedule* chosen, double* ms_per_schedule) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  if (n <= 0) return sched_err(h, FV_ERR_INVALID_ARG, "empty batch");
+  if (!(dx > 0.0) || !(cfl > 0.0)) return sched_err(h, FV_ERR_INVALID_ARG, "dx, cfl > 0");
+  if (h->plan_n != n || h->plan_sizes != sizes) {
+    fv_status st = fv_batch_plan(h, sizes, n);
+    if (st != FV_OK) return st;
+  }
+  // keep the caller's wave speed and time step: the trial steps overwrite them
+  unsigned long long* backup = h->d_lam + 2;  // workspace slots 2, 3
+  const int lam0 = h->lam_cur;
+  cudaError_t e = cudaMemcpyAsync(backup, &h->d_lam[lam0], 8, cudaMemcpyDeviceToDevice,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(backup + 1, h->d_dt, 8, cudaMemcpyDeviceToDevice, h->stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
+  const int saved = h->sched;
+  double best = 1e300;
+  int best_s = saved;
+  fv_status st = FV_OK;
+  for (int s = 0; s < 3 && st == FV_OK; ++s) {
+    h->sched = s;
+    float ms_total = 0.f;
+    for (int rep = 0; rep < 4 && st == FV_OK; ++rep) {  // one warm-up, three timed
+      h->lam_cur = lam0;
+      e = cudaMemcpyAsync(&h->d_lam[lam0], backup, 8, cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+      if (e != cudaSuccess) {
+        st = sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
+        break;
+      }
+      st = nbr ? fv_time_step(h, in, scratch_out, off, sizes, nbr, n, dx, cfl, nullptr)
+               : fv_patch_update_batch(h, in, scratch_out, off, sizes, n, h->d, h->s, dx,
+                                       cfl * dx);
+      e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess && st == FV_OK) st = sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
+      if (rep > 0) ms_total += ms;
+    }
+    const double avg = ms_total / 3.0;
+    if (ms_per_schedule) ms_per_schedule[s] = avg;
+    if (st == FV_OK && avg < best) {
+      best = avg;
+      best_s = s;
+    }
+  }
+  h->sched = st == FV_OK ? best_s : saved;
+  h->lam_cur = lam0;
+  cudaMemcpyAsync(&h->d_lam[lam0], backup, 8, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(h->d_dt, backup + 1, 8, cudaMemcpyDeviceToDevice, h->stream);
+  cudaStreamSynchronize(h->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (chosen) *chosen = (fv_schedule)h->sched;
+  return st;
+}
+
+}  // extern "C"

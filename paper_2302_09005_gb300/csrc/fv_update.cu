@@ -41,7 +41,9 @@ struct StepParams {
   const int64_t* __restrict__ off;
   const int32_t* __restrict__ sizes;
   const int32_t* __restrict__ nbr;  // time-step mode
-  int64_t n;
+  const int32_t* __restrict__ order;  // processing order (patch indices), or null
+  int64_t i_begin, i_end;             // positions of the sequence this launch runs
+  int64_t n;                          // patches in the batch
   int64_t n_elems;
   int pmax;
   int nstage;  // shared-memory stages: 2 (copy overlaps compute) or 1
@@ -254,7 +256,8 @@ struct Pipe {
 
 template <typename T>
 struct NextPatch {
-  int64_t j;  // >= n: none
+  int64_t j;    // position in the processing sequence; >= i_end: none
+  int64_t pid;  // patch index
   int p;
   int64_t off;
   T* st;
@@ -267,7 +270,7 @@ struct NextPatch {
 template <typename T, int D, bool GATHER>
 __device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
                                          const NextPatch<T>& nx) {
-  if (nx.j >= a.n) return;
+  if (nx.j >= a.i_end) return;
   const bool ok = mbar_wait_bounded(&pp.bar[nx.slot], (pp.parity >> nx.slot) & 1u, kWaitLimit);
   if (ok) {
     pp.parity ^= 1u << nx.slot;
@@ -520,14 +523,20 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV
   Pipe pp{bar, 0u, 0u, false};
   unsigned long long lam_next = 0ull;
 
+  // Processing sequence: positions [i_begin, i_end), patch order[pos] (or
+  // pos itself), CTA b takes positions i_begin + b, + gridDim.x, ...
+  auto pid_of = [&](int64_t pos) -> int64_t {
+    return a.order != nullptr ? (int64_t)a.order[pos] : pos;
+  };
   // first valid patch of this CTA, staged before the loop
-  int64_t cur = blockIdx.x;
+  int64_t cur = a.i_begin + blockIdx.x;
+  int64_t pidc = 0;
   int pc = 0;
   int64_t oc = 0;
-  while (cur < a.n && !patch_ok<T, D>(a, cur, pc, oc)) cur += gridDim.x;
+  while (cur < a.i_end && !patch_ok<T, D>(a, pidc = pid_of(cur), pc, oc)) cur += gridDim.x;
   int s = 0;
-  if (cur < a.n) {
-    face_sources<T, D, GATHER>(a, cur, pc, oc, fsrc);
+  if (cur < a.i_end) {
+    face_sources<T, D, GATHER>(a, pidc, pc, oc, fsrc);
     if (tid == 0) issue_stage<T, D>(a, pc, oc, stage[0], &bar[0]);
     pp.pending = 1u;
     __syncthreads();  // face sources visible
@@ -541,29 +550,31 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV
     }
     cp_async_wait_all();
   }
-  if (__syncthreads_or(pp.timeout)) cur = a.n;
+  if (__syncthreads_or(pp.timeout)) cur = a.i_end;
 
-  while (cur < a.n) {
+  while (cur < a.i_end) {
     NextPatch<T> nx;
     nx.j = cur + gridDim.x;
-    while (nx.j < a.n && !patch_ok<T, D>(a, nx.j, nx.p, nx.off)) nx.j += gridDim.x;
+    nx.pid = 0;
+    while (nx.j < a.i_end && !patch_ok<T, D>(a, nx.pid = pid_of(nx.j), nx.p, nx.off))
+      nx.j += gridDim.x;
     nx.slot = single ? 0 : s ^ 1;
     nx.st = stage[nx.slot];
     nx.fs = fsrc + 6 * nx.slot;
     // visible to all threads after the barrier that ends the cell phase
-    if (nx.j < a.n) face_sources<T, D, GATHER>(a, nx.j, nx.p, nx.off, nx.fs);
+    if (nx.j < a.i_end) face_sources<T, D, GATHER>(a, nx.pid, nx.p, nx.off, nx.fs);
     NextPatch<T> nx_mid = nx;  // what the mid-patch hook waits for and gathers
     if (single) {
-      nx_mid.j = a.n;  // the one stage is busy until this patch is done
-    } else if (nx.j < a.n) {
+      nx_mid.j = a.i_end;  // the one stage is busy until this patch is done
+    } else if (nx.j < a.i_end) {
       if (tid == 0) issue_stage<T, D>(a, nx.p, nx.off, nx.st, &bar[nx.slot]);
       pp.pending |= 1u << nx.slot;
     }
-    patch_dispatch<T, D, GATHER, FUSED>(a, pc, cur, oc, stage[s], F, G, hr, red, lam_next, pp,
+    patch_dispatch<T, D, GATHER, FUSED>(a, pc, pidc, oc, stage[s], F, G, hr, red, lam_next, pp,
                                         nx_mid);
     cp_async_wait_all();
     if (__syncthreads_or(pp.timeout)) break;
-    if (single && nx.j < a.n) {
+    if (single && nx.j < a.i_end) {
       if (tid == 0) issue_stage<T, D>(a, nx.p, nx.off, nx.st, &bar[0]);
       pp.pending |= 1u;
       mid_hook<T, D, GATHER>(a, pp, nx);
@@ -571,6 +582,7 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV
       if (__syncthreads_or(pp.timeout)) break;
     }
     cur = nx.j;
+    pidc = nx.pid;
     pc = nx.p;
     oc = nx.off;
     if (!single) s ^= 1;
@@ -629,10 +641,13 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.off = l.off;
   a.sizes = l.sizes;
   a.nbr = l.nbr;
+  a.order = l.order;
+  a.i_begin = l.i_begin;
+  a.i_end = l.i_end >= 0 ? l.i_end : l.n;
   a.n = l.n;
   a.n_elems = l.n_elems;
   a.pmax = l.pmax;
-  a.nstage = h->nstage;
+  a.nstage = l.nstage > 0 ? l.nstage : h->nstage;
   a.gamma = (T)l.gamma;
   a.gm1 = (T)(l.gamma - 1.0);
   a.dx = l.dx;
@@ -644,7 +659,7 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.dt_slot = l.dt_slot;
   a.lam_patch = l.lam_patch;
   a.status = l.status;
-  const size_t smem = update_smem_bytes(D, h->prec, l.pmax, h->nstage);
+  const size_t smem = update_smem_bytes(D, h->prec, l.pmax, a.nstage);
   cudaError_t e = ensure_smem<T, D, GATHER, FUSED>(smem);
   if (e != cudaSuccess) return e;
   step_kernel<T, D, GATHER, FUSED><<<grid, FV_NT, smem, h->stream>>>(a);
@@ -668,8 +683,8 @@ cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& l, int grid) {
 }
 
 template <typename T, int D, bool GATHER, bool FUSED>
-static cudaError_t occupancy_t(const fv_batch* h, int* bps) {
-  const size_t smem = update_smem_bytes(D, h->prec, h->max_patch_size, h->nstage);
+static cudaError_t occupancy_t(const fv_batch* h, int pmax, int nstage, int* bps) {
+  const size_t smem = update_smem_bytes(D, h->prec, pmax, nstage);
   cudaError_t e = ensure_smem<T, D, GATHER, FUSED>(smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, step_kernel<T, D, GATHER, FUSED>,
@@ -677,18 +692,22 @@ static cudaError_t occupancy_t(const fv_batch* h, int* bps) {
 }
 
 template <typename T, bool GATHER, bool FUSED>
-static cudaError_t occ_by_d(const fv_batch* h, int* bps) {
-  if (h->d == 1) return occupancy_t<T, 1, GATHER, FUSED>(h, bps);
-  if (h->d == 2) return occupancy_t<T, 2, GATHER, FUSED>(h, bps);
-  return occupancy_t<T, 3, GATHER, FUSED>(h, bps);
+static cudaError_t occ_by_d(const fv_batch* h, int pmax, int nstage, int* bps) {
+  if (h->d == 1) return occupancy_t<T, 1, GATHER, FUSED>(h, pmax, nstage, bps);
+  if (h->d == 2) return occupancy_t<T, 2, GATHER, FUSED>(h, pmax, nstage, bps);
+  return occupancy_t<T, 3, GATHER, FUSED>(h, pmax, nstage, bps);
+}
+
+cudaError_t step_occupancy(const fv_batch* h, bool fused, int pmax, int nstage, int* bps) {
+  if (fused)
+    return h->prec == FV_FP64 ? occ_by_d<double, true, true>(h, pmax, nstage, bps)
+                              : occ_by_d<float, true, true>(h, pmax, nstage, bps);
+  return h->prec == FV_FP64 ? occ_by_d<double, false, false>(h, pmax, nstage, bps)
+                            : occ_by_d<float, false, false>(h, pmax, nstage, bps);
 }
 
 cudaError_t update_occupancy(const fv_batch* h, bool fused, int* bps) {
-  if (fused)
-    return h->prec == FV_FP64 ? occ_by_d<double, true, true>(h, bps)
-                              : occ_by_d<float, true, true>(h, bps);
-  return h->prec == FV_FP64 ? occ_by_d<double, false, false>(h, bps)
-                            : occ_by_d<float, false, false>(h, bps);
+  return step_occupancy(h, fused, h->max_patch_size, h->nstage, bps);
 }
 
 }  // namespace fv

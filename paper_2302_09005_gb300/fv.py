@@ -85,6 +85,13 @@ def _lib() -> ctypes.CDLL:
         L.fv_run_steps.restype = c_int
         L.fv_read_dt.argtypes = [vp, ctypes.POINTER(dbl)]
         L.fv_read_dt.restype = c_int
+        L.fv_batch_plan.argtypes = [vp, vp, i64]
+        L.fv_batch_plan.restype = c_int
+        L.fv_batch_set_schedule.argtypes = [vp, c_int]
+        L.fv_batch_set_schedule.restype = c_int
+        L.fv_batch_autotune.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl,
+                                        ctypes.POINTER(c_int), ctypes.POINTER(dbl)]
+        L.fv_batch_autotune.restype = c_int
         L.fv_last_error.argtypes = [vp]
         L.fv_last_error.restype = ctypes.c_char_p
         for name in ("fv_batch_create", "fv_batch_destroy", "fv_batch_set_stream",
@@ -214,6 +221,31 @@ def fv_get_dt_ptr(h) -> int:
     p = ctypes.c_void_p()
     _check(h, _lib().fv_get_dt_ptr(h, ctypes.byref(p)), "fv_get_dt_ptr")
     return p.value
+
+
+FV_SCHED_STRIDE = 0
+FV_SCHED_LPT = 1
+FV_SCHED_CLASSES = 2
+
+
+def fv_batch_plan(h, patch_sizes, n_patches: int):
+    _check(h, _lib().fv_batch_plan(h, _ptr(patch_sizes), n_patches), "fv_batch_plan")
+
+
+def fv_batch_set_schedule(h, schedule: int):
+    _check(h, _lib().fv_batch_set_schedule(h, schedule), "fv_batch_set_schedule")
+
+
+def fv_batch_autotune(h, in_with_halo, scratch_out, patch_offsets, patch_sizes, neighbours,
+                      n_patches: int, dx: float, cfl: float):
+    """Returns (chosen schedule, [ms of STRIDE, LPT, CLASSES])."""
+    chosen = ctypes.c_int()
+    ms = (ctypes.c_double * 3)()
+    st = _lib().fv_batch_autotune(h, _ptr(in_with_halo), _ptr(scratch_out), _ptr(patch_offsets),
+                                  _ptr(patch_sizes), _ptr(neighbours), n_patches, dx, cfl,
+                                  ctypes.byref(chosen), ms)
+    _check(h, st, "fv_batch_autotune")
+    return chosen.value, list(ms)
 
 
 def fv_read_dt(h) -> float:

@@ -85,9 +85,16 @@ def random_batch(n: int, p, d: int, *, seed: int = 0, halo: int = 1, dtype=np.fl
                 view[c0:c1, :ne] = random_cells(rng, (c1 - c0) * ne // s, d,
                                                 gamma).reshape(c1 - c0, ne)
         else:
-            for i in range(n):
-                ne = patch_elems(int(sizes[i]), d, s, halo)
-                q[off[i]:off[i] + ne] = random_cells(rng, ne // s, d, gamma).reshape(-1)
+            # one draw per size class, patches of a class in index order
+            for pv in np.unique(sizes):
+                sel = np.nonzero(sizes == pv)[0]
+                ne = patch_elems(int(pv), d, s, halo)
+                chunk = max(1, (1 << 22) // ne)
+                for c0 in range(0, len(sel), chunk):
+                    part = sel[c0:c0 + chunk]
+                    idx = off[part][:, None] + np.arange(ne)[None, :]
+                    q[idx] = random_cells(rng, len(part) * ne // s, d,
+                                          gamma).reshape(len(part), ne)
     return q.astype(dtype), off, sizes
 
 

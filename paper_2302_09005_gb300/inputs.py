@@ -85,16 +85,18 @@ def random_batch(n: int, p, d: int, *, seed: int = 0, halo: int = 1, dtype=np.fl
                 view[c0:c1, :ne] = random_cells(rng, (c1 - c0) * ne // s, d,
                                                 gamma).reshape(c1 - c0, ne)
         else:
-            # one draw per size class, patches of a class in index order
-            for pv in np.unique(sizes):
-                sel = np.nonzero(sizes == pv)[0]
-                ne = patch_elems(int(pv), d, s, halo)
-                chunk = max(1, (1 << 22) // ne)
-                for c0 in range(0, len(sel), chunk):
-                    part = sel[c0:c0 + chunk]
-                    idx = off[part][:, None] + np.arange(ne)[None, :]
-                    q[idx] = random_cells(rng, len(part) * ne // s, d,
-                                          gamma).reshape(len(part), ne)
+            # one draw for all cells, written over every element that is not
+            # alignment padding (patches are consecutive in the buffer)
+            lens = (sizes.astype(np.int64) + 2 * halo) ** d * s
+            padded = np.diff(np.append(off, total))
+            npad = padded - lens
+            mask = np.ones(total, dtype=bool)
+            if npad.sum():
+                ends = np.cumsum(npad)
+                pos = (np.arange(ends[-1]) - np.repeat(ends - npad, npad)
+                       + np.repeat(off + lens, npad))
+                mask[pos] = False
+            q[mask] = random_cells(rng, int(lens.sum()) // s, d, gamma).reshape(-1)
     return q.astype(dtype), off, sizes
 
 

@@ -305,6 +305,7 @@ def run_ours(args, ws, rank, local):
         del h_out
         variants["batching_uneven_fp64"] = batching_variant(args, "f64")
         variants["batching_uneven_fp32"] = batching_variant(args, "f32")
+        variants["precision_2d_4095"] = precision_variant(args)
 
     peaks, peak_src = _peaks()
     if prec == "f64":
@@ -438,6 +439,68 @@ def batching_variant(args, prec: str, n: int = 200000, steps_per_graph: int = 20
             "ms_per_step_by_schedule": dict(zip(names, ms_sched)),
             "e2e": {"value": steps_per_graph * cells / (ems / 1e3), "unit": UNIT,
                     "h2d_bytes": q.nbytes, "d2h_bytes": q.nbytes}}
+
+
+def precision_variant(args, N: int = 4095, p: int = 5, steps: int = 100):
+    """Periodic 2D Fourier-perturbed state (rho = 1 + drho, (u, v) random
+    modes 1-16, amplitude 0.1, p = 1) on N^2 cells in p x p patches, `steps`
+    fused time steps in FP64 and in FP32 (FP32 fluxes and update, FP64
+    conservation sums and dt), each as one CUDA graph: time per step, relative
+    L1 distance of FP32 to FP64, and the drift of the conserved totals."""
+    import torch
+    from paper_2302_09005_gb300 import fv, inputs
+    U = inputs.fourier_perturbation(N, seed=0)
+    q64, off, sz, grid = inputs.domain_to_patches(U, p, align_bytes=32)
+    del U
+    nbr = inputs.grid_neighbours(grid)
+    n = len(off)
+    toff, tsz, tnbr = (torch.from_numpy(a).cuda() for a in (off, sz, nbr))
+    dx, cfl = 1.0 / N, 0.4
+    stride = int(off[1] - off[0])
+    out = {}
+    finals = {}
+    for prec in ("f64", "f32"):
+        stream = torch.cuda.Stream()
+        b = fv.Batch(2, precision=fv.FV_FP64 if prec == "f64" else fv.FV_FP32,
+                     max_patch_size=p, stream=stream)
+        q = q64 if prec == "f64" else q64.astype(np.float32)
+        x0 = torch.from_numpy(q).cuda()
+        x, y = x0.clone(), x0.clone()
+        t0 = torch.zeros(4, dtype=torch.float64, device="cuda")
+        t1 = torch.zeros(4, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            b.totals(x, toff, tsz, t0)
+            b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps, use_graph=True)  # capture+run
+        stream.synchronize()
+        res = x if steps % 2 == 0 else y
+        with torch.cuda.stream(stream):
+            b.totals(res, toff, tsz, t1)
+        stream.synchronize()
+        finals[prec] = _interior_view(res, n, stride, p, 2, 4).double().clone()
+        # timing: replay the graph from the initial state
+        x.copy_(x0)
+        torch.cuda.synchronize()
+        e0, e1 = _events(1)[0]
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps, use_graph=True)
+            e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        ok = b.status() == fv.FV_OK
+        a0, a1 = t0.cpu().numpy(), t1.cpu().numpy()
+        out[prec] = {"ms_per_step": ms / steps, "value": n * p * p * steps / (ms / 1e3),
+                     "unit": UNIT, "status_ok": ok,
+                     "conserved_totals_start": a0.tolist(),
+                     "conserved_drift_rel": (np.abs(a1 - a0) / np.maximum(np.abs(a0), 1e-300)
+                                             ).tolist()}
+        b.close()
+        del x0, x, y
+    d64, d32 = finals["f64"], finals["f32"]
+    rel_l1 = ((d32 - d64).abs().reshape(-1, 4).sum(0) / d64.abs().reshape(-1, 4).sum(0)).tolist()
+    del finals, d64, d32
+    return {"domain": f"{N}x{N} periodic, {n} patches of {p}x{p}", "steps": steps, **out,
+            "fp32_rel_l1_vs_fp64_after_steps": rel_l1}
 
 
 def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, stream):

@@ -483,7 +483,7 @@ __device__ __forceinline__ void patch_dispatch(const StepParams<T>& a, int p, in
 #define FV_MINBLOCKS_FP64 3
 #endif
 #ifndef FV_MINBLOCKS_FP32
-#define FV_MINBLOCKS_FP32 4
+#define FV_MINBLOCKS_FP32 6
 #endif
 
 template <typename T, int D, bool GATHER, bool FUSED>

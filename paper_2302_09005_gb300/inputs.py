@@ -244,17 +244,20 @@ def fourier_perturbation(N: int, *, seed: int = 0, amp: float = 0.1, modes: int 
     max(|k_x|, |k_y|) in [1, modes] and random phases, scaled to max |.| = amp."""
     rng = np.random.default_rng(seed)
     x = cell_centres(N)
-    X, Y = np.meshgrid(x, x, indexing="xy")  # arrays of shape (Ny, Nx)
     fields = []
     for _ in range(3):
-        f = np.zeros((N, N))
+        f = np.zeros((N, N))  # (y, x)
         for _w in range(nwaves):
             while True:
                 kx, ky = rng.integers(-modes, modes + 1, size=2)
                 if max(abs(kx), abs(ky)) >= 1:
                     break
             phi = rng.uniform(0, 2 * np.pi)
-            f += np.sin(2 * np.pi * (kx * X + ky * Y) + phi)
+            # sin(a + b) = sin a cos b + cos a sin b, a = 2 pi kx x + phi, b = 2 pi ky y
+            a = 2 * np.pi * kx * x + phi
+            b = 2 * np.pi * ky * x
+            f += np.sin(b)[:, None] * np.cos(a)[None, :]
+            f += np.cos(b)[:, None] * np.sin(a)[None, :]
         f *= amp / np.max(np.abs(f))
         fields.append(f)
     rho = 1.0 + fields[0]

@@ -116,3 +116,47 @@ def test_run_steps_graph_equals_eager(fv, prec, n_steps):
         b.close()
     mask = fvtest.interior_mask(off, sz, d, d + 2, len(q))
     assert np.array_equal(res[0][mask], res[1][mask])
+
+
+def test_fp32_path_conserves_and_tracks_fp64(fv):
+    """Precision workload in small: a periodic 2D Fourier-perturbed state in
+    5x5 patches, 20 fused steps in FP64 and in FP32.  FP64 conserves the
+    totals to roundoff; the FP32 path (FP32 fluxes and update, FP64 sums
+    and dt) drifts by FP32 roundoff only and stays within 1e-5 (relative L1)
+    of the FP64 state."""
+    torch = fvtest.torch_cuda()
+    N, p, steps = 255, 5, 20
+    U = inputs.fourier_perturbation(N, seed=3)
+    q64, off, sz, grid = inputs.domain_to_patches(U, p, align_bytes=32)
+    nbr = inputs.grid_neighbours(grid)
+    toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
+    dx, cfl = 1.0 / N, 0.4
+    res = {}
+    for prec in (0, 1):
+        q = q64 if prec == 0 else q64.astype(np.float32)
+        b = fv.Batch(2, precision=prec, max_patch_size=p)
+        x, y = fvtest.to_dev(q), fvtest.to_dev(q)
+        t0 = torch.zeros(4, dtype=torch.float64, device="cuda")
+        t1 = torch.zeros(4, dtype=torch.float64, device="cuda")
+        b.totals(x, toff, tsz, t0)
+        b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps)
+        out = x if steps % 2 == 0 else y
+        b.totals(out, toff, tsz, t1)
+        assert b.status() == fv.FV_OK
+        res[prec] = (inputs.patches_to_domain(out.cpu().numpy(), off, p, grid, 4),
+                     t0.cpu().numpy(), t1.cpu().numpy())
+        b.close()
+    d64, a64, b64 = res[0]
+    d32, a32, b32 = res[1]
+    scale = np.abs(a64)
+    assert np.all(np.abs(b64 - a64) <= 1e-13 * np.maximum(scale, 1.0))
+    assert np.all(np.abs(b32 - a32) <= 1e-5 * np.maximum(scale, 1.0))
+    rel_l1 = np.abs(d32 - d64).sum(axis=(0, 1)) / np.abs(d64).sum(axis=(0, 1))
+    assert np.all(rel_l1 <= 1e-5), rel_l1
+    # and the FP64 run matches the oracle
+    ref = q64.copy()
+    for _ in range(steps):
+        ref, _ = oracle.step(ref, off, sz, nbr, 2, dx, cfl)
+    dref = inputs.patches_to_domain(ref, off, p, grid, 4)
+    err = np.abs(d64 - dref).max(axis=(0, 1)) / np.abs(dref).max(axis=(0, 1))
+    assert np.all(err <= 1e-11), err

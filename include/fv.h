@@ -250,6 +250,44 @@ fv_status fv_batch_autotune(fv_batch* h, const void* in_with_halo, void* scratch
                             fv_schedule* chosen, double* ms_per_schedule);
 
 /*
+ * Learned face-flux correction (the build's addition on top of Eq. 4; not in
+ * the paper).  A network of 16 -> 64 -> 64 -> 4 units with GELU activations
+ * maps the normalised 4-cell stencil Q_{i-2..i+1} normal to a face (in the
+ * face's normal frame: rho, j_n, j_t, E per cell) to a correction C that is
+ * added to the Rusanov flux of that face, once per face, so both cells see
+ * the same flux and the totals are conserved by construction.
+ * Parameters: one FP32 device vector of FV_MLP_NPARAM floats, in the order
+ * W1 (64x16, output-major), b1 (64), W2 (64x64), b2 (64), W3 (4x64), b3 (4).
+ * Normalisation: FP32 device vector of FV_MLP_NNORM floats: mu_x (16),
+ * sd_x (16), sd_y (4); x = (stencil - mu_x) / sd_x, C = y * sd_y.
+ * All products run on the tensor cores in BF16 with FP32 accumulation.
+ */
+#define FV_MLP_NPARAM 5508
+#define FV_MLP_NNORM 36
+
+typedef struct fv_mlp_trainer fv_mlp_trainer; /* opaque */
+
+/* Workspace for batches of up to max_batch samples, on cuda_stream. */
+fv_status fv_mlp_trainer_create(fv_mlp_trainer** t, int64_t max_batch, void* cuda_stream);
+fv_status fv_mlp_trainer_destroy(fv_mlp_trainer* t);
+
+/* y (device float[batch*4]) = network(x) for normalised inputs x
+ * (device float[batch*16]). */
+fv_status fv_mlp_forward(fv_mlp_trainer* t, const float* params, const float* x, int64_t batch,
+                         float* y);
+
+/* Mean squared error of network(x) against target (device float[batch*4])
+ * into *loss (device float) and its gradient into grad (device
+ * float[FV_MLP_NPARAM]); deterministic. */
+fv_status fv_mlp_grad(fv_mlp_trainer* t, const float* params, const float* x,
+                      const float* target, int64_t batch, float* grad, float* loss);
+
+/* One Adam step (lr, step >= 1 counts the steps; moments kept in the
+ * trainer) on params in place; *loss receives the batch loss before it. */
+fv_status fv_mlp_train_step(fv_mlp_trainer* t, float* params, const float* x, const float* target,
+                            int64_t batch, float lr, int step, float* loss);
+
+/*
  * fv_conserved_totals -- FP64 sums over all interior cells of every unknown
  * (mass, momentum, energy), for conservation checks.  Fixed-order two-stage
  * reduction (per patch, then per block, then one block), so the result is

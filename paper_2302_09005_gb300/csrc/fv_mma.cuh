@@ -1,0 +1,65 @@
+// fv_mma.cuh -- BF16 tensor-core building blocks (warp-level mma.sync,
+// m16n8k16, FP32 accumulation) and the activation of the learned face-flux
+// correction network.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace fv {
+
+// D += A (16x16, row-major bf16) * B (16x8, column-major bf16), FP32 D.
+// Fragment ownership (lane = 4 g + t):
+//   a[0]: A[g][2t, 2t+1]      a[1]: A[g+8][2t, 2t+1]
+//   a[2]: A[g][2t+8, 2t+9]    a[3]: A[g+8][2t+8, 2t+9]
+//   b[0]: B[2t, 2t+1][g]      b[1]: B[2t+8, 2t+9][g]
+//   d[0..1]: D[g][2t, 2t+1]   d[2..3]: D[g+8][2t, 2t+1]
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4],
+                                          const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Two floats -> two bf16 (round to nearest even) packed low, high.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ uint32_t pack_bf16_raw(uint16_t lo, uint16_t hi) {
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+__device__ __forceinline__ float bf16_to_f32(uint16_t x) {
+  return __uint_as_float((uint32_t)x << 16);
+}
+__device__ __forceinline__ uint16_t f32_to_bf16(float x) {
+  const __nv_bfloat16 v = __float2bfloat16_rn(x);
+  return *reinterpret_cast<const uint16_t*>(&v);
+}
+
+// gelu(z) = z Phi(z), Phi the standard normal distribution function.
+__device__ __forceinline__ float gelu_f(float z) {
+  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+// gelu'(z) = Phi(z) + z phi(z).
+__device__ __forceinline__ float gelu_prime_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+         z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+
+// Layout of the flat parameter vector of the 16 -> 64 -> 64 -> 4 network:
+// W1 (64x16, output-major), b1 (64), W2 (64x64), b2 (64), W3 (4x64), b3 (4).
+constexpr int kMlpIn = 16, kMlpHid = 64, kMlpOut = 4;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kMlpHid * kMlpIn;    // 1024
+constexpr int kOffW2 = kOffB1 + kMlpHid;             // 1088
+constexpr int kOffB2 = kOffW2 + kMlpHid * kMlpHid;   // 5184
+constexpr int kOffW3 = kOffB2 + kMlpHid;             // 5248
+constexpr int kOffB3 = kOffW3 + kMlpOut * kMlpHid;   // 5504
+constexpr int kMlpParams = kOffB3 + kMlpOut;         // 5508
+// Normalisation block: mu_x (16), sd_x (16), sd_y (4).
+constexpr int kNormLen = 36;
+
+}  // namespace fv

@@ -92,6 +92,14 @@ def _lib() -> ctypes.CDLL:
         L.fv_batch_autotune.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl,
                                         ctypes.POINTER(c_int), ctypes.POINTER(dbl)]
         L.fv_batch_autotune.restype = c_int
+        L.fv_mlp_trainer_create.argtypes = [ctypes.POINTER(vp), i64, vp]
+        L.fv_mlp_trainer_destroy.argtypes = [vp]
+        L.fv_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
+        L.fv_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        L.fv_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, c_int, vp]
+        for name in ("fv_mlp_trainer_create", "fv_mlp_trainer_destroy", "fv_mlp_forward",
+                     "fv_mlp_grad", "fv_mlp_train_step"):
+            getattr(L, name).restype = c_int
         L.fv_last_error.argtypes = [vp]
         L.fv_last_error.restype = ctypes.c_char_p
         for name in ("fv_batch_create", "fv_batch_destroy", "fv_batch_set_stream",
@@ -246,6 +254,49 @@ def fv_batch_autotune(h, in_with_halo, scratch_out, patch_offsets, patch_sizes, 
                                   ctypes.byref(chosen), ms)
     _check(h, st, "fv_batch_autotune")
     return chosen.value, list(ms)
+
+
+FV_MLP_NPARAM = 5508
+FV_MLP_NNORM = 36
+
+
+class MlpTrainer:
+    """Owns an fv_mlp_trainer (workspace for batches up to max_batch)."""
+
+    def __init__(self, max_batch: int, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        sp = stream if isinstance(stream, int) else stream.cuda_stream
+        h = ctypes.c_void_p()
+        _check(None, _lib().fv_mlp_trainer_create(ctypes.byref(h), max_batch, sp),
+               "fv_mlp_trainer_create")
+        self.h = h.value
+        self.max_batch = max_batch
+
+    def close(self):
+        if self.h:
+            _check(None, _lib().fv_mlp_trainer_destroy(self.h), "fv_mlp_trainer_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, params, x, y):
+        _check(None, _lib().fv_mlp_forward(self.h, _ptr(params), _ptr(x), x.shape[0], _ptr(y)),
+               "fv_mlp_forward")
+
+    def grad(self, params, x, target, grad, loss):
+        _check(None, _lib().fv_mlp_grad(self.h, _ptr(params), _ptr(x), _ptr(target), x.shape[0],
+                                        _ptr(grad), _ptr(loss)), "fv_mlp_grad")
+
+    def train_step(self, params, x, target, lr: float, step: int, loss):
+        _check(None, _lib().fv_mlp_train_step(self.h, _ptr(params), _ptr(x), _ptr(target),
+                                              x.shape[0], lr, step, _ptr(loss)),
+               "fv_mlp_train_step")
 
 
 def fv_read_dt(h) -> float:

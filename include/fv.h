@@ -123,6 +123,8 @@ typedef struct {
   int64_t n_elems;      /* element count of both buffers; > 0 makes the
                            kernels skip (and flag) patches that would run
                            past it; 0 disables the check                    */
+  const float* corr;    /* per-face flux corrections (2D handles; layout of
+                           fv_flux_correction) added to F, or NULL          */
 } fv_update_extras;
 
 /* fv_patch_update_batch with optional outputs (extras may be NULL). */
@@ -286,6 +288,70 @@ fv_status fv_mlp_grad(fv_mlp_trainer* t, const float* params, const float* x,
  * trainer) on params in place; *loss receives the batch loss before it. */
 fv_status fv_mlp_train_step(fv_mlp_trainer* t, float* params, const float* x, const float* target,
                             int64_t batch, float lr, int step, float* loss);
+
+/*
+ * Learned correction on 2D patch meshes (handles with d == 2 and patches of
+ * at most 16 cells per axis).  Per-face arrays hold, per patch, the faces of
+ * each direction k (x then y), each unknown v, face j = tr + p b (b the
+ * halo-1 coordinate of the face's left cell along k, tr the transverse
+ * interior index from 0): element [patch * fv_corr_stride(h) +
+ * (k * 4 + v) * (p + 1) * p + j].
+ */
+/* Floats per patch of the per-face arrays: 8 (pmax + 1) pmax. */
+int64_t fv_corr_stride(const fv_batch* h);
+
+/*
+ * fv_flux_correction -- C for every face of every patch of the state q (the
+ * stencil cells outside a patch come from the neighbours by the rules of
+ * fv_halo_fill, two layers deep), into corr (device float, fv_corr_stride(h)
+ * per patch).  params: device float[FV_MLP_NPARAM]; norm: device
+ * float[FV_MLP_NNORM].  Runs on the tensor cores (BF16, FP32 accumulate).
+ */
+fv_status fv_flux_correction(fv_batch* h, const void* q, const int64_t* patch_offsets,
+                             const int32_t* patch_sizes, const int32_t* neighbours,
+                             int64_t n_patches, const float* params, const float* norm,
+                             float* corr);
+
+/* fv_time_step with the face fluxes F + C, C from fv_flux_correction on the
+ * same state (conservative: one F + C per face). */
+fv_status fv_time_step_corrected(fv_batch* h, const void* in_with_halo, void* out,
+                                 const int64_t* patch_offsets, const int32_t* patch_sizes,
+                                 const int32_t* neighbours, int64_t n_patches, double dx,
+                                 double cfl, const float* corr);
+
+/*
+ * Training data of the correction, on regular periodic 2D meshes: patches of
+ * one size per mesh, patch index a + px b (x fastest), the fine mesh covering
+ * the same domain at `ratio` times the resolution; the fine handle is FP64.
+ * fv_restrict_mesh        coarse interior cells = means of their ratio^2 fine
+ *                         cells;
+ * fv_accumulate_face_flux acc[face] += weight * mean of the ratio fine
+ *                         Rusanov fluxes on each coarse face (acc: device
+ *                         double, fv_corr_stride(hc) per coarse patch; the
+ *                         fine halos must be filled);
+ * fv_correction_samples   per coarse face (sample = patch * 2 (p+1) p +
+ *                         k (p+1) p + j): the raw 16-value stencil x_raw and
+ *                         the target C* = acc - F_Rusanov(coarse state) t_raw
+ *                         (4 values), both in the face's normal frame; FP64
+ *                         coarse handle.
+ */
+fv_status fv_restrict_mesh(fv_batch* h_fine, const void* q_fine, const int64_t* off_fine,
+                           int px_fine, int py_fine, fv_batch* h_coarse, void* q_coarse,
+                           const int64_t* off_coarse, int px_coarse, int py_coarse, int ratio);
+fv_status fv_accumulate_face_flux(fv_batch* h_fine, const void* q_fine, const int64_t* off_fine,
+                                  int px_fine, int py_fine, fv_batch* h_coarse, int px_coarse,
+                                  int py_coarse, int ratio, double weight, double* acc);
+fv_status fv_correction_samples(fv_batch* h_coarse, const void* q_coarse,
+                                const int64_t* patch_offsets, const int32_t* patch_sizes,
+                                const int32_t* neighbours, int64_t n_patches, const double* acc,
+                                float* x_raw, float* t_raw);
+/* Column sums and sums of squares (FP64) of a row-major float matrix;
+ * scratch: device double[2 cols ceil(rows / 65536)]. */
+fv_status fv_column_moments(const float* x, int64_t rows, int cols, double* sum, double* sumsq,
+                            double* scratch, void* cuda_stream);
+/* x[r][c] = (x[r][c] - mu[c]) / sd[c] in place (mu nullable: 0). */
+fv_status fv_normalize_columns(float* x, int64_t rows, int cols, const float* mu, const float* sd,
+                               void* cuda_stream);
 
 /*
  * fv_conserved_totals -- FP64 sums over all interior cells of every unknown

@@ -212,6 +212,9 @@ fv_status fv_patch_update_batch_ex(fv_batch* h, const void* in, void* out, const
   l.dt = dt;
   l.dt_dev = h->d_dt;
   l.lam_patch = ex ? ex->lambda_patch : nullptr;
+  l.corr = ex ? ex->corr : nullptr;
+  l.corr_stride = 2ll * 4 * (h->max_patch_size + 1) * h->max_patch_size;
+  if (l.corr && h->d != 2) return set_err(h, FV_ERR_UNSUPPORTED, "corrections are 2D");
   l.status = h->d_status;
   l.fused = false;
   cudaError_t e = fv::launch_scheduled(h, l);
@@ -305,9 +308,28 @@ fv_status fv_conserved_totals(fv_batch* h, const void* q, const int64_t* off,
   return FV_OK;
 }
 
+static fv_status time_step_impl(fv_batch* h, const void* in, void* out, const int64_t* off,
+                                const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
+                                double cfl, double* lambda_patch, const float* corr);
+
 fv_status fv_time_step(fv_batch* h, const void* in, void* out, const int64_t* off,
                        const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
                        double cfl, double* lambda_patch) {
+  return time_step_impl(h, in, out, off, sizes, nbr, n, dx, cfl, lambda_patch, nullptr);
+}
+
+fv_status fv_time_step_corrected(fv_batch* h, const void* in, void* out, const int64_t* off,
+                                 const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
+                                 double cfl, const float* corr) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  if (!corr) return set_err(h, FV_ERR_INVALID_ARG, "null corrections");
+  if (h->d != 2) return set_err(h, FV_ERR_UNSUPPORTED, "corrections are 2D");
+  return time_step_impl(h, in, out, off, sizes, nbr, n, dx, cfl, nullptr, corr);
+}
+
+static fv_status time_step_impl(fv_batch* h, const void* in, void* out, const int64_t* off,
+                                const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
+                                double cfl, double* lambda_patch, const float* corr) {
   if (!h) return FV_ERR_INVALID_ARG;
   h->last_error[0] = 0;
   if (!(dx > 0.0) || !(cfl > 0.0)) return set_err(h, FV_ERR_INVALID_ARG, "dx, cfl must be > 0");
@@ -337,6 +359,8 @@ fv_status fv_time_step(fv_batch* h, const void* in, void* out, const int64_t* of
   l.lam_patch = lambda_patch;
   l.status = h->d_status;
   l.fused = true;
+  l.corr = corr;
+  l.corr_stride = 2ll * 4 * (h->max_patch_size + 1) * h->max_patch_size;
   e = fv::launch_scheduled(h, l);
   if (e != cudaSuccess) return cuda_err(h, e, "time step kernel");
   h->lam_cur = nxt;

@@ -64,6 +64,8 @@ struct UpdateLaunch {
   unsigned long long* lam_next = nullptr;      // time-step mode
   double* dt_slot = nullptr;                   // time-step mode
   double* lam_patch = nullptr;
+  const float* corr = nullptr;  // learned flux corrections (fv_learned.cu)
+  int64_t corr_stride = 0;
   unsigned int* status = nullptr;
   bool fused = false;  // time-step mode: gather halos, dt from lam_in, reduce lam_next
   int nstage = 0;      // shared-memory stages (0: the handle's)

@@ -55,6 +55,8 @@ struct StepParams {
   double* dt_slot;                    // time-step mode: dt used, written once
   double* lam_patch;
   unsigned int* status;
+  const float* corr;    // per-face flux corrections [patch][k][v][face], or null
+  int64_t corr_stride;  // floats per patch of corr
 };
 
 template <int D>
@@ -391,7 +393,10 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
       // f_L + f_R - a (Q_R - Q_L), with the sign folded into the difference
       const T dqn = st[cl * S + v] - st[cr * S + v];
       const T fs = Fk[v * nbox + bl] + Fk[v * nbox + bl + ptr];
-      Gk[v * nface + j] = fma(am, dqn, fs);
+      T gv = fma(am, dqn, fs);
+      // learned correction C of this face (G = 2F, so G + 2C = 2(F + C))
+      if (a.corr != nullptr) gv += T(2) * (T)a.corr[i * a.corr_stride + (k * S + v) * nface + j];
+      Gk[v * nface + j] = gv;
     }
   }
   __syncthreads();
@@ -658,6 +663,8 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.lam_next = l.lam_next;
   a.dt_slot = l.dt_slot;
   a.lam_patch = l.lam_patch;
+  a.corr = l.corr;
+  a.corr_stride = l.corr_stride;
   a.status = l.status;
   const size_t smem = update_smem_bytes(D, h->prec, l.pmax, a.nstage);
   cudaError_t e = ensure_smem<T, D, GATHER, FUSED>(smem);

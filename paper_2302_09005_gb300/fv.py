@@ -39,7 +39,8 @@ class fv_options(ctypes.Structure):
 
 
 class fv_update_extras(ctypes.Structure):
-    _fields_ = [("lambda_patch", ctypes.c_void_p), ("n_elems", ctypes.c_int64)]
+    _fields_ = [("lambda_patch", ctypes.c_void_p), ("n_elems", ctypes.c_int64),
+                ("corr", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -99,6 +100,20 @@ def _lib() -> ctypes.CDLL:
         L.fv_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, c_int, vp]
         for name in ("fv_mlp_trainer_create", "fv_mlp_trainer_destroy", "fv_mlp_forward",
                      "fv_mlp_grad", "fv_mlp_train_step"):
+            getattr(L, name).restype = c_int
+        L.fv_corr_stride.argtypes = [vp]
+        L.fv_corr_stride.restype = i64
+        L.fv_flux_correction.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp]
+        L.fv_time_step_corrected.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, vp]
+        L.fv_restrict_mesh.argtypes = [vp, vp, vp, c_int, c_int, vp, vp, vp, c_int, c_int, c_int]
+        L.fv_accumulate_face_flux.argtypes = [vp, vp, vp, c_int, c_int, vp, c_int, c_int, c_int,
+                                              dbl, vp]
+        L.fv_correction_samples.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp]
+        L.fv_column_moments.argtypes = [vp, i64, c_int, vp, vp, vp, vp]
+        L.fv_normalize_columns.argtypes = [vp, i64, c_int, vp, vp, vp]
+        for name in ("fv_flux_correction", "fv_time_step_corrected", "fv_restrict_mesh",
+                     "fv_accumulate_face_flux", "fv_correction_samples", "fv_column_moments",
+                     "fv_normalize_columns"):
             getattr(L, name).restype = c_int
         L.fv_last_error.argtypes = [vp]
         L.fv_last_error.restype = ctypes.c_char_p
@@ -166,8 +181,8 @@ def fv_patch_update_batch(h, in_with_halo, out, patch_offsets, patch_sizes, n_pa
 
 def fv_patch_update_batch_ex(h, in_with_halo, out, patch_offsets, patch_sizes, n_patches: int,
                              d: int, s: int, dx: float, dt: float, lambda_patch=None,
-                             n_elems: int = 0):
-    ex = fv_update_extras(_ptr(lambda_patch), n_elems)
+                             n_elems: int = 0, corr=None):
+    ex = fv_update_extras(_ptr(lambda_patch), n_elems, _ptr(corr))
     st = _lib().fv_patch_update_batch_ex(h, _ptr(in_with_halo), _ptr(out), _ptr(patch_offsets),
                                          _ptr(patch_sizes), n_patches, d, s, dx, dt,
                                          ctypes.byref(ex))
@@ -299,6 +314,67 @@ class MlpTrainer:
                "fv_mlp_train_step")
 
 
+def _sp(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def fv_corr_stride(h) -> int:
+    return _lib().fv_corr_stride(h)
+
+
+def fv_flux_correction(h, q, patch_offsets, patch_sizes, neighbours, n_patches: int, params,
+                       norm, corr):
+    st = _lib().fv_flux_correction(h, _ptr(q), _ptr(patch_offsets), _ptr(patch_sizes),
+                                   _ptr(neighbours), n_patches, _ptr(params), _ptr(norm),
+                                   _ptr(corr))
+    _check(h, st, "fv_flux_correction")
+
+
+def fv_time_step_corrected(h, in_with_halo, out, patch_offsets, patch_sizes, neighbours,
+                           n_patches: int, dx: float, cfl: float, corr):
+    st = _lib().fv_time_step_corrected(h, _ptr(in_with_halo), _ptr(out), _ptr(patch_offsets),
+                                       _ptr(patch_sizes), _ptr(neighbours), n_patches, dx, cfl,
+                                       _ptr(corr))
+    _check(h, st, "fv_time_step_corrected")
+
+
+def fv_restrict_mesh(hf, qf, off_f, pfx: int, pfy: int, hc, qc, off_c, pcx: int, pcy: int,
+                     ratio: int):
+    st = _lib().fv_restrict_mesh(hf, _ptr(qf), _ptr(off_f), pfx, pfy, hc, _ptr(qc), _ptr(off_c),
+                                 pcx, pcy, ratio)
+    _check(hc, st, "fv_restrict_mesh")
+
+
+def fv_accumulate_face_flux(hf, qf, off_f, pfx: int, pfy: int, hc, pcx: int, pcy: int,
+                            ratio: int, weight: float, acc):
+    st = _lib().fv_accumulate_face_flux(hf, _ptr(qf), _ptr(off_f), pfx, pfy, hc, pcx, pcy, ratio,
+                                        weight, _ptr(acc))
+    _check(hc, st, "fv_accumulate_face_flux")
+
+
+def fv_correction_samples(hc, qc, patch_offsets, patch_sizes, neighbours, n_patches: int, acc,
+                          x_raw, t_raw):
+    st = _lib().fv_correction_samples(hc, _ptr(qc), _ptr(patch_offsets), _ptr(patch_sizes),
+                                      _ptr(neighbours), n_patches, _ptr(acc), _ptr(x_raw),
+                                      _ptr(t_raw))
+    _check(hc, st, "fv_correction_samples")
+
+
+def fv_column_moments(x, s, s2, scratch, stream=None):
+    st = _lib().fv_column_moments(_ptr(x), x.shape[0], x.shape[1], _ptr(s), _ptr(s2),
+                                  _ptr(scratch), _sp(stream))
+    _check(None, st, "fv_column_moments")
+
+
+def fv_normalize_columns(x, mu, sd, stream=None):
+    st = _lib().fv_normalize_columns(_ptr(x), x.shape[0], x.shape[1], _ptr(mu), _ptr(sd),
+                                     _sp(stream))
+    _check(None, st, "fv_normalize_columns")
+
+
 def fv_read_dt(h) -> float:
     """Synchronise and return the handle's device time step."""
     x = ctypes.c_double()
@@ -345,13 +421,14 @@ class Batch:
         except Exception:
             pass
 
-    def update(self, q_in, q_out, off, sizes, dx, dt, lambda_patch=None, n_elems=None):
+    def update(self, q_in, q_out, off, sizes, dx, dt, lambda_patch=None, n_elems=None,
+               corr=None):
         n = off.numel()
-        if lambda_patch is None and n_elems is None:
+        if lambda_patch is None and n_elems is None and corr is None:
             fv_patch_update_batch(self.h, q_in, q_out, off, sizes, n, self.d, self.s, dx, dt)
         else:
             fv_patch_update_batch_ex(self.h, q_in, q_out, off, sizes, n, self.d, self.s, dx, dt,
-                                     lambda_patch, n_elems or 0)
+                                     lambda_patch, n_elems or 0, corr)
 
     def halo_fill(self, q, off, sizes, nbr):
         fv_halo_fill(self.h, q, off, sizes, nbr, off.numel())

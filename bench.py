@@ -306,6 +306,7 @@ def run_ours(args, ws, rank, local):
         variants["batching_uneven_fp64"] = batching_variant(args, "f64")
         variants["batching_uneven_fp32"] = batching_variant(args, "f32")
         variants["precision_2d_4095"] = precision_variant(args)
+        variants["learned_correction_1024"] = learned_variant(args)
 
     peaks, peak_src = _peaks()
     if prec == "f64":
@@ -502,6 +503,101 @@ def precision_variant(args, N: int = 4095, p: int = 5, steps: int = 100):
     del finals, d64, d32
     return {"domain": f"{N}x{N} periodic, {n} patches of {p}x{p}", "steps": steps, **out,
             "fp32_rel_l1_vs_fp64_after_steps": rel_l1}
+
+
+def learned_variant(args, Nc: int = 1024, pc: int = 8, pf: int = 8, r: int = 4, steps: int = 8,
+                    train_seeds=(1, 2), eval_seed: int = 3, train_steps: int = 2000,
+                    batch: int = 32768):
+    """Learned face-flux correction on a periodic shear layer: training data
+    from 4x finer FP64 runs (two seeds), BF16 tensor-core training, then on a
+    held-out seed the relative L1 distance to the restricted fine run of
+    plain Rusanov at Nc, learned at Nc and plain Rusanov at 2 Nc (the
+    equal-cost comparison), with the time per coarse step of each, and the
+    throughput of the correction kernel against the BF16 roofline."""
+    import torch
+    from paper_2302_09005_gb300 import fv, inputs, learned
+    st = torch.cuda.Stream()
+    Xs, Ts = [], []
+    for seed in train_seeds:
+        X, T, _, _ = learned.generate(inputs.shear_layer(Nc * r, seed=seed), Nc, pc, pf, r,
+                                      steps, 0.4, st)
+        Xs.append(X)
+        Ts.append(T)
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    del Xs, Ts
+    nsamples = X.shape[0]
+    norm = learned.normalisation(X, T, st)
+    e0, e1 = _events(1)[0]
+    e0.record(st)
+    params, losses = learned.train(X, T, norm, steps=train_steps, batch=batch, lr=2e-3, seed=0,
+                                   stream=st)
+    e1.record(st)
+    st.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    del X, T
+    Uf = inputs.shear_layer(Nc * r, seed=eval_seed)
+    _, _, dts, refs = learned.generate(Uf, Nc, pc, pf, r, steps, 0.4, st)
+    l1_plain, l1_learned, ms = learned.evaluate(refs[0], refs, dts, pc, params, norm, st)
+    # plain Rusanov at twice the resolution, two substeps per coarse step
+    fine = learned.Mesh2D(Nc * r, pf, fv.FV_FP64, st, U=Uf)
+    m2 = learned.Mesh2D(2 * Nc, pc, fv.FV_FP64, st)
+    mc = learned.Mesh2D(Nc, pc, fv.FV_FP64, st)
+    fv.fv_restrict_mesh(fine.b.h, fine.x, fine.off, *fine.grid, m2.b.h, m2.x, m2.off, *m2.grid,
+                        r // 2)
+    fine.close()
+    l1_2x, ms_2x = [], 0.0
+    for n, dt in enumerate(dts):
+        a, b = _events(1)[0]
+        with torch.cuda.stream(st):
+            a.record(st)
+            m2.step(dt / 2)
+            m2.step(dt / 2)
+            b.record(st)
+            fv.fv_restrict_mesh(m2.b.h, m2.x, m2.off, *m2.grid, mc.b.h, mc.x, mc.off, *mc.grid,
+                                2)
+        st.synchronize()
+        ms_2x += a.elapsed_time(b)
+        D, ref = mc.domain(), refs[n + 1]
+        l1_2x.append((np.abs(D - ref).sum(axis=(0, 1)) / np.abs(ref).sum(axis=(0, 1))).tolist())
+    m2.close()
+    # correction kernel alone: faces/s and BF16 TFLOP/s (10,752 flop per face)
+    m = learned.Mesh2D(Nc, pc, fv.FV_FP32, st, U=refs[0])
+    corr = torch.zeros(m.n * fv.fv_corr_stride(m.b.h), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            fv.fv_flux_correction(m.b.h, m.x, m.off, m.sizes, m.nbr, m.n, params, norm, corr)
+        a, b = _events(1)[0]
+        a.record(st)
+        for _ in range(10):
+            fv.fv_flux_correction(m.b.h, m.x, m.off, m.sizes, m.nbr, m.n, params, norm, corr)
+        b.record(st)
+    st.synchronize()
+    kms = a.elapsed_time(b) / 10
+    faces = m.n * 2 * (pc + 1) * pc
+    flops = faces * 2 * (16 * 64 + 64 * 64 + 64 * 4)
+    m.close()
+    mc.close()
+    peaks, src = _peaks()
+    tf = flops / (kms / 1e3) / 1e12
+    mean = lambda rows: float(np.mean(rows[-1]))  # noqa: E731
+    return {
+        "domain": f"{Nc}x{Nc} periodic shear layer, {pc}x{pc} patches; fine {Nc * r}^2 FP64",
+        "train": {"samples": nsamples, "seeds": list(train_seeds), "steps": train_steps,
+                  "batch": batch, "ms": train_ms, "loss_first_last": [losses[0][1],
+                                                                      losses[-1][1]]},
+        "eval_seed": eval_seed, "coarse_steps": steps,
+        "rel_l1_after_steps": {"plain_Nc": l1_plain[-1], "learned_Nc": l1_learned[-1],
+                               "plain_2Nc": l1_2x[-1]},
+        "mean_rel_l1": {"plain_Nc": mean(l1_plain), "learned_Nc": mean(l1_learned),
+                        "plain_2Nc": mean(l1_2x)},
+        "ms_per_coarse_step": {"plain_Nc": ms[False], "learned_Nc": ms[True],
+                               "plain_2Nc": ms_2x / len(dts)},
+        "correction_kernel": {"ms": kms, "faces": faces, "gflop": flops / 1e9,
+                              "roofline": {"bound": "tensor", "achieved": tf,
+                                           "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                                           "frac": tf / peaks["bf16_tflops"],
+                                           "peak_source": src + " (BF16 dense, burst)"}},
+    }
 
 
 def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, stream):

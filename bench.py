@@ -738,14 +738,39 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant", choices=["batching", "precision", "learned"], default=None,
+                    help="run one variant on its own")
+    ap.add_argument("--small", action="store_true", help="small case of --variant")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     ws, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.variant:
+        run_variant(args)
+    elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
         run_ours(args, ws, rank, local)
+
+
+def run_variant(args):
+    """One variant on its own (profiling captures, focused measurements);
+    --small shrinks it to a case that an ncu capture finishes quickly."""
+    import torch
+    from paper_2302_09005_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    if args.variant == "batching":
+        res = batching_variant(args, "f64", n=20000 if args.small else 200000)
+    elif args.variant == "precision":
+        res = precision_variant(args, N=1020 if args.small else 4095,
+                                steps=10 if args.small else 100)
+    elif args.variant == "learned":
+        res = (learned_variant(args, Nc=256, steps=4, train_steps=200, batch=8192)
+               if args.small else learned_variant(args))
+    else:
+        raise SystemExit(f"unknown variant {args.variant}")
+    print(json.dumps({"variant": args.variant, "small": bool(args.small), **res}), flush=True)
 
 
 if __name__ == "__main__":

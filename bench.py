@@ -72,31 +72,44 @@ FP64_LANES_PER_SM = 2
 NUM_SMS = 152
 
 
-def fp64_ops_per_patch(d: int, p: int, fused: bool = False) -> int:
-    """FP64 pipe operations one patch update needs (the algorithm's count,
-    with the reciprocal and square root counted as the FP64 operations of
-    their Newton refinements: 3 and 5).  Per cell with primitives: 3 (1/rho)
-    + d (u) + d (j.u) + 2 (p) + 1 (E+p) + 2 (c^2) + 5 (sqrt) = 13 + 2d;
-    per (cell, direction) flux: |u|+c (1) + f (d + 1); per face: 3 s; per
-    interior cell update: s (2d - 1) + s."""
+def fp64_ops_per_patch(d: int, p: int, mode: str = "carry") -> int:
+    """FP64 pipe operations of one patch in the step kernel (the algorithm's
+    count, the reciprocal and square root counted as the FP64 operations of
+    their Newton refinements: 3 and 5).
+      primitives of a cell: 3 (1/rho) + d (u) + d (j.u) + 2 (p) + 1 (E+p)
+                            + 2 (c^2) + 5 (sqrt) = 13 + 2d;
+      face flux G:          2 (a) + 1 (p_L+p_R) + 1 (rho) + 2d (momenta)
+                            + 2 (energy) + s (Q_L-Q_R) + s (fma) = 4d + 10;
+      cell update:          s (2d) (sum of G_+ - G_- over d directions, fma);
+      next-step wave speed: primitives + d adds.
+    mode "update": primitives of the interior and face-halo cells, faces,
+    update; "step": that plus the next-step wave speed; "carry": the time
+    step with the primitive carry (no conversion of the input state)."""
     s = d + 2
     interior = p ** d
     halo = 2 * d * p ** (d - 1)
     faces = d * (p + 1) * p ** (d - 1)
     prim = 13 + 2 * d
-    flux = 1 + (d + 1)
-    ops = (interior * (prim + d * flux) + halo * (prim + flux) + faces * 3 * s
-           + interior * (s * (2 * d - 1) + s))
-    if fused:  # wave speed of the new state for the next step: primitives + d adds
-        ops += interior * (prim - 1 + d)
+    ops = faces * (4 * d + 10) + interior * s * 2 * d
+    if mode in ("update", "step"):
+        ops += (interior + halo) * prim
+    if mode in ("step", "carry"):
+        ops += interior * (prim + d)
     return ops
 
 
-def alg_bytes_per_patch(d: int, p: int, itemsize: int) -> int:
+def alg_bytes_per_patch(d: int, p: int, itemsize: int, carry: bool = False) -> int:
     """Algorithmic HBM bytes of one patch update: read the interior and the
-    face-halo cells, write the interior."""
+    face-halo cells, write the interior; with the primitive carry also read
+    the interior (d+3 values) and face-halo (4 values) primitives and write
+    the interior ones."""
     s = d + 2
-    return ((p ** d + 2 * d * p ** (d - 1)) * s + p ** d * s) * itemsize
+    interior = p ** d
+    halo = 2 * d * p ** (d - 1)
+    b = ((interior + halo) * s + interior * s) * itemsize
+    if carry:
+        b += (2 * interior * (d + 3) + halo * 4) * itemsize
+    return b
 
 
 class ClockSampler:
@@ -211,10 +224,21 @@ def run_ours(args, ws, rank, local):
         b.halo_fill(x, toff, tsz, tnbr)
         b.max_eigenvalue(x, toff, tsz, cfl, dx)
 
+    # primitive carry: each step reads the primitives the previous one wrote
+    pdt = torch.float64 if prec == "f64" else torch.float32
+    prims = [torch.empty(n * b.prim_stride(), dtype=pdt, device="cuda") for _ in range(2)]
+    carry = {"in": None, "k": 0}
+
+    def step(x, y):
+        pout = prims[carry["k"] & 1]
+        b.time_step_prim(x, y, carry["in"], pout, toff, tsz, tnbr, dx, cfl)
+        carry["in"] = pout
+        carry["k"] += 1
+
     with torch.cuda.stream(stream):
         seed(qa)
         for _ in range(args.warmup):
-            b.time_step(qa, qb, toff, tsz, tnbr, dx, cfl)
+            step(qa, qb)
             qa, qb = qb, qa
     stream.synchronize()
     if b.status() != fv.FV_OK:
@@ -233,7 +257,7 @@ def run_ours(args, ws, rank, local):
         t0.record(stream)
         for k in range(args.steps):
             ev[k][0].record(stream)
-            b.time_step(qa, qb, toff, tsz, tnbr, dx, cfl)
+            step(qa, qb)
             ev[k][1].record(stream)
             qa, qb = qb, qa
         t1.record(stream)
@@ -254,6 +278,21 @@ def run_ours(args, ws, rank, local):
 
     variants = {}
     if not args.no_variants:
+        # the same step without the primitive carry (fv_time_step)
+        k2 = max(1, min(args.steps, 5))
+        ev2 = _events(k2)
+        with torch.cuda.stream(stream):
+            for k in range(k2):
+                ev2[k][0].record(stream)
+                b.time_step(qa, qb, toff, tsz, tnbr, dx, cfl)
+                ev2[k][1].record(stream)
+                qa, qb = qb, qa
+        stream.synchronize()
+        nc_ms = sum(e[0].elapsed_time(e[1]) for e in ev2) / k2
+        variants["time_step_no_carry"] = {
+            "value": cells_per_step / (nc_ms / 1e3), "unit": UNIT, "ms_per_step": nc_ms,
+            "steps": k2, "what": "fv_time_step: the same fused step converting its input "
+                                "state to primitives itself"}
         # the same step as three separate kernels (halo fill, reduce, update)
         k2 = max(1, min(args.steps, 5))
         ev2 = _events(k2)
@@ -310,10 +349,10 @@ def run_ours(args, ws, rank, local):
 
     peaks, peak_src = _peaks()
     if prec == "f64":
-        ops = fp64_ops_per_patch(d, p, fused=True) * n
+        ops = fp64_ops_per_patch(d, p, "carry") * n
         peak_ops = FP64_LANES_PER_SM * NUM_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6
         achieved = ops / (kern_ms / 1e3)
-        roof = {"bound": "alu", "kernel": "step_kernel<double,3,gather,fused>",
+        roof = {"bound": "alu", "kernel": "step_kernel<double,3,gather,fused,carry>",
                 "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "T FP64-pipe ops/s", "frac": achieved / peak_ops,
                 "traffic": _traffic(args.workload),
@@ -322,12 +361,12 @@ def run_ours(args, ws, rank, local):
                                f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
     else:
         roof = None
-    alg_bytes = alg_bytes_per_patch(d, p, itemsize) * n
+    alg_bytes = alg_bytes_per_patch(d, p, itemsize, carry=True) * n
     hbm = {"achieved": alg_bytes / (kern_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
            "unit": "GB/s", "frac": alg_bytes / (kern_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
            "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src}
     if roof is None:
-        roof = {"bound": "hbm", "kernel": "step_kernel<float,3,gather,fused>", **hbm,
+        roof = {"bound": "hbm", "kernel": "step_kernel<float,3,gather,fused,carry>", **hbm,
                 "traffic": _traffic(args.workload)}
     b.close()
 
@@ -342,8 +381,9 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": args.workload, "d": d, "s": s, "patch": p,
                        "n_patches_per_gpu": n, "patch_grid": list(grid), "halo": 1,
                        "cfl": 0.4, "gamma": 1.4,
-                       "step": "fv_time_step: halo gather + Rusanov update + next-step "
-                               "CFL max in one kernel (initial CFL max seeded once)",
+                       "step": "fv_time_step_prim: halo gather + Rusanov update + "
+                               "next-step CFL max in one kernel, primitives (u, p, c, E+p) "
+                               "carried from step to step (initial CFL max seeded once)",
                        "l2": "inputs larger than L2 (2 x %.1f GB), no flush"
                              % (h_q.numel() * itemsize / 1e9),
                        "parallelism": f"replicas x{ws}"},
@@ -639,12 +679,32 @@ def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, s
             ev[k][1].record(stream)
             x, y = y, x
     stream.synchronize()
-    ok = b.status() == fv.FV_OK
     ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    # the same with the primitive carry
+    prims = [torch.empty(n * b.prim_stride(), dtype=torch.float32, device="cuda")
+             for _ in range(2)]
+    ev = _events(args.steps)
+    with torch.cuda.stream(stream):
+        b.time_step_prim(x, y, None, prims[0], toff, tsz, tnbr, dx, cfl)
+        x, y = y, x
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            b.time_step_prim(x, y, prims[k & 1], prims[(k + 1) & 1], toff, tsz, tnbr, dx, cfl)
+            ev[k][1].record(stream)
+            x, y = y, x
+    stream.synchronize()
+    ms_carry = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    del prims
+    ok = b.status() == fv.FV_OK
     peaks, peak_src = _peaks()
     alg = alg_bytes_per_patch(d, p, 4) * n
+    alg_c = alg_bytes_per_patch(d, p, 4, carry=True) * n
     b.close()
     return {"value": n * p ** d / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "what": "fv_time_step in FP32 (no primitive carry)",
+            "carry": {"value": n * p ** d / (ms_carry / 1e3), "ms_per_step": ms_carry,
+                      "what": "fv_time_step_prim in FP32",
+                      "hbm_frac": alg_c / (ms_carry / 1e3) / 1e9 / peaks["hbm_gbs"]},
             "status_ok": ok,
             "rel_l1_vs_fp64_one_step": rel_l1, "max_rel_err_vs_fp64_one_step":
                 max_rel.tolist(),

@@ -196,9 +196,42 @@ fv_status fv_time_step(fv_batch* h, const void* in_with_halo, void* out,
                        double* lambda_patch);
 
 /*
+ * Primitive carry between time steps.  A time step converts its new state
+ * to primitives (u_1..u_d, p, c, E + p of every interior cell; Eq. 2) for
+ * the next step's CFL condition anyway; handing them to the next step saves
+ * that step the conversion of every interior and face-halo cell (about a
+ * quarter of the FP64 work of a 3D step).
+ *
+ * fv_prim_stride -- elements (of the handle's precision) per patch of a
+ * primitive buffer: (d + 3) * max_patch_size^d rounded up to 16 bytes.  A
+ * buffer for n patches holds n * stride elements; patch i's block starts at
+ * element i * stride: component m (u_1..u_d, p, c, E + p) of interior cell
+ * (x, y, z) (0-based, x fastest) at m * p^d + x + p (y + p z).
+ *
+ * fv_time_step_prim -- fv_time_step with the carry: prim_in (device,
+ * nullable) holds the primitives of in_with_halo as the previous
+ * fv_time_step_prim wrote them to its prim_out; NULL computes them from the
+ * state (the first step).  prim_out (device, nullable) receives the
+ * primitives of out.  Both 16-byte aligned, n_patches * fv_prim_stride
+ * elements, distinct (prim_in == prim_out is FV_ERR_INVALID_ARG).  The
+ * caller owns them and must not change the state between the step that
+ * wrote prim_out and the step that reads it as prim_in: stale primitives
+ * give wrong fluxes (no error is detected).  The result is bitwise that of
+ * fv_time_step.
+ */
+fv_status fv_prim_stride(const fv_batch* h, int64_t* elems_per_patch);
+fv_status fv_time_step_prim(fv_batch* h, const void* in_with_halo, void* out,
+                            const void* prim_in, void* prim_out, const int64_t* patch_offsets,
+                            const int32_t* patch_sizes, const int32_t* neighbours,
+                            int64_t n_patches, double dx, double cfl, double* lambda_patch);
+
+/*
  * fv_run_steps -- n_steps time steps from q0: fv_halo_fill and
- * fv_max_eigenvalue_reduce on q0, then fv_time_step ping-ponging between q0
- * and q1.  The result is in q0 if n_steps is even, else in q1.
+ * fv_max_eigenvalue_reduce on q0, then fv_time_step_prim ping-ponging
+ * between q0 and q1, the primitives carried from step to step in two buffers
+ * the handle allocates on first use (2 * n_patches * fv_prim_stride
+ * elements, kept until fv_batch_destroy; growing them drops the cached
+ * graphs).  The result is in q0 if n_steps is even, else in q1.
  * use_graph != 0 captures the whole sequence into a CUDA graph the first
  * time a given set of arguments is seen, caches the instantiated graph in
  * the handle (keyed by every pointer and value argument) and replays it;

@@ -149,8 +149,8 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
   h->d_lam = reinterpret_cast<unsigned long long*>(w + 128);
   h->d_partials = reinterpret_cast<unsigned long long*>(w + 256);
   h->d_sum_partials = reinterpret_cast<double*>(w + 256 + 8ull * FV_MAX_RED_BLOCKS);
-  e = fv::update_occupancy(h, false, &h->update_blocks_per_sm);
-  if (e == cudaSuccess) e = fv::update_occupancy(h, true, &h->step_blocks_per_sm);
+  for (int mode = fv::kModeUpdate; mode <= fv::kModePrim && e == cudaSuccess; ++mode)
+    e = fv::step_occupancy(h, mode, h->max_patch_size, h->nstage, &h->blocks_per_sm[mode]);
   if (e != cudaSuccess) {
     cudaFree(h->ws);
     delete h;
@@ -165,6 +165,8 @@ fv_status fv_batch_destroy(fv_batch* h) {
   cudaError_t e = cudaStreamSynchronize(h->stream);
   graph_cache_clear(h);
   fv::plan_free(h);
+  for (void* pbuf : h->d_prim)
+    if (pbuf) cudaFree(pbuf);
   cudaError_t e2 = cudaFree(h->ws);
   delete h;
   return (e == cudaSuccess && e2 == cudaSuccess) ? FV_OK : FV_ERR_CUDA;
@@ -310,12 +312,28 @@ fv_status fv_conserved_totals(fv_batch* h, const void* q, const int64_t* off,
 
 static fv_status time_step_impl(fv_batch* h, const void* in, void* out, const int64_t* off,
                                 const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
-                                double cfl, double* lambda_patch, const float* corr);
+                                double cfl, double* lambda_patch, const float* corr,
+                                const void* prim_in, void* prim_out);
 
 fv_status fv_time_step(fv_batch* h, const void* in, void* out, const int64_t* off,
                        const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
                        double cfl, double* lambda_patch) {
-  return time_step_impl(h, in, out, off, sizes, nbr, n, dx, cfl, lambda_patch, nullptr);
+  return time_step_impl(h, in, out, off, sizes, nbr, n, dx, cfl, lambda_patch, nullptr, nullptr,
+                        nullptr);
+}
+
+fv_status fv_prim_stride(const fv_batch* h, int64_t* elems_per_patch) {
+  if (!h || !elems_per_patch) return FV_ERR_INVALID_ARG;
+  *elems_per_patch = fv::prim_stride_elems(h->d, h->prec, h->max_patch_size);
+  return FV_OK;
+}
+
+fv_status fv_time_step_prim(fv_batch* h, const void* in, void* out, const void* prim_in,
+                            void* prim_out, const int64_t* off, const int32_t* sizes,
+                            const int32_t* nbr, int64_t n, double dx, double cfl,
+                            double* lambda_patch) {
+  return time_step_impl(h, in, out, off, sizes, nbr, n, dx, cfl, lambda_patch, nullptr, prim_in,
+                        prim_out);
 }
 
 fv_status fv_time_step_corrected(fv_batch* h, const void* in, void* out, const int64_t* off,
@@ -324,12 +342,13 @@ fv_status fv_time_step_corrected(fv_batch* h, const void* in, void* out, const i
   if (!h) return FV_ERR_INVALID_ARG;
   if (!corr) return set_err(h, FV_ERR_INVALID_ARG, "null corrections");
   if (h->d != 2) return set_err(h, FV_ERR_UNSUPPORTED, "corrections are 2D");
-  return time_step_impl(h, in, out, off, sizes, nbr, n, dx, cfl, nullptr, corr);
+  return time_step_impl(h, in, out, off, sizes, nbr, n, dx, cfl, nullptr, corr, nullptr, nullptr);
 }
 
 static fv_status time_step_impl(fv_batch* h, const void* in, void* out, const int64_t* off,
                                 const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
-                                double cfl, double* lambda_patch, const float* corr) {
+                                double cfl, double* lambda_patch, const float* corr,
+                                const void* prim_in, void* prim_out) {
   if (!h) return FV_ERR_INVALID_ARG;
   h->last_error[0] = 0;
   if (!(dx > 0.0) || !(cfl > 0.0)) return set_err(h, FV_ERR_INVALID_ARG, "dx, cfl must be > 0");
@@ -339,6 +358,10 @@ static fv_status time_step_impl(fv_batch* h, const void* in, void* out, const in
   if (!out || !nbr) return set_err(h, FV_ERR_INVALID_ARG, "null output or neighbour table");
   if (!aligned16(out)) return set_err(h, FV_ERR_ALIGNMENT, "output not 16-byte aligned");
   if (in == out) return set_err(h, FV_ERR_INVALID_ARG, "in and out alias");
+  if ((prim_in && !aligned16(prim_in)) || (prim_out && !aligned16(prim_out)))
+    return set_err(h, FV_ERR_ALIGNMENT, "primitive buffer not 16-byte aligned");
+  if (prim_in && prim_in == prim_out)
+    return set_err(h, FV_ERR_INVALID_ARG, "prim_in and prim_out alias");
   const int nxt = h->lam_cur ^ 1;
   cudaError_t e = cudaMemsetAsync(&h->d_lam[nxt], 0, sizeof(unsigned long long), h->stream);
   if (e != cudaSuccess) return cuda_err(h, e, "time step: reset wave speed");
@@ -361,6 +384,9 @@ static fv_status time_step_impl(fv_batch* h, const void* in, void* out, const in
   l.fused = true;
   l.corr = corr;
   l.corr_stride = 2ll * 4 * (h->max_patch_size + 1) * h->max_patch_size;
+  l.prim_in = prim_in;
+  l.prim_out = prim_out;
+  l.prim_stride = fv::prim_stride_elems(h->d, h->prec, h->max_patch_size);
   e = fv::launch_scheduled(h, l);
   if (e != cudaSuccess) return cuda_err(h, e, "time step kernel");
   h->lam_cur = nxt;
@@ -374,6 +400,25 @@ fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* off, cons
   h->last_error[0] = 0;
   if (n_steps < 0) return set_err(h, FV_ERR_INVALID_ARG, "n_steps < 0");
   if (q0 == q1) return set_err(h, FV_ERR_INVALID_ARG, "q0 and q1 alias");
+  // the primitive carry: two buffers, grown (never shrunk) before any capture;
+  // graphs that refer to the old buffers are dropped when they move
+  if (n_steps > 1 && n > 0) {
+    const size_t es = h->prec == FV_FP64 ? 8 : 4;
+    const int64_t need = n * fv::prim_stride_elems(h->d, h->prec, h->max_patch_size);
+    if (need > h->prim_cap) {
+      cudaError_t e = cudaStreamSynchronize(h->stream);
+      graph_cache_clear(h);
+      for (void*& pbuf : h->d_prim) {
+        if (pbuf) cudaFree(pbuf);
+        pbuf = nullptr;
+      }
+      h->prim_cap = 0;
+      for (void*& pbuf : h->d_prim)
+        if (e == cudaSuccess) e = cudaMalloc(&pbuf, es * (size_t)need);
+      if (e != cudaSuccess) return cuda_err(h, e, "primitive buffers");
+      h->prim_cap = need;
+    }
+  }
   auto enqueue = [&]() -> fv_status {
     fv_status s = fv_halo_fill(h, q0, off, sizes, nbr, n);
     if (s == FV_OK) s = fv_max_eigenvalue_reduce(h, q0, off, sizes, n, nullptr, nullptr, cfl, dx,
@@ -381,7 +426,10 @@ fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* off, cons
     void* a = q0;
     void* b = q1;
     for (int k = 0; k < n_steps && s == FV_OK; ++k) {
-      s = fv_time_step(h, a, b, off, sizes, nbr, n, dx, cfl, nullptr);
+      // step k reads the primitives step k-1 left and hands on its own
+      const void* pin = k == 0 ? nullptr : h->d_prim[(k - 1) & 1];
+      void* pout = k + 1 < n_steps ? h->d_prim[k & 1] : nullptr;
+      s = time_step_impl(h, a, b, off, sizes, nbr, n, dx, cfl, nullptr, nullptr, pin, pout);
       std::swap(a, b);
     }
     return s;

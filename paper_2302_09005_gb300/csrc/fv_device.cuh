@@ -83,6 +83,15 @@ __device__ __forceinline__ double neg_t(double x) {
 }
 __device__ __forceinline__ float neg_t(float x) { return -x; }
 
+// Explicitly rounded add, subtract and multiply: never contracted into an
+// FMA, so an expression rounds the same way wherever it is inlined.
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
 // ---------------------------------------------------------------------------
 // Reciprocal and square root, once per cell of the interior and face halo.
 //
@@ -143,9 +152,9 @@ __device__ __forceinline__ double sqrt_t(double x) {
   float rf;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
   const double r = f32_as_f64(rf);
-  const double s0 = x * r;
+  const double s0 = mul_rn(x, r);
   const double e = fma(neg_t(s0), r, 1.0);
-  const double t = e * fma(e, 0.375, 0.5);
+  const double t = mul_rn(e, fma(e, 0.375, 0.5));
   return fma(s0, t, s0);
 }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
@@ -169,12 +178,12 @@ __device__ __forceinline__ Prim<T, D> primitives(const T* q, T gm1, T gamma, boo
   T jj = T(0);
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    w.u[k] = q[1 + k] * inv;
-    jj = k == 0 ? q[1] * w.u[0] : fma(q[1 + k], w.u[k], jj);
+    w.u[k] = mul_rn(q[1 + k], inv);
+    jj = k == 0 ? mul_rn(q[1], w.u[0]) : fma(q[1 + k], w.u[k], jj);
   }
-  w.p = gm1 * fma(T(-0.5), jj, q[D + 1]);
-  w.ep = q[D + 1] + w.p;
-  T c2 = (gamma * w.p) * inv;
+  w.p = mul_rn(gm1, fma(T(-0.5), jj, q[D + 1]));
+  w.ep = add_rn(q[D + 1], w.p);
+  T c2 = mul_rn(mul_rn(gamma, w.p), inv);
   w.c = sqrt_t(c2);
   bad |= !(positive_finite(q[0]) && positive_finite(w.p));
   return w;
@@ -186,9 +195,9 @@ __device__ __forceinline__ void flux_dir(const T* q, const Prim<T, D>& w, int k,
   T uk = w.u[k];
   f[0] = q[1 + k];
 #pragma unroll
-  for (int m = 0; m < D; ++m) f[1 + m] = (m == k) ? fma(q[1 + m], uk, w.p) : q[1 + m] * uk;
-  f[D + 1] = w.ep * uk;
-  lam = abs_t(uk) + w.c;
+  for (int m = 0; m < D; ++m) f[1 + m] = (m == k) ? fma(q[1 + m], uk, w.p) : mul_rn(q[1 + m], uk);
+  f[D + 1] = mul_rn(w.ep, uk);
+  lam = add_rn(abs_t(uk), w.c);
 }
 
 // ---------------------------------------------------------------------------
@@ -252,6 +261,21 @@ struct Geom {
       const int c1 = k == 0 ? a : (k == 1 ? ck : b);
       const int c2 = k == 2 ? ck : b;
       return c0 + ne * (c1 + ne * c2);
+    }
+  }
+  // Interior cell index (0-based coordinates, x fastest, stride p) of the
+  // cell with interior coordinate c along direction k and transverse index t.
+  __device__ __forceinline__ int icell_kt(int k, int c, int t) const {
+    if constexpr (D == 1) {
+      return c;
+    } else if constexpr (D == 2) {
+      return k == 0 ? c + p * t : t + p * c;
+    } else {
+      const int a = t % p, b = t / p;
+      const int c0 = k == 0 ? c : a;
+      const int c1 = k == 0 ? a : (k == 1 ? c : b);
+      const int c2 = k == 2 ? c : b;
+      return c0 + p * (c1 + p * c2);
     }
   }
   // Stride of the cell index along direction k.

@@ -28,8 +28,10 @@ struct fv_batch {
   int lam_cur = 0;                           // slot holding lambda of the current state
   unsigned long long* d_partials = nullptr;  // FV_MAX_RED_BLOCKS slots
   double* d_sum_partials = nullptr;          // FV_MAX_RED_BLOCKS * 8 slots
-  int update_blocks_per_sm = 0;              // occupancy cache, update mode
-  int step_blocks_per_sm = 0;                // occupancy cache, time-step mode
+  int blocks_per_sm[3] = {0, 0, 0};          // occupancy by kernel mode (kModeUpdate..)
+  // primitive carry of fv_run_steps: two buffers of prim_cap elements
+  void* d_prim[2] = {nullptr, nullptr};
+  int64_t prim_cap = 0;
   void* graph_cache = nullptr;               // captured multi-step graphs
   // schedule (fv_sched.cu): processing order sorted by size, size classes
   int sched = 0;                             // fv_schedule
@@ -39,7 +41,7 @@ struct fv_batch {
   int ncls = 0;
   int cls_p[64] = {0};
   int64_t cls_begin[64] = {0}, cls_end[64] = {0};
-  int occ_cache[2][64] = {{0}};              // CTAs per SM by (time-step mode, p)
+  int occ_cache[3][64] = {{0}};              // CTAs per SM by (kernel mode, p)
   int smem_optin = 0;                        // opt-in shared memory per CTA
   char last_error[512] = {0};
 };
@@ -69,14 +71,39 @@ struct UpdateLaunch {
   unsigned int* status = nullptr;
   bool fused = false;  // time-step mode: gather halos, dt from lam_in, reduce lam_next
   int nstage = 0;      // shared-memory stages (0: the handle's)
+  const void* prim_in = nullptr;  // time step: carried primitives of `in`, or null
+  void* prim_out = nullptr;       // time step: primitives of `out`, or null
+  int64_t prim_stride = 0;        // elements per patch of the primitive buffers
 };
+
+// Kernel modes: update (halos filled by the caller), time step (halo gather,
+// CFL from the device, next-step maximum), time step with primitive carry.
+constexpr int kModeUpdate = 0;
+constexpr int kModeStep = 1;
+constexpr int kModePrim = 2;
+inline int step_mode(const UpdateLaunch& l) {
+  return !l.fused ? kModeUpdate : (l.prim_in != nullptr ? kModePrim : kModeStep);
+}
+
+// Elements per patch of a primitive buffer: (d + 3) p^d for p = pmax, rounded
+// up to 16 bytes.
+inline int64_t prim_stride_elems(int d, fv_precision prec, int pmax) {
+  int64_t c = d + 3;
+  for (int k = 0; k < d; ++k) c *= pmax;
+  const int64_t vec = prec == FV_FP64 ? 2 : 4;
+  return (c + vec - 1) / vec * vec;
+}
 
 // Shared memory bytes of the update kernel for patches up to pmax.
 size_t update_smem_bytes(int d, fv_precision prec, int pmax, int nstage);
 cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& a, int grid);
-cudaError_t update_occupancy(const fv_batch* h, bool fused, int* blocks_per_sm);
-cudaError_t step_occupancy(const fv_batch* h, bool fused, int pmax, int nstage,
+cudaError_t step_occupancy(const fv_batch* h, int mode, int pmax, int nstage,
                            int* blocks_per_sm);
+// Per-precision launch and occupancy (fv_update.cu: double, fv_update_f32.cu: float).
+template <typename T>
+cudaError_t launch_step_prec(const fv_batch* h, const UpdateLaunch& l, int grid);
+template <typename T>
+cudaError_t occupancy_prec(int d, int mode, int pmax, int nstage, int* bps);
 // Launches the update / time-step kernel(s) under the handle's schedule.
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l);
 // Frees the schedule plan of a handle.

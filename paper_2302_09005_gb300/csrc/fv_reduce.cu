@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(FV_NT) eig_kernel(EigParams<T> a) {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         if (kdir < 0 || kdir == k) {
-          const T lam = abs_t(w.u[k]) + w.c;
+          const T lam = add_rn(abs_t(w.u[k]), w.c);
           const unsigned long long b = order_bits(lam);
           m = b > m ? b : m;
         }

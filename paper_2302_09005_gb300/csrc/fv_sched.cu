@@ -62,7 +62,7 @@ static int grid_for(const fv_batch* h, int64_t count, int bps) {
 
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
   const bool plan_ok = h->d_order != nullptr && h->plan_n == l.n && h->plan_sizes == l.sizes;
-  const int f = l.fused ? 1 : 0;
+  const int f = step_mode(l);
   if (h->sched == FV_SCHED_CLASSES && plan_ok) {
     for (int c = 0; c < h->ncls; ++c) {
       const int64_t cnt = h->cls_end[c] - h->cls_begin[c];
@@ -75,7 +75,7 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
       lc.nstage = stages_for(h, lc.pmax);
       int& bps = h->occ_cache[f][lc.pmax < 64 ? lc.pmax : 63];
       if (bps == 0) {
-        cudaError_t e = step_occupancy(h, l.fused, lc.pmax, lc.nstage, &bps);
+        cudaError_t e = step_occupancy(h, f, lc.pmax, lc.nstage, &bps);
         if (e != cudaSuccess) return e;
       }
       cudaError_t e = launch_update(h, lc, grid_for(h, cnt, bps));
@@ -83,7 +83,11 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
     }
     return cudaSuccess;
   }
-  const int bps = l.fused ? h->step_blocks_per_sm : h->update_blocks_per_sm;
+  int& bps = h->blocks_per_sm[f];
+  if (bps == 0) {
+    cudaError_t e = step_occupancy(h, f, h->max_patch_size, h->nstage, &bps);
+    if (e != cudaSuccess) return e;
+  }
   if (h->sched == FV_SCHED_LPT && plan_ok) {
     l.order = h->d_order;
     l.i_begin = 0;

@@ -1,0 +1,793 @@
+// fv_step.cuh -- the batched Rusanov patch update (Eq. 3-5, Algorithm 1 with
+// the outer loop over patches), one kernel template with three modes:
+//
+//   update     (fv_patch_update_batch) the halo cells are read from the input
+//              patch, as filled by fv_halo_fill;
+//   time step  (fv_time_step) the face-halo cells are gathered straight from
+//              the neighbours' interiors (periodic / outflow / wall as in
+//              fv_halo_fill), dt comes from the CFL condition on the maximum
+//              wave speed the previous step left on the device, and the
+//              kernel reduces the maximum wave speed of the new state for the
+//              next step.  One launch replaces halo fill + reduce + update
+//              and gives bitwise the same result;
+//   primitive  (fv_time_step_prim) a time step that also receives the
+//   carry      primitive state (u, p, c, E + p) of its input from the
+//              previous step and hands that of its output to the next.  The
+//              time step computes the primitives of the new state anyway (for
+//              the next CFL maximum), so carrying them removes the conversion
+//              of every interior and face-halo cell from the next step:
+//              a quarter of the FP64 work of a 3D step.  Bitwise equal to the
+//              time step without the carry.
+//
+// Each CTA is persistent and walks its patches i = blockIdx.x + k*gridDim.x.
+// While it computes patch i, the TMA engine copies patch i+1 (and, carrying
+// primitives, their interior block) into the other of two shared-memory
+// stages (cp.async.bulk, completion on an mbarrier), and the halo cells of
+// patch i+1 that live elsewhere are gathered with cp.async.
+// Per patch:
+//   cells   (not when primitives are carried) every interior and face-halo
+//           cell converts to primitives once (Eq. 2); interior cells keep
+//           all of (u, p, c, E + p), halo cells the normal velocity, p, c,
+//           E + p.  The two groups start on warp boundaries;
+//   faces   every face flux G = f_L + f_R - a (Q_R - Q_L) = 2F (Eq. 4, 5) is
+//           computed exactly once, from the states and primitives of its two
+//           cells, and shared by both;
+//   update  every interior cell sums G_+ - G_- over x, then y, then z and
+//           writes Q - (dt / 2dx) sum (Eq. 3); a time step then converts the
+//           new state to primitives for the next CFL maximum (and the carry).
+// Every floating-point operation is written out (fma or an explicitly
+// rounded add / multiply), so the compiler cannot contract differently in
+// different modes: the modes agree bitwise.  Maxima (per-patch a of
+// Algorithm 1 step 10, next-step wave speed) are taken on integer bit
+// patterns: exact and independent of the order of work.
+#pragma once
+
+#include "fv_device.cuh"
+#include "fv_internal.h"
+#include "fv_ptx.cuh"
+
+namespace fv {
+
+template <typename T>
+struct StepParams {
+  const T* __restrict__ in;
+  T* __restrict__ out;
+  const int64_t* __restrict__ off;
+  const int32_t* __restrict__ sizes;
+  const int32_t* __restrict__ nbr;  // time-step modes
+  const int32_t* __restrict__ order;  // processing order (patch indices), or null
+  int64_t i_begin, i_end;             // positions of the sequence this launch runs
+  int64_t n;                          // patches in the batch
+  int64_t n_elems;
+  int pmax;
+  int nstage;  // shared-memory stages: 2 (copy overlaps compute) or 1
+  T gamma, gm1;
+  double dx, dt, cfl;
+  const double* dt_dev;               // update mode with dt <= 0
+  const unsigned long long* lam_in;   // time-step modes: bits of lambda(Q^n)
+  unsigned long long* lam_next;       // time-step modes: bits of lambda(Q^n+1)
+  double* dt_slot;                    // time-step modes: dt used, written once
+  double* lam_patch;
+  unsigned int* status;
+  const float* corr;    // per-face flux corrections [patch][k][v][face], or null
+  int64_t corr_stride;  // floats per patch of corr
+  const T* __restrict__ prim_in;  // carried primitives of `in` (primitive-carry mode)
+  T* __restrict__ prim_out;       // primitives of `out` (time-step modes), or null
+  int64_t prim_stride;            // elements per patch of prim_in / prim_out
+};
+
+template <int D>
+__host__ __device__ inline int ipow_d(int b) {
+  return D == 1 ? b : D == 2 ? b * b : b * b * b;
+}
+// state box of a patch with its halo: (p+2)^D cells of D+2 unknowns
+template <int D>
+__host__ __device__ inline int stage_elems(int p) {
+  return ipow_d<D>(p + 2) * (D + 2);
+}
+// interior primitives: D+3 components (u_1..u_D, p, c, E+p) of p^D cells
+template <int D>
+__host__ __device__ inline int iprim_elems(int p) {
+  return (D + 3) * ipow_d<D>(p);
+}
+// face-halo primitives: 2D faces x 4 components (u_normal, p, c, E+p) x p^(D-1)
+template <int D>
+__host__ __device__ inline int hprim_elems(int p) {
+  return 2 * D * 4 * (ipow_d<D>(p) / p);
+}
+// face fluxes G: D directions x (D+2) unknowns x (p+1) p^(D-1) faces
+template <int D>
+__host__ __device__ inline int gface_elems(int p) {
+  return D * (D + 2) * (p + 1) * (ipow_d<D>(p) / p);
+}
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Unroll factors of the cell and face loops.
+#ifndef FV_UNROLL_CELLS
+#define FV_UNROLL_CELLS 1
+#endif
+#ifndef FV_UNROLL_FACES
+#define FV_UNROLL_FACES 1
+#endif
+#define FV_STR_(x) #x
+#define FV_PRAGMA_UNROLL(n) _Pragma(FV_STR_(unroll n))
+
+// Where the face-halo cells of one face come from: a patch (its index and
+// element offset), the layer along the face normal in that patch (halo-
+// inclusive coordinate), and whether the normal momentum is negated (wall).
+struct FaceSrc {
+  long long off;
+  int ck;
+  int neg;
+  int pidx;
+  int pad;
+};
+
+// Shared-memory header: two mbarriers (16 B), per-warp reduction slots, and
+// the face sources of the two stages (2 x 6 x 24 B).
+constexpr int kRedOff = 16;
+constexpr int kFaceSrcOff = 64;
+constexpr int kHdrBytes = 384;
+static_assert(kRedOff + 8 * (FV_NT / 32) <= kFaceSrcOff, "header too small");
+static_assert(kFaceSrcOff + 2 * 6 * (int)sizeof(FaceSrc) <= kHdrBytes, "header too small");
+
+// Shared-memory carve-up for patches up to pmax (element counts of T).  A
+// stage holds the state box, the interior primitives and the face-halo
+// primitives of one patch; two stages let the copy of the next patch overlap
+// the current one (one stage when two do not fit: the copy of the next
+// patch then starts after the current patch is done).  The face fluxes G
+// follow the stages.
+template <int D>
+struct Carve {
+  int nstage, box, ip, hp, stage, g;
+  __host__ __device__ Carve(int pmax, int vec, int nstage_)
+      : nstage(nstage_),
+        box(round_up(stage_elems<D>(pmax), vec)),
+        ip(round_up(iprim_elems<D>(pmax), vec)),
+        hp(round_up(hprim_elems<D>(pmax), vec)),
+        stage(box + ip + hp),
+        g(round_up(gface_elems<D>(pmax), vec)) {}
+  __host__ __device__ int total() const { return nstage * stage + g; }
+};
+
+template <typename T>
+struct Stage {
+  T* box;  // state, AoS cells (x fastest), halo-inclusive
+  T* ip;   // interior primitives [component][interior cell]
+  T* hp;   // face-halo primitives [face][component][transverse index]
+};
+
+// Clock cycles a CTA waits for a copy before it reports FV_ERR_TIMEOUT
+// (about one second at 2 GHz).
+constexpr long long kWaitLimit = 2000000000ll;
+
+// ---------------------------------------------------------------------------
+// Copies into a stage
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__device__ __forceinline__ bool patch_ok(const StepParams<T>& a, int64_t j, int& pj,
+                                         int64_t& offj) {
+  constexpr int VEC = 16 / sizeof(T);
+  pj = a.sizes[j];
+  offj = a.off[j];
+  bool ok = pj >= 1 && pj <= a.pmax && offj >= 0 && (offj % VEC) == 0;
+  if (ok && a.n_elems > 0) ok = offj + (int64_t)stage_elems<D>(pj) <= a.n_elems;
+  if (!ok && threadIdx.x == 0) atomicOr(a.status, ST_BAD_PATCH);
+  return ok;
+}
+
+// Thread 0: bulk copy of the 16-byte-aligned body of patch j into a stage,
+// and, carrying primitives, of its interior primitive block.  The state's
+// ragged tail (< 16 bytes) lies in the last cell of the patch, a corner
+// (d >= 2, never read) or the +x halo cell (d = 1, gathered separately).
+template <typename T, int D, bool PRIMIN>
+__device__ __forceinline__ void issue_stage(const StepParams<T>& a, int64_t pid, int pj,
+                                            int64_t offj, const Stage<T>& st, uint64_t* bar) {
+  const uint32_t bytes = (uint32_t)(stage_elems<D>(pj) * sizeof(T)) & ~15u;
+  uint32_t pbytes = 0;
+  if constexpr (PRIMIN) pbytes = (uint32_t)round_up(iprim_elems<D>(pj) * (int)sizeof(T), 16);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_expect_tx(bar, bytes + pbytes);
+  bulk_copy_g2s(st.box, a.in + offj, bytes, bar);
+  if constexpr (PRIMIN) bulk_copy_g2s(st.ip, a.prim_in + pid * a.prim_stride, pbytes, bar);
+}
+
+// Threads 0 .. 2d-1: resolve the sources of the 2d faces of patch j once (the
+// neighbour table and the neighbour's metadata are read and checked here, not
+// per halo element).  Time-step modes follow the rules of fv_halo_fill;
+// update mode with d = 1 re-reads the patch's own halo cells.
+template <typename T, int D, bool GATHER>
+__device__ __forceinline__ void face_sources(const StepParams<T>& a, int64_t j, int pj,
+                                             int64_t offj, FaceSrc* fs) {
+  if constexpr (!GATHER && D != 1) return;
+  constexpr int VEC = 16 / sizeof(T);
+  const int f = threadIdx.x;
+  if (f >= 2 * D) return;
+  const int side = f & 1;
+  FaceSrc r;
+  r.off = offj;
+  r.neg = 0;
+  r.pidx = (int)j;
+  r.pad = 0;
+  if constexpr (!GATHER) {
+    r.ck = side ? pj + 1 : 0;  // the own halo layer
+  } else {
+    r.ck = side ? pj : 1;  // outflow: the own interior layer next to the face
+    const int32_t nb = a.nbr[j * 2 * D + f];
+    if (nb >= 0) {
+      bool ok = nb < a.n;
+      int64_t onb = 0;
+      if (ok) {
+        onb = a.off[nb];
+        ok = a.sizes[nb] == pj && onb >= 0 && (onb % VEC) == 0 &&
+             (a.n_elems <= 0 || onb + (int64_t)stage_elems<D>(pj) <= a.n_elems);
+      }
+      if (ok) {
+        r.off = onb;
+        r.pidx = nb;
+        r.ck = side ? 1 : pj;  // the neighbour's interior layer next to the face
+      } else {
+        atomicOr(a.status, ST_BAD_PATCH);
+      }
+    } else if (nb == -2) {
+      r.neg = 1;  // wall: mirror of the own interior layer
+    } else if (nb != -1) {
+      atomicOr(a.status, ST_BAD_PATCH);
+    }
+  }
+  fs[f] = r;
+}
+
+// All threads: fetch the face-halo cells of a patch that do not come with its
+// bulk copy, from the sources resolved by face_sources, as cp.async element
+// copies (a wall's negated normal momentum with a plain load and store); when
+// primitives are carried, also the face-halo primitives (u_normal, p, c,
+// E + p) from the sources' carried blocks (a wall negates u_normal).
+template <typename T, int D, int P, bool GATHER, bool PRIMIN>
+__device__ __forceinline__ void gather_halo(const StepParams<T>& a, int pj, const Stage<T>& s,
+                                            const FaceSrc* fs) {
+  if constexpr (!GATHER && D != 1) return;
+  constexpr int S = D + 2;
+  const Geom<D, P> g(pj);
+  const int p = g.p;
+  const int ptr = g.ptrans();
+  for (int hc = threadIdx.x; hc < 2 * D * ptr; hc += FV_NT) {
+    const int f = hc / ptr;
+    const int r = hc - f * ptr;
+    const int k = f >> 1;
+    const FaceSrc m = fs[f];
+    const int cd = g.cell_kt(k, (f & 1) ? p + 1 : 0, r);
+    const int cs = g.cell_kt(k, m.ck, r);
+    T* dst = s.box + cd * S;
+    const T* src = a.in + m.off + (int64_t)cs * S;
+#pragma unroll
+    for (int v = 0; v < S; ++v) {
+      if (m.neg && v == 1 + k)
+        dst[v] = neg_t(__ldg(src + v));
+      else
+        cp_async_elem(dst + v, src + v);
+    }
+    if constexpr (PRIMIN) {
+      const int nint = g.nint();
+      const T* ps = a.prim_in + (int64_t)m.pidx * a.prim_stride + g.icell_kt(k, m.ck - 1, r);
+      T* pd = s.hp + f * 4 * ptr + r;
+      if (m.neg)
+        pd[0] = neg_t(__ldg(ps + k * nint));
+      else
+        cp_async_elem(pd, ps + k * nint);
+#pragma unroll
+      for (int v = 1; v < 4; ++v) cp_async_elem(pd + v * ptr, ps + (D + v - 1) * nint);
+    }
+  }
+  cp_async_commit();
+}
+
+template <typename T, int D, bool GATHER, bool PRIMIN>
+__device__ __forceinline__ void gather_dispatch(const StepParams<T>& a, int pj,
+                                                const Stage<T>& s, const FaceSrc* fs) {
+  if constexpr (!GATHER && D != 1) return;
+  if constexpr (D == 3) {
+    switch (pj) {
+      case 3: gather_halo<T, D, 3, GATHER, PRIMIN>(a, pj, s, fs); return;
+      case 5: gather_halo<T, D, 5, GATHER, PRIMIN>(a, pj, s, fs); return;
+      case 7: gather_halo<T, D, 7, GATHER, PRIMIN>(a, pj, s, fs); return;
+      default: gather_halo<T, D, 0, GATHER, PRIMIN>(a, pj, s, fs); return;
+    }
+  } else if constexpr (D == 2) {
+    switch (pj) {
+      case 3: gather_halo<T, D, 3, GATHER, PRIMIN>(a, pj, s, fs); return;
+      case 5: gather_halo<T, D, 5, GATHER, PRIMIN>(a, pj, s, fs); return;
+      case 8: gather_halo<T, D, 8, GATHER, PRIMIN>(a, pj, s, fs); return;
+      default: gather_halo<T, D, 0, GATHER, PRIMIN>(a, pj, s, fs); return;
+    }
+  } else {
+    gather_halo<T, D, 0, GATHER, PRIMIN>(a, pj, s, fs);
+  }
+}
+
+// State of the copy pipeline of one CTA.
+struct Pipe {
+  uint64_t* bar;
+  uint32_t parity;   // bit s: parity of the next completion of bar[s]
+  uint32_t pending;  // bit s: a bulk copy into stage s is in flight
+  bool timeout;
+};
+
+template <typename T>
+struct NextPatch {
+  int64_t j;    // position in the processing sequence; >= i_end: none
+  int64_t pid;  // patch index
+  int p;
+  int64_t off;
+  Stage<T> st;
+  FaceSrc* fs;
+  int slot;
+};
+
+// Inside a patch, after a barrier: wait for the bulk copy of the next patch
+// and start its halo gather, so both overlap the rest of this patch.
+template <typename T, int D, bool GATHER, bool PRIMIN>
+__device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
+                                         const NextPatch<T>& nx) {
+  if (nx.j >= a.i_end) return;
+  const bool ok = mbar_wait_bounded(&pp.bar[nx.slot], (pp.parity >> nx.slot) & 1u, kWaitLimit);
+  if (ok) {
+    pp.parity ^= 1u << nx.slot;
+    pp.pending &= ~(1u << nx.slot);
+  }
+  if (!ok) {
+    pp.timeout = true;
+    return;
+  }
+  gather_dispatch<T, D, GATHER, PRIMIN>(a, nx.p, nx.st, nx.fs);
+}
+
+// ---------------------------------------------------------------------------
+// One patch: cells, faces, update.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int P, bool GATHER, bool FUSED, bool PRIMIN>
+__device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, int64_t i,
+                                              int64_t off, const Stage<T>& cur, T* G, T mhr,
+                                              unsigned long long* red,
+                                              unsigned long long& lam_next, Pipe& pp,
+                                              const NextPatch<T>& nx) {
+  constexpr int S = D + 2;
+  constexpr int NT = FV_NT;
+  const Geom<D, P> g(p_rt);
+  const int p = g.p;
+  const int nface = g.nface(), nint = g.nint(), ptr = g.ptrans();
+  const int tid = threadIdx.x;
+  const T* __restrict__ st = cur.box;
+  T* ip = cur.ip;
+  T* hp = cur.hp;
+  bool bad = false;
+
+  // ---- cells: primitives of the interior and face-halo cells ---------------
+  if constexpr (!PRIMIN) {
+    const int nint_pad = (nint + 31) & ~31;
+    const int nA = nint_pad + 2 * D * ptr;
+    FV_PRAGMA_UNROLL(FV_UNROLL_CELLS)
+    for (int t = tid; t < nA; t += NT) {
+      if (t < nint) {
+        int c[3] = {0, 0, 0};
+        int r = t;
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          c[m] = 1 + r % p;
+          r /= p;
+        }
+        const int cid = g.cell(c);
+        T q[S];
+#pragma unroll
+        for (int v = 0; v < S; ++v) q[v] = st[cid * S + v];
+        const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
+#pragma unroll
+        for (int m = 0; m < D; ++m) ip[m * nint + t] = w.u[m];
+        ip[D * nint + t] = w.p;
+        ip[(D + 1) * nint + t] = w.c;
+        ip[(D + 2) * nint + t] = w.ep;
+      } else if (t >= nint_pad) {
+        const int hc = t - nint_pad;
+        const int f = hc / ptr;
+        const int r = hc - f * ptr;
+        const int k = f >> 1;
+        const int cid = g.cell_kt(k, (f & 1) ? p + 1 : 0, r);
+        T q[S];
+#pragma unroll
+        for (int v = 0; v < S; ++v) q[v] = st[cid * S + v];
+        const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
+        T uk = w.u[0];
+#pragma unroll
+        for (int m = 1; m < D; ++m) uk = (k == m) ? w.u[m] : uk;
+        T* h = hp + f * 4 * ptr + r;
+        h[0] = uk;
+        h[ptr] = w.p;
+        h[2 * ptr] = w.c;
+        h[3 * ptr] = w.ep;
+      }
+    }
+    __syncthreads();
+    mid_hook<T, D, GATHER, PRIMIN>(a, pp, nx);
+  }
+
+  // ---- faces: G = f_L + f_R - a (Q_R - Q_L), once per face -------------------
+  unsigned long long lmax = 0ull;
+  FV_PRAGMA_UNROLL(FV_UNROLL_FACES)
+  for (int t = tid; t < D * nface; t += NT) {
+    const int k = t / nface;
+    const int j = t - k * nface;
+    const int b = j / ptr;  // the face lies between cells b and b+1 along k
+    const int tr = j - b * ptr;
+    const int cl = g.cell_kt(k, b, tr);
+    const int cr = cl + g.stride(k);
+    // primitives of the two cells: face-halo block at the patch boundary,
+    // interior block inside
+    const bool hl = b == 0, hrt = b == p;
+    const int icl = g.icell_kt(k, hl ? 0 : b - 1, tr);
+    const int icr = g.icell_kt(k, hrt ? p - 1 : b, tr);
+    const T* ul = hl ? hp + 8 * k * ptr + tr : ip + k * nint + icl;
+    const T* pl = hl ? hp + (8 * k + 1) * ptr + tr : ip + D * nint + icl;
+    const int sl = hl ? ptr : nint;
+    const T* ur = hrt ? hp + (8 * k + 4) * ptr + tr : ip + k * nint + icr;
+    const T* pr = hrt ? hp + (8 * k + 5) * ptr + tr : ip + D * nint + icr;
+    const int sr = hrt ? ptr : nint;
+    const T uL = ul[0], pL = pl[0], cL = pl[sl], eL = pl[2 * sl];
+    const T uR = ur[0], pR = pr[0], cR = pr[sr], eR = pr[2 * sr];
+    T qL[S], qR[S];
+#pragma unroll
+    for (int v = 0; v < S; ++v) {
+      qL[v] = st[cl * S + v];
+      qR[v] = st[cr * S + v];
+    }
+    // a = max(|u_k| + c) over the two cells (Eq. 5)
+    const T am = max_by_bits(add_rn(abs_t(uL), cL), add_rn(abs_t(uR), cR));
+    const unsigned long long ab = order_bits(am);
+    lmax = ab > lmax ? ab : lmax;
+    // f_L + f_R (Eq. 2): j_k; j_m u_k + p delta_mk; (E + p) u_k
+    T jkL = qL[1], jkR = qR[1];
+#pragma unroll
+    for (int m = 1; m < D; ++m) {
+      jkL = (k == m) ? qL[1 + m] : jkL;
+      jkR = (k == m) ? qR[1 + m] : jkR;
+    }
+    const T ps = add_rn(pL, pR);
+    T fs[S];
+    fs[0] = add_rn(jkL, jkR);
+#pragma unroll
+    for (int m = 0; m < D; ++m)
+      fs[1 + m] = fma(qL[1 + m], uL, fma(qR[1 + m], uR, (m == k) ? ps : T(-0.0)));
+    fs[D + 1] = fma(eL, uL, mul_rn(eR, uR));
+    T* Gk = G + k * S * nface;
+#pragma unroll
+    for (int v = 0; v < S; ++v) {
+      T gv = fma(am, sub_rn(qL[v], qR[v]), fs[v]);
+      // learned correction C of this face (G = 2F, so G + 2C = 2(F + C))
+      if (a.corr != nullptr)
+        gv = add_rn(gv, T(2) * (T)a.corr[i * a.corr_stride + (k * S + v) * nface + j]);
+      Gk[v * nface + j] = gv;
+    }
+  }
+  __syncthreads();
+  if constexpr (PRIMIN) mid_hook<T, D, GATHER, PRIMIN>(a, pp, nx);
+
+  // ---- update: Q - (dt/2dx) sum_k (G_+ - G_-) -----------------------------------
+  T* dst_base = a.out + off;
+  for (int t = tid; t < nint; t += NT) {
+    int c[3] = {0, 0, 0};
+    int r = t;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      c[m] = 1 + r % p;
+      r /= p;
+    }
+    const int cid = g.cell(c);
+    T acc[S];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int jm = g.trans(c, k) + ptr * (c[k] - 1);
+      const T* Gk = G + k * S * nface;
+#pragma unroll
+      for (int v = 0; v < S; ++v) {
+        const T dG = sub_rn(Gk[v * nface + jm + ptr], Gk[v * nface + jm]);
+        acc[v] = k == 0 ? dG : add_rn(acc[v], dG);
+      }
+    }
+    T qn[S];
+#pragma unroll
+    for (int v = 0; v < S; ++v) qn[v] = fma(mhr, acc[v], st[cid * S + v]);
+    T* dst = dst_base + (int64_t)cid * S;
+#pragma unroll
+    for (int v = 0; v < S; ++v) dst[v] = qn[v];
+    if constexpr (FUSED) {
+      // primitives and wave speed of the new state, for the next step's CFL
+      // condition (and its primitive carry)
+      const Prim<T, D> w = primitives<T, D>(qn, a.gm1, a.gamma, bad);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const unsigned long long lb = order_bits(add_rn(abs_t(w.u[k]), w.c));
+        lam_next = lb > lam_next ? lb : lam_next;
+      }
+      if (a.prim_out != nullptr) {
+        T* po = a.prim_out + i * a.prim_stride + t;
+#pragma unroll
+        for (int m = 0; m < D; ++m) po[m * nint] = w.u[m];
+        po[D * nint] = w.p;
+        po[(D + 1) * nint] = w.c;
+        po[(D + 2) * nint] = w.ep;
+      }
+    }
+  }
+
+  if (bad) atomicOr(a.status, ST_NONPHYSICAL);
+  if (a.lam_patch != nullptr) {
+    lmax = warp_max_u64(lmax);
+    if ((tid & 31) == 0) red[tid >> 5] = lmax;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long m = red[0];
+#pragma unroll
+      for (int w = 1; w < NT / 32; ++w) m = red[w] > m ? red[w] : m;
+      a.lam_patch[i] = order_value<T>(m);
+    }
+  }
+}
+
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+__device__ __forceinline__ void patch_dispatch(const StepParams<T>& a, int p, int64_t i,
+                                               int64_t off, const Stage<T>& st, T* G, T hr,
+                                               unsigned long long* red,
+                                               unsigned long long& lam_next, Pipe& pp,
+                                               const NextPatch<T>& nx) {
+#define FV_PC(PP) \
+  patch_compute<T, D, PP, GATHER, FUSED, PRIMIN>(a, p, i, off, st, G, hr, red, lam_next, pp, nx)
+  if constexpr (D == 3) {
+    switch (p) {
+      case 3: FV_PC(3); return;
+      case 5: FV_PC(5); return;
+      case 7: FV_PC(7); return;
+      default: FV_PC(0); return;
+    }
+  } else if constexpr (D == 2) {
+    switch (p) {
+      case 3: FV_PC(3); return;
+      case 5: FV_PC(5); return;
+      case 8: FV_PC(8); return;
+      case 17: FV_PC(17); return;
+      default: FV_PC(0); return;
+    }
+  } else {
+    FV_PC(0);
+  }
+#undef FV_PC
+}
+
+// Resident CTAs per SM the register allocation is sized for.
+#ifndef FV_MINBLOCKS_FP64
+#define FV_MINBLOCKS_FP64 3
+#endif
+#ifndef FV_MINBLOCKS_FP32
+#define FV_MINBLOCKS_FP32 6
+#endif
+
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+__global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV_MINBLOCKS_FP32)
+    step_kernel(StepParams<T> a) {
+  static_assert(!PRIMIN || (GATHER && FUSED), "the primitive carry is a time-step mode");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(smem_raw + kRedOff);
+  FaceSrc* fsrc = reinterpret_cast<FaceSrc*>(smem_raw + kFaceSrcOff);  // [stage][face]
+  constexpr int VEC = 16 / sizeof(T);
+  const Carve<D> cv(a.pmax, VEC, a.nstage);
+  const bool single = a.nstage == 1;
+  T* const sbase = reinterpret_cast<T*>(smem_raw + kHdrBytes);
+  // stage s (0 or 1; the same one when single), built by arithmetic so the
+  // pointers stay in registers
+  auto stage_at = [&](int s) -> Stage<T> {
+    T* b = sbase + (single ? 0 : s) * cv.stage;
+    return Stage<T>{b, b + cv.box, b + cv.box + cv.ip};
+  };
+  T* G = sbase + cv.nstage * cv.stage;
+  const int tid = threadIdx.x;
+
+  double dtv;
+  if constexpr (FUSED) {
+    const double lam = order_value<T>(*a.lam_in);
+    dtv = (a.cfl * a.dx) / ((double)D * lam);
+    if (blockIdx.x == 0 && tid == 0) *a.dt_slot = dtv;
+  } else {
+    dtv = a.dt > 0.0 ? a.dt : *a.dt_dev;
+  }
+  const T hr = neg_t((T)(0.5 * (dtv / a.dx)));  // -dt / (2 dx), passed as mhr
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  Pipe pp{bar, 0u, 0u, false};
+  unsigned long long lam_next = 0ull;
+
+  // Processing sequence: positions [i_begin, i_end), patch order[pos] (or
+  // pos itself), CTA b takes positions i_begin + b, + gridDim.x, ...
+  auto pid_of = [&](int64_t pos) -> int64_t {
+    return a.order != nullptr ? (int64_t)a.order[pos] : pos;
+  };
+  // first valid patch of this CTA, staged before the loop
+  int64_t cur = a.i_begin + blockIdx.x;
+  int64_t pidc = 0;
+  int pc = 0;
+  int64_t oc = 0;
+  while (cur < a.i_end && !patch_ok<T, D>(a, pidc = pid_of(cur), pc, oc)) cur += gridDim.x;
+  int s = 0;
+  if (cur < a.i_end) {
+    face_sources<T, D, GATHER>(a, pidc, pc, oc, fsrc);
+    if (tid == 0) issue_stage<T, D, PRIMIN>(a, pidc, pc, oc, stage_at(0), &bar[0]);
+    pp.pending = 1u;
+    __syncthreads();  // face sources visible
+    const bool ok = mbar_wait_bounded(&bar[0], 0u, kWaitLimit);
+    if (ok) {
+      pp.parity ^= 1u;
+      pp.pending = 0u;
+      gather_dispatch<T, D, GATHER, PRIMIN>(a, pc, stage_at(0), fsrc);
+    } else {
+      pp.timeout = true;
+    }
+    cp_async_wait_all();
+  }
+  if (__syncthreads_or(pp.timeout)) cur = a.i_end;
+
+  while (cur < a.i_end) {
+    NextPatch<T> nx;
+    nx.j = cur + gridDim.x;
+    nx.pid = 0;
+    while (nx.j < a.i_end && !patch_ok<T, D>(a, nx.pid = pid_of(nx.j), nx.p, nx.off))
+      nx.j += gridDim.x;
+    nx.slot = single ? 0 : s ^ 1;
+    nx.st = stage_at(nx.slot);
+    nx.fs = fsrc + 6 * nx.slot;
+    // visible to all threads after the barrier inside the patch
+    if (nx.j < a.i_end) face_sources<T, D, GATHER>(a, nx.pid, nx.p, nx.off, nx.fs);
+    NextPatch<T> nx_mid = nx;  // what the mid-patch hook waits for and gathers
+    if (single) {
+      nx_mid.j = a.i_end;  // the one stage is busy until this patch is done
+    } else if (nx.j < a.i_end) {
+      if (tid == 0) issue_stage<T, D, PRIMIN>(a, nx.pid, nx.p, nx.off, nx.st, &bar[nx.slot]);
+      pp.pending |= 1u << nx.slot;
+    }
+    patch_dispatch<T, D, GATHER, FUSED, PRIMIN>(a, pc, pidc, oc, stage_at(s), G, hr, red,
+                                                lam_next, pp, nx_mid);
+    cp_async_wait_all();
+    if (__syncthreads_or(pp.timeout)) break;
+    if (single && nx.j < a.i_end) {
+      if (tid == 0) issue_stage<T, D, PRIMIN>(a, nx.pid, nx.p, nx.off, nx.st, &bar[0]);
+      pp.pending |= 1u;
+      mid_hook<T, D, GATHER, PRIMIN>(a, pp, nx);
+      cp_async_wait_all();
+      if (__syncthreads_or(pp.timeout)) break;
+    }
+    cur = nx.j;
+    pidc = nx.pid;
+    pc = nx.p;
+    oc = nx.off;
+    if (!single) s ^= 1;
+  }
+  if (pp.timeout) {
+    // a copy did not complete in time: report, give the copies in flight a
+    // second bounded wait, and leave
+    if (tid == 0) atomicOr(a.status, ST_TIMEOUT);
+    if (pp.pending & 1u) mbar_wait_bounded(&bar[0], pp.parity & 1u, kWaitLimit);
+    if (pp.pending & 2u) mbar_wait_bounded(&bar[1], (pp.parity >> 1) & 1u, kWaitLimit);
+    cp_async_wait_all();
+    return;
+  }
+  if constexpr (FUSED) {
+    lam_next = warp_max_u64(lam_next);
+    if ((tid & 31) == 0) red[tid >> 5] = lam_next;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long m = red[0];
+#pragma unroll
+      for (int w = 1; w < FV_NT / 32; ++w) m = red[w] > m ? red[w] : m;
+      atomicMax(a.lam_next, m);
+    }
+  }
+}
+
+// Bytes of dynamic shared memory of the kernel for patches up to pmax.
+template <int D>
+inline size_t step_smem_bytes(int es, int pmax, int nstage) {
+  return kHdrBytes + (size_t)es * Carve<D>(pmax, 16 / es, nstage).total();
+}
+
+// Raises the kernel's dynamic shared-memory limit on the current device once
+// (not per launch, so launches can be captured into CUDA graphs).
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+static cudaError_t ensure_smem(size_t smem) {
+  static int set_bytes[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && set_bytes[dev] >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(step_kernel<T, D, GATHER, FUSED, PRIMIN>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) set_bytes[dev] = (int)smem;
+  return e;
+}
+
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int grid) {
+  StepParams<T> a;
+  a.in = static_cast<const T*>(l.in);
+  a.out = static_cast<T*>(l.out);
+  a.off = l.off;
+  a.sizes = l.sizes;
+  a.nbr = l.nbr;
+  a.order = l.order;
+  a.i_begin = l.i_begin;
+  a.i_end = l.i_end >= 0 ? l.i_end : l.n;
+  a.n = l.n;
+  a.n_elems = l.n_elems;
+  a.pmax = l.pmax;
+  a.nstage = l.nstage > 0 ? l.nstage : h->nstage;
+  a.gamma = (T)l.gamma;
+  a.gm1 = (T)(l.gamma - 1.0);
+  a.dx = l.dx;
+  a.dt = l.dt;
+  a.cfl = l.cfl;
+  a.dt_dev = l.dt_dev;
+  a.lam_in = l.lam_in;
+  a.lam_next = l.lam_next;
+  a.dt_slot = l.dt_slot;
+  a.lam_patch = l.lam_patch;
+  a.corr = l.corr;
+  a.corr_stride = l.corr_stride;
+  a.status = l.status;
+  a.prim_in = static_cast<const T*>(l.prim_in);
+  a.prim_out = static_cast<T*>(l.prim_out);
+  a.prim_stride = l.prim_stride;
+  const size_t smem = step_smem_bytes<D>((int)sizeof(T), l.pmax, a.nstage);
+  cudaError_t e = ensure_smem<T, D, GATHER, FUSED, PRIMIN>(smem);
+  if (e != cudaSuccess) return e;
+  step_kernel<T, D, GATHER, FUSED, PRIMIN><<<grid, FV_NT, smem, h->stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+static cudaError_t occupancy_t(int pmax, int nstage, int* bps) {
+  const size_t smem = step_smem_bytes<D>((int)sizeof(T), pmax, nstage);
+  cudaError_t e = ensure_smem<T, D, GATHER, FUSED, PRIMIN>(smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      bps, step_kernel<T, D, GATHER, FUSED, PRIMIN>, FV_NT, smem);
+}
+
+// Launch / occupancy of one precision, dispatched over d and the mode.
+template <typename T>
+cudaError_t launch_step_prec(const fv_batch* h, const UpdateLaunch& l, int grid) {
+  const int mode = step_mode(l);
+#define FV_LAUNCH_D(G_, F_, P_)                                           \
+  (h->d == 1   ? launch_step_t<T, 1, G_, F_, P_>(h, l, grid)              \
+   : h->d == 2 ? launch_step_t<T, 2, G_, F_, P_>(h, l, grid)              \
+               : launch_step_t<T, 3, G_, F_, P_>(h, l, grid))
+  if (mode == kModePrim) return FV_LAUNCH_D(true, true, true);
+  if (mode == kModeStep) return FV_LAUNCH_D(true, true, false);
+  return FV_LAUNCH_D(false, false, false);
+#undef FV_LAUNCH_D
+}
+
+template <typename T>
+cudaError_t occupancy_prec(int d, int mode, int pmax, int nstage, int* bps) {
+#define FV_OCC_D(G_, F_, P_)                                            \
+  (d == 1   ? occupancy_t<T, 1, G_, F_, P_>(pmax, nstage, bps)          \
+   : d == 2 ? occupancy_t<T, 2, G_, F_, P_>(pmax, nstage, bps)          \
+            : occupancy_t<T, 3, G_, F_, P_>(pmax, nstage, bps))
+  if (mode == kModePrim) return FV_OCC_D(true, true, true);
+  if (mode == kModeStep) return FV_OCC_D(true, true, false);
+  return FV_OCC_D(false, false, false);
+#undef FV_OCC_D
+}
+
+}  // namespace fv

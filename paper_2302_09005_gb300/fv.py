@@ -82,6 +82,10 @@ def _lib() -> ctypes.CDLL:
         L.fv_conserved_totals_noalloc.restype = c_int
         L.fv_time_step.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, vp]
         L.fv_time_step.restype = c_int
+        L.fv_time_step_prim.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i64, dbl, dbl, vp]
+        L.fv_time_step_prim.restype = c_int
+        L.fv_prim_stride.argtypes = [vp, ctypes.POINTER(i64)]
+        L.fv_prim_stride.restype = c_int
         L.fv_run_steps.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, c_int, c_int]
         L.fv_run_steps.restype = c_int
         L.fv_read_dt.argtypes = [vp, ctypes.POINTER(dbl)]
@@ -210,6 +214,20 @@ def fv_time_step(h, in_with_halo, out, patch_offsets, patch_sizes, neighbours, n
                              _ptr(patch_sizes), _ptr(neighbours), n_patches, dx, cfl,
                              _ptr(lambda_patch))
     _check(h, st, "fv_time_step")
+
+
+def fv_prim_stride(h) -> int:
+    out = ctypes.c_int64(0)
+    _check(h, _lib().fv_prim_stride(h, ctypes.byref(out)), "fv_prim_stride")
+    return int(out.value)
+
+
+def fv_time_step_prim(h, in_with_halo, out, prim_in, prim_out, patch_offsets, patch_sizes,
+                      neighbours, n_patches: int, dx: float, cfl: float, lambda_patch=None):
+    st = _lib().fv_time_step_prim(h, _ptr(in_with_halo), _ptr(out), _ptr(prim_in),
+                                  _ptr(prim_out), _ptr(patch_offsets), _ptr(patch_sizes),
+                                  _ptr(neighbours), n_patches, dx, cfl, _ptr(lambda_patch))
+    _check(h, st, "fv_time_step_prim")
 
 
 def fv_run_steps(h, q0, q1, patch_offsets, patch_sizes, neighbours, n_patches: int, dx: float,
@@ -435,6 +453,14 @@ class Batch:
 
     def time_step(self, q_in, q_out, off, sizes, nbr, dx, cfl, lambda_patch=None):
         fv_time_step(self.h, q_in, q_out, off, sizes, nbr, off.numel(), dx, cfl, lambda_patch)
+
+    def time_step_prim(self, q_in, q_out, prim_in, prim_out, off, sizes, nbr, dx, cfl,
+                       lambda_patch=None):
+        fv_time_step_prim(self.h, q_in, q_out, prim_in, prim_out, off, sizes, nbr, off.numel(),
+                          dx, cfl, lambda_patch)
+
+    def prim_stride(self) -> int:
+        return fv_prim_stride(self.h)
 
     def run_steps(self, q0, q1, off, sizes, nbr, dx, cfl, n_steps, use_graph=False):
         fv_run_steps(self.h, q0, q1, off, sizes, nbr, off.numel(), dx, cfl, n_steps, use_graph)

@@ -78,8 +78,8 @@ def fp64_ops_per_patch(d: int, p: int, mode: str = "carry") -> int:
     their Newton refinements: 3 and 5).
       primitives of a cell: 3 (1/rho) + d (u) + d (j.u) + 2 (p) + 1 (E+p)
                             + 2 (c^2) + 5 (sqrt) = 13 + 2d;
-      face flux G:          2 (a) + 1 (p_L+p_R) + 1 (rho) + 2d (momenta)
-                            + 2 (energy) + s (Q_L-Q_R) + s (fma) = 4d + 10;
+      face flux G:          2 (a) + 2 (u_L + a, u_R - a) + 1 (p_L + p_R)
+                            + 2 (rho) + 2d (momenta) + 4 (energy) = 2d + 11;
       cell update:          s (2d) (sum of G_+ - G_- over d directions, fma);
       next-step wave speed: primitives + d adds.
     mode "update": primitives of the interior and face-halo cells, faces,
@@ -90,7 +90,7 @@ def fp64_ops_per_patch(d: int, p: int, mode: str = "carry") -> int:
     halo = 2 * d * p ** (d - 1)
     faces = d * (p + 1) * p ** (d - 1)
     prim = 13 + 2 * d
-    ops = faces * (4 * d + 10) + interior * s * 2 * d
+    ops = faces * (2 * d + 11) + interior * s * 2 * d
     if mode in ("update", "step"):
         ops += (interior + halo) * prim
     if mode in ("step", "carry"):

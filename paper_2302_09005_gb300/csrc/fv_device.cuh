@@ -22,11 +22,17 @@ enum : unsigned int {
 // patterns are exact, order independent, and propagate NaN.  They run on the
 // integer pipe, which keeps the FP64 pipe free.
 // ---------------------------------------------------------------------------
+// The mask is applied in inline PTX: written as C++, the compiler recognises
+// "clear the sign bit" as |x| and spends an FP64 add on it.
 __device__ __forceinline__ unsigned long long order_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long r;
+  asm("and.b64 %0, %1, 0x7FFFFFFFFFFFFFFF;" : "=l"(r) : "l"(__double_as_longlong(x)));
+  return r;
 }
 __device__ __forceinline__ unsigned long long order_bits(float x) {
-  return (unsigned long long)(__float_as_uint(x) & 0x7FFFFFFFu);
+  unsigned int r;
+  asm("and.b32 %0, %1, 0x7FFFFFFF;" : "=r"(r) : "r"(__float_as_uint(x)));
+  return (unsigned long long)r;
 }
 // Value of a maximum taken on order_bits of type T, as a double.
 template <typename T>

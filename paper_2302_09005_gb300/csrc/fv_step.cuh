@@ -443,24 +443,25 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
     const T am = max_by_bits(add_rn(abs_t(uL), cL), add_rn(abs_t(uR), cR));
     const unsigned long long ab = order_bits(am);
     lmax = ab > lmax ? ab : lmax;
-    // f_L + f_R (Eq. 2): j_k; j_m u_k + p delta_mk; (E + p) u_k
-    T jkL = qL[1], jkR = qR[1];
-#pragma unroll
-    for (int m = 1; m < D; ++m) {
-      jkL = (k == m) ? qL[1 + m] : jkL;
-      jkR = (k == m) ? qR[1 + m] : jkR;
-    }
+    // G = f_L + f_R - a (Q_R - Q_L) = (f_L + a Q_L) + (f_R - a Q_R).  The
+    // fluxes of rho and of the momenta are the conserved value times u_k
+    // (Eq. 2: j_k = rho u_k; j_m u_k, plus p on the normal momentum), so
+    // f + a Q folds to Q (u_k + a) (+ p): with s_L = u_L + a, s_R = u_R - a,
+    //   G_rho = rho_L s_L + rho_R s_R,
+    //   G_m   = j_mL s_L + j_mR s_R + (p_L + p_R) [m = k],
+    //   G_E   = (E + p)_L u_L + (E + p)_R u_R + a (E_L - E_R).
+    const T sL = add_rn(uL, am), sR = sub_rn(uR, am);
     const T ps = add_rn(pL, pR);
-    T fs[S];
-    fs[0] = add_rn(jkL, jkR);
+    T gs[S];
+    gs[0] = fma(qL[0], sL, mul_rn(qR[0], sR));
 #pragma unroll
     for (int m = 0; m < D; ++m)
-      fs[1 + m] = fma(qL[1 + m], uL, fma(qR[1 + m], uR, (m == k) ? ps : T(-0.0)));
-    fs[D + 1] = fma(eL, uL, mul_rn(eR, uR));
+      gs[1 + m] = fma(qL[1 + m], sL, fma(qR[1 + m], sR, (m == k) ? ps : T(-0.0)));
+    gs[D + 1] = fma(am, sub_rn(qL[D + 1], qR[D + 1]), fma(eL, uL, mul_rn(eR, uR)));
     T* Gk = G + k * S * nface;
 #pragma unroll
     for (int v = 0; v < S; ++v) {
-      T gv = fma(am, sub_rn(qL[v], qR[v]), fs[v]);
+      T gv = gs[v];
       // learned correction C of this face (G = 2F, so G + 2C = 2(F + C))
       if (a.corr != nullptr)
         gv = add_rn(gv, T(2) * (T)a.corr[i * a.corr_stride + (k * S + v) * nface + j]);

@@ -99,6 +99,38 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
 // ---------------------------------------------------------------------------
+// The adds, subtracts and multiplies of the FP64 kernels as FMAs.  On GB300
+// the FP64 pipe retires DFMA about 1.19 times faster than DADD or DMUL
+// (measured: 0.60 vs 0.50 T instructions/s), and
+//   a + b = fma(a, 1, b),   a - b = fma(b, -1, a),   a * b = fma(a, b, -0)
+// hold bitwise (the product is exact, or the addend -0 leaves it as it is,
+// and there is one rounding), signed zeros included.  The constants 1, -1
+// and -0 come in as kernel arguments: a literal would let the compiler fold
+// the FMA back into the slower instruction.  FP32 keeps plain operations
+// (FADD and FMUL run at the FFMA rate).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Arith {
+  T one, mone, mzero;
+  __device__ __forceinline__ T add(T a, T b) const { return add_rn(a, b); }
+  __device__ __forceinline__ T sub(T a, T b) const { return sub_rn(a, b); }
+  __device__ __forceinline__ T mul(T a, T b) const { return mul_rn(a, b); }
+};
+template <>
+struct Arith<double> {
+  double one, mone, mzero;
+  __device__ __forceinline__ double add(double a, double b) const { return fma(a, one, b); }
+  __device__ __forceinline__ double sub(double a, double b) const { return fma(b, mone, a); }
+  __device__ __forceinline__ double mul(double a, double b) const { return fma(a, b, mzero); }
+};
+// The same operations with literal constants (the compiler may use plain
+// adds and multiplies; the results are the same bits).
+template <typename T>
+__device__ __forceinline__ Arith<T> plain_arith() {
+  return Arith<T>{T(1), T(-1), T(-0.0)};
+}
+
+// ---------------------------------------------------------------------------
 // Reciprocal and square root, once per cell of the interior and face halo.
 //
 // FP64 is the scarce unit on GB300 (two FP64 lanes per SM), so the FP64
@@ -140,7 +172,7 @@ __device__ __forceinline__ double f32_as_f64(float f) {
   return __hiloint2double((int)((e << 20) | ((b & 0x7FFFFFu) >> 3)), (int)((b & 7u) << 29));
 }
 
-__device__ __forceinline__ double recip(double a) {
+__device__ __forceinline__ double recip(double a, const Arith<double>& ar = plain_arith<double>()) {
   float f;
   if (!f64_seed_as_f32(a, f)) return 1.0 / a;
   float rf;
@@ -150,20 +182,24 @@ __device__ __forceinline__ double recip(double a) {
   const double t = fma(e, e, e);
   return fma(y, t, y);
 }
-__device__ __forceinline__ float recip(float a) { return 1.0f / a; }
+__device__ __forceinline__ float recip(float a, const Arith<float>& = plain_arith<float>()) {
+  return 1.0f / a;
+}
 
-__device__ __forceinline__ double sqrt_t(double x) {
+__device__ __forceinline__ double sqrt_t(double x, const Arith<double>& ar = plain_arith<double>()) {
   float f;
   if (!f64_seed_as_f32(x, f)) return sqrt(x);
   float rf;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
   const double r = f32_as_f64(rf);
-  const double s0 = mul_rn(x, r);
+  const double s0 = ar.mul(x, r);
   const double e = fma(neg_t(s0), r, 1.0);
-  const double t = mul_rn(e, fma(e, 0.375, 0.5));
+  const double t = ar.mul(e, fma(e, 0.375, 0.5));
   return fma(s0, t, s0);
 }
-__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ float sqrt_t(float x, const Arith<float>& = plain_arith<float>()) {
+  return sqrtf(x);
+}
 
 // ---------------------------------------------------------------------------
 // Euler physics of one cell, Eq. 2: q = (rho, j_1..j_D, E),
@@ -178,19 +214,20 @@ struct Prim {
 };
 
 template <typename T, int D>
-__device__ __forceinline__ Prim<T, D> primitives(const T* q, T gm1, T gamma, bool& bad) {
+__device__ __forceinline__ Prim<T, D> primitives(const T* q, T gm1, T gamma, bool& bad,
+                                                 const Arith<T>& ar = plain_arith<T>()) {
   Prim<T, D> w;
-  T inv = recip(q[0]);
+  T inv = recip(q[0], ar);
   T jj = T(0);
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    w.u[k] = mul_rn(q[1 + k], inv);
-    jj = k == 0 ? mul_rn(q[1], w.u[0]) : fma(q[1 + k], w.u[k], jj);
+    w.u[k] = ar.mul(q[1 + k], inv);
+    jj = k == 0 ? ar.mul(q[1], w.u[0]) : fma(q[1 + k], w.u[k], jj);
   }
-  w.p = mul_rn(gm1, fma(T(-0.5), jj, q[D + 1]));
-  w.ep = add_rn(q[D + 1], w.p);
-  T c2 = mul_rn(mul_rn(gamma, w.p), inv);
-  w.c = sqrt_t(c2);
+  w.p = ar.mul(gm1, fma(T(-0.5), jj, q[D + 1]));
+  w.ep = ar.add(q[D + 1], w.p);
+  T c2 = ar.mul(ar.mul(gamma, w.p), inv);
+  w.c = sqrt_t(c2, ar);
   bad |= !(positive_finite(q[0]) && positive_finite(w.p));
   return w;
 }

@@ -71,6 +71,7 @@ struct StepParams {
   unsigned int* status;
   const float* corr;    // per-face flux corrections [patch][k][v][face], or null
   int64_t corr_stride;  // floats per patch of corr
+  T one, mone, mzero;  // 1, -1, -0 as arguments (see Arith)
   const T* __restrict__ prim_in;  // carried primitives of `in` (primitive-carry mode)
   T* __restrict__ prim_out;       // primitives of `out` (time-step modes), or null
   int64_t prim_stride;            // elements per patch of prim_in / prim_out
@@ -360,6 +361,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
   const T* __restrict__ st = cur.box;
   T* ip = cur.ip;
   T* hp = cur.hp;
+  const Arith<T> ar{a.one, a.mone, a.mzero};
   bool bad = false;
 
   // ---- cells: primitives of the interior and face-halo cells ---------------
@@ -380,7 +382,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
         T q[S];
 #pragma unroll
         for (int v = 0; v < S; ++v) q[v] = st[cid * S + v];
-        const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
+        const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad, ar);
 #pragma unroll
         for (int m = 0; m < D; ++m) ip[m * nint + t] = w.u[m];
         ip[D * nint + t] = w.p;
@@ -395,7 +397,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
         T q[S];
 #pragma unroll
         for (int v = 0; v < S; ++v) q[v] = st[cid * S + v];
-        const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
+        const Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad, ar);
         T uk = w.u[0];
 #pragma unroll
         for (int m = 1; m < D; ++m) uk = (k == m) ? w.u[m] : uk;
@@ -440,7 +442,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
       qR[v] = st[cr * S + v];
     }
     // a = max(|u_k| + c) over the two cells (Eq. 5)
-    const T am = max_by_bits(add_rn(abs_t(uL), cL), add_rn(abs_t(uR), cR));
+    const T am = max_by_bits(ar.add(abs_t(uL), cL), ar.add(abs_t(uR), cR));
     const unsigned long long ab = order_bits(am);
     lmax = ab > lmax ? ab : lmax;
     // G = f_L + f_R - a (Q_R - Q_L) = (f_L + a Q_L) + (f_R - a Q_R).  The
@@ -450,21 +452,21 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
     //   G_rho = rho_L s_L + rho_R s_R,
     //   G_m   = j_mL s_L + j_mR s_R + (p_L + p_R) [m = k],
     //   G_E   = (E + p)_L u_L + (E + p)_R u_R + a (E_L - E_R).
-    const T sL = add_rn(uL, am), sR = sub_rn(uR, am);
-    const T ps = add_rn(pL, pR);
+    const T sL = ar.add(uL, am), sR = ar.sub(uR, am);
+    const T ps = ar.add(pL, pR);
     T gs[S];
-    gs[0] = fma(qL[0], sL, mul_rn(qR[0], sR));
+    gs[0] = fma(qL[0], sL, ar.mul(qR[0], sR));
 #pragma unroll
     for (int m = 0; m < D; ++m)
       gs[1 + m] = fma(qL[1 + m], sL, fma(qR[1 + m], sR, (m == k) ? ps : T(-0.0)));
-    gs[D + 1] = fma(am, sub_rn(qL[D + 1], qR[D + 1]), fma(eL, uL, mul_rn(eR, uR)));
+    gs[D + 1] = fma(am, ar.sub(qL[D + 1], qR[D + 1]), fma(eL, uL, ar.mul(eR, uR)));
     T* Gk = G + k * S * nface;
 #pragma unroll
     for (int v = 0; v < S; ++v) {
       T gv = gs[v];
       // learned correction C of this face (G = 2F, so G + 2C = 2(F + C))
       if (a.corr != nullptr)
-        gv = add_rn(gv, T(2) * (T)a.corr[i * a.corr_stride + (k * S + v) * nface + j]);
+        gv = ar.add(gv, T(2) * (T)a.corr[i * a.corr_stride + (k * S + v) * nface + j]);
       Gk[v * nface + j] = gv;
     }
   }
@@ -489,8 +491,8 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
       const T* Gk = G + k * S * nface;
 #pragma unroll
       for (int v = 0; v < S; ++v) {
-        const T dG = sub_rn(Gk[v * nface + jm + ptr], Gk[v * nface + jm]);
-        acc[v] = k == 0 ? dG : add_rn(acc[v], dG);
+        const T dG = ar.sub(Gk[v * nface + jm + ptr], Gk[v * nface + jm]);
+        acc[v] = k == 0 ? dG : ar.add(acc[v], dG);
       }
     }
     T qn[S];
@@ -502,10 +504,10 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
     if constexpr (FUSED) {
       // primitives and wave speed of the new state, for the next step's CFL
       // condition (and its primitive carry)
-      const Prim<T, D> w = primitives<T, D>(qn, a.gm1, a.gamma, bad);
+      const Prim<T, D> w = primitives<T, D>(qn, a.gm1, a.gamma, bad, ar);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const unsigned long long lb = order_bits(add_rn(abs_t(w.u[k]), w.c));
+        const unsigned long long lb = order_bits(ar.add(abs_t(w.u[k]), w.c));
         lam_next = lb > lam_next ? lb : lam_next;
       }
       if (a.prim_out != nullptr) {
@@ -746,6 +748,9 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.corr = l.corr;
   a.corr_stride = l.corr_stride;
   a.status = l.status;
+  a.one = T(1);
+  a.mone = T(-1);
+  a.mzero = T(-0.0);
   a.prim_in = static_cast<const T*>(l.prim_in);
   a.prim_out = static_cast<T*>(l.prim_out);
   a.prim_stride = l.prim_stride;

@@ -421,7 +421,8 @@ def _uneven_batch(n: int):
 def batching_variant(args, prec: str, n: int = 200000, steps_per_graph: int = 20,
                      replays: int = 3):
     """Uneven patch sizes (50% 3^3, 30% 5^3, 20% 7^3, shuffled; self-periodic
-    halos): plan + autotune of the schedule, then CUDA graphs of
+    halos): plan + autotune of the per-size CTA size and the schedule, then
+    CUDA graphs of
     `steps_per_graph` fused time steps (plus the halo fill and CFL reduce that
     seed the first step) replayed; cell-updates/s over the replays."""
     import torch
@@ -444,6 +445,7 @@ def batching_variant(args, prec: str, n: int = 200000, steps_per_graph: int = 20
         b.halo_fill(x, toff, tsz, tnbr)
         b.max_eigenvalue(x, toff, tsz, cfl, dx)
     chosen, ms_sched = fv.fv_batch_autotune(b.h, x, y, toff, tsz, tnbr, n, dx, cfl)
+    class_threads = {f"{p}^3": fv.fv_batch_class_threads(b.h, p) for p in (3, 5, 7)}
     x0 = x.clone()
     with torch.cuda.stream(stream):  # capture + first run
         b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps_per_graph, use_graph=True)
@@ -478,6 +480,7 @@ def batching_variant(args, prec: str, n: int = 200000, steps_per_graph: int = 20
             "n_patches": n, "cells_per_step": cells, "dtype": prec,
             "schedule_chosen": names[chosen],
             "ms_per_step_by_schedule": dict(zip(names, ms_sched)),
+            "class_threads_chosen": class_threads,
             "e2e": {"value": steps_per_graph * cells / (ems / 1e3), "unit": UNIT,
                     "h2d_bytes": q.nbytes, "d2h_bytes": q.nbytes}}
 

@@ -271,11 +271,24 @@ fv_status fv_batch_plan(fv_batch* h, const int32_t* patch_sizes, int64_t n_patch
 fv_status fv_batch_set_schedule(fv_batch* h, fv_schedule schedule);
 
 /*
- * fv_batch_autotune -- times the three schedules on the caller's batch (one
- * warm-up and three timed fv_time_step calls each, or fv_patch_update_batch
- * calls with dt = cfl * dx when neighbours is NULL), keeps the fastest in
- * the handle and returns it in *chosen (nullable); ms_per_schedule (host
- * double[3], nullable) receives the average milliseconds of each.
+ * Patch-to-thread mapping of the FV_SCHED_CLASSES launches: one CTA advances
+ * one patch at a time with `threads` threads (32: a warp per patch, 64, 128
+ * or 256: a CTA per patch), set per patch size p (1..max_patch_size).  The
+ * default is 128; d = 1 supports 128 only (FV_ERR_UNSUPPORTED otherwise).
+ * The mapping never changes the results (bitwise).  fv_batch_class_threads
+ * reads the current choice.
+ */
+fv_status fv_batch_set_class_threads(fv_batch* h, int p, int threads);
+fv_status fv_batch_class_threads(const fv_batch* h, int p, int* threads);
+
+/*
+ * fv_batch_autotune -- first picks, for every size class of the batch, the
+ * fastest of the CTA sizes 32, 64, 128 and 256 (one-class launches), then
+ * times the three schedules on the caller's batch (one warm-up and three
+ * timed fv_time_step calls each, or fv_patch_update_batch calls with
+ * dt = cfl * dx when neighbours is NULL), keeps the fastest in the handle and
+ * returns it in *chosen (nullable); ms_per_schedule (host double[3],
+ * nullable) receives the average milliseconds of each.
  * Plans the batch first if needed.  scratch_out is overwritten; the
  * handle's wave speed and time step are restored afterwards.  Synchronises.
  */

@@ -41,7 +41,9 @@ struct fv_batch {
   int ncls = 0;
   int cls_p[64] = {0};
   int64_t cls_begin[64] = {0}, cls_end[64] = {0};
-  int occ_cache[3][64] = {{0}};              // CTAs per SM by (kernel mode, p)
+  int occ_cache[3][64][4] = {{{0}}};         // CTAs per SM by (kernel mode, p, CTA size)
+  int cls_nt[64] = {0};                      // CTA size of the size-class launches (0: 128)
+  int cls_only = -1;                         // autotuner: launch only this class (-1: all)
   int smem_optin = 0;                        // opt-in shared memory per CTA
   char last_error[512] = {0};
 };
@@ -71,6 +73,7 @@ struct UpdateLaunch {
   unsigned int* status = nullptr;
   bool fused = false;  // time-step mode: gather halos, dt from lam_in, reduce lam_next
   int nstage = 0;      // shared-memory stages (0: the handle's)
+  int nt = 128;        // threads per CTA
   const void* prim_in = nullptr;  // time step: carried primitives of `in`, or null
   void* prim_out = nullptr;       // time step: primitives of `out`, or null
   int64_t prim_stride = 0;        // elements per patch of the primitive buffers
@@ -97,13 +100,18 @@ inline int64_t prim_stride_elems(int d, fv_precision prec, int pmax) {
 // Shared memory bytes of the update kernel for patches up to pmax.
 size_t update_smem_bytes(int d, fv_precision prec, int pmax, int nstage);
 cudaError_t launch_update(const fv_batch* h, const UpdateLaunch& a, int grid);
-cudaError_t step_occupancy(const fv_batch* h, int mode, int pmax, int nstage,
+cudaError_t step_occupancy(const fv_batch* h, int mode, int pmax, int nstage, int nt,
                            int* blocks_per_sm);
-// Per-precision launch and occupancy (fv_update.cu: double, fv_update_f32.cu: float).
-template <typename T>
-cudaError_t launch_step_prec(const fv_batch* h, const UpdateLaunch& l, int grid);
-template <typename T>
-cudaError_t occupancy_prec(int d, int mode, int pmax, int nstage, int* bps);
+// Threads per CTA of the step kernel for one launch: 32, 64, 128 or 256.
+inline bool valid_nt(int nt) { return nt == 32 || nt == 64 || nt == 128 || nt == 256; }
+inline int nt_index(int nt) { return nt == 32 ? 0 : nt == 64 ? 1 : nt == 128 ? 2 : 3; }
+// Per-precision, per-CTA-size launch and occupancy (fv_update.cu: double and
+// 128 threads; fv_update_f32.cu: float and 128; fv_update_nt.cu and
+// fv_update_nt_f32.cu: 32, 64 and 256 threads).
+template <typename T, int NT>
+cudaError_t launch_step_nt(const fv_batch* h, const UpdateLaunch& l, int grid);
+template <typename T, int NT>
+cudaError_t occupancy_nt(int d, int mode, int pmax, int nstage, int* bps);
 // Launches the update / time-step kernel(s) under the handle's schedule.
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l);
 // Frees the schedule plan of a handle.

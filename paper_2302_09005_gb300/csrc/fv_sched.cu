@@ -66,16 +66,18 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
   if (h->sched == FV_SCHED_CLASSES && plan_ok) {
     for (int c = 0; c < h->ncls; ++c) {
       const int64_t cnt = h->cls_end[c] - h->cls_begin[c];
-      if (cnt <= 0) continue;
+      if (cnt <= 0 || (h->cls_only >= 0 && c != h->cls_only)) continue;
       UpdateLaunch lc = l;
       lc.order = h->d_order;
       lc.i_begin = h->cls_begin[c];
       lc.i_end = h->cls_end[c];
       lc.pmax = h->cls_p[c];
       lc.nstage = stages_for(h, lc.pmax);
-      int& bps = h->occ_cache[f][lc.pmax < 64 ? lc.pmax : 63];
+      const int pi = lc.pmax < 64 ? lc.pmax : 63;
+      lc.nt = h->cls_nt[pi] > 0 ? h->cls_nt[pi] : 128;
+      int& bps = h->occ_cache[f][pi][nt_index(lc.nt)];
       if (bps == 0) {
-        cudaError_t e = step_occupancy(h, f, lc.pmax, lc.nstage, &bps);
+        cudaError_t e = step_occupancy(h, f, lc.pmax, lc.nstage, lc.nt, &bps);
         if (e != cudaSuccess) return e;
       }
       cudaError_t e = launch_update(h, lc, grid_for(h, cnt, bps));
@@ -85,7 +87,7 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
   }
   int& bps = h->blocks_per_sm[f];
   if (bps == 0) {
-    cudaError_t e = step_occupancy(h, f, h->max_patch_size, h->nstage, &bps);
+    cudaError_t e = step_occupancy(h, f, h->max_patch_size, h->nstage, 128, &bps);
     if (e != cudaSuccess) return e;
   }
   if (h->sched == FV_SCHED_LPT && plan_ok) {
@@ -179,6 +181,23 @@ fv_status fv_batch_set_schedule(fv_batch* h, fv_schedule s) {
   return FV_OK;
 }
 
+fv_status fv_batch_set_class_threads(fv_batch* h, int p, int threads) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  if (p < 1 || p > h->max_patch_size || p >= 64)
+    return sched_err(h, FV_ERR_INVALID_ARG, "patch size outside 1..max_patch_size");
+  if (threads == 0) threads = 128;
+  if (!fv::valid_nt(threads)) return sched_err(h, FV_ERR_INVALID_ARG, "threads: 32, 64, 128, 256");
+  if (h->d == 1 && threads != 128) return sched_err(h, FV_ERR_UNSUPPORTED, "d = 1: 128 threads");
+  h->cls_nt[p] = threads;
+  return FV_OK;
+}
+
+fv_status fv_batch_class_threads(const fv_batch* h, int p, int* threads) {
+  if (!h || !threads || p < 1 || p >= 64) return FV_ERR_INVALID_ARG;
+  *threads = h->cls_nt[p] > 0 ? h->cls_nt[p] : 128;
+  return FV_OK;
+}
+
 fv_status fv_batch_autotune(fv_batch* h, const void* in, void* scratch_out, const int64_t* off,
                             const int32_t* sizes, const int32_t* nbr, int64_t n, double dx,
                             double cfl, fv_schedule* chosen, double* ms_per_schedule) {
@@ -201,13 +220,12 @@ fv_status fv_batch_autotune(fv_batch* h, const void* in, void* scratch_out, cons
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
   const int saved = h->sched;
-  double best = 1e300;
-  int best_s = saved;
   fv_status st = FV_OK;
-  for (int s = 0; s < 3 && st == FV_OK; ++s) {
-    h->sched = s;
+  // average ms of three timed calls after one warm-up, under the current
+  // schedule (and class restriction)
+  auto time_calls = [&](double* avg) {
     float ms_total = 0.f;
-    for (int rep = 0; rep < 4 && st == FV_OK; ++rep) {  // one warm-up, three timed
+    for (int rep = 0; rep < 4 && st == FV_OK; ++rep) {
       h->lam_cur = lam0;
       e = cudaMemcpyAsync(&h->d_lam[lam0], backup, 8, cudaMemcpyDeviceToDevice, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
@@ -225,7 +243,37 @@ fv_status fv_batch_autotune(fv_batch* h, const void* in, void* scratch_out, cons
       if (e != cudaSuccess && st == FV_OK) st = sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
       if (rep > 0) ms_total += ms;
     }
-    const double avg = ms_total / 3.0;
+    *avg = ms_total / 3.0;
+  };
+  // 1. the CTA size of each size class (one-class launches)
+  h->sched = FV_SCHED_CLASSES;
+  for (int c = 0; c < h->ncls && st == FV_OK; ++c) {
+    const int pi = h->cls_p[c] < 64 ? h->cls_p[c] : 63;
+    const int keep = h->cls_nt[pi];
+    double best_c = 1e300;
+    int best_nt = keep;
+    h->cls_only = c;
+    for (int nt : {32, 64, 128, 256}) {
+      if (h->d == 1 && nt != 128) continue;
+      h->cls_nt[pi] = nt;
+      double avg = 0;
+      time_calls(&avg);
+      if (st == FV_OK && avg < best_c) {
+        best_c = avg;
+        best_nt = nt;
+      }
+    }
+    h->cls_nt[pi] = best_nt;
+    h->cls_only = -1;
+  }
+  h->cls_only = -1;
+  // 2. the schedule
+  double best = 1e300;
+  int best_s = saved;
+  for (int s = 0; s < 3 && st == FV_OK; ++s) {
+    h->sched = s;
+    double avg = 0;
+    time_calls(&avg);
     if (ms_per_schedule) ms_per_schedule[s] = avg;
     if (st == FV_OK && avg < best) {
       best = avg;

@@ -124,12 +124,15 @@ struct FaceSrc {
   int pad;
 };
 
+// Threads per CTA the kernel is built for: one CTA advances one patch at a
+// time; small patches use a warp or two, the largest eight warps.
+constexpr int kMaxNT = 256;
 // Shared-memory header: two mbarriers (16 B), per-warp reduction slots, and
 // the face sources of the two stages (2 x 6 x 24 B).
 constexpr int kRedOff = 16;
-constexpr int kFaceSrcOff = 64;
-constexpr int kHdrBytes = 384;
-static_assert(kRedOff + 8 * (FV_NT / 32) <= kFaceSrcOff, "header too small");
+constexpr int kFaceSrcOff = 128;
+constexpr int kHdrBytes = 512;
+static_assert(kRedOff + 8 * (kMaxNT / 32) <= kFaceSrcOff, "header too small");
 static_assert(kFaceSrcOff + 2 * 6 * (int)sizeof(FaceSrc) <= kHdrBytes, "header too small");
 
 // Shared-memory carve-up for patches up to pmax (element counts of T).  A
@@ -244,7 +247,7 @@ __device__ __forceinline__ void face_sources(const StepParams<T>& a, int64_t j, 
 // copies (a wall's negated normal momentum with a plain load and store); when
 // primitives are carried, also the face-halo primitives (u_normal, p, c,
 // E + p) from the sources' carried blocks (a wall negates u_normal).
-template <typename T, int D, int P, bool GATHER, bool PRIMIN>
+template <typename T, int D, int P, bool GATHER, bool PRIMIN, int NT>
 __device__ __forceinline__ void gather_halo(const StepParams<T>& a, int pj, const Stage<T>& s,
                                             const FaceSrc* fs) {
   if constexpr (!GATHER && D != 1) return;
@@ -252,7 +255,7 @@ __device__ __forceinline__ void gather_halo(const StepParams<T>& a, int pj, cons
   const Geom<D, P> g(pj);
   const int p = g.p;
   const int ptr = g.ptrans();
-  for (int hc = threadIdx.x; hc < 2 * D * ptr; hc += FV_NT) {
+  for (int hc = threadIdx.x; hc < 2 * D * ptr; hc += NT) {
     const int f = hc / ptr;
     const int r = hc - f * ptr;
     const int k = f >> 1;
@@ -283,27 +286,30 @@ __device__ __forceinline__ void gather_halo(const StepParams<T>& a, int pj, cons
   cp_async_commit();
 }
 
-template <typename T, int D, bool GATHER, bool PRIMIN>
+// Patch sizes with a compile-time specialisation, per CTA size: the common
+// sizes for 128 threads, small ones for one or two warps, large ones for 256.
+template <int D, int NT>
+__host__ __device__ constexpr bool specialised(int p) {
+  if (D == 1) return false;
+  if (NT <= 64) return D == 3 ? p == 3 : (p == 3 || p == 5 || p == 8);
+  if (NT >= 256) return D == 3 ? p == 7 : p == 17;
+  return D == 3 ? (p == 3 || p == 5 || p == 7) : (p == 3 || p == 5 || p == 8 || p == 17);
+}
+
+template <typename T, int D, bool GATHER, bool PRIMIN, int NT>
 __device__ __forceinline__ void gather_dispatch(const StepParams<T>& a, int pj,
                                                 const Stage<T>& s, const FaceSrc* fs) {
   if constexpr (!GATHER && D != 1) return;
-  if constexpr (D == 3) {
-    switch (pj) {
-      case 3: gather_halo<T, D, 3, GATHER, PRIMIN>(a, pj, s, fs); return;
-      case 5: gather_halo<T, D, 5, GATHER, PRIMIN>(a, pj, s, fs); return;
-      case 7: gather_halo<T, D, 7, GATHER, PRIMIN>(a, pj, s, fs); return;
-      default: gather_halo<T, D, 0, GATHER, PRIMIN>(a, pj, s, fs); return;
-    }
-  } else if constexpr (D == 2) {
-    switch (pj) {
-      case 3: gather_halo<T, D, 3, GATHER, PRIMIN>(a, pj, s, fs); return;
-      case 5: gather_halo<T, D, 5, GATHER, PRIMIN>(a, pj, s, fs); return;
-      case 8: gather_halo<T, D, 8, GATHER, PRIMIN>(a, pj, s, fs); return;
-      default: gather_halo<T, D, 0, GATHER, PRIMIN>(a, pj, s, fs); return;
-    }
-  } else {
-    gather_halo<T, D, 0, GATHER, PRIMIN>(a, pj, s, fs);
+#define FV_GH(PP)                                                               \
+  if constexpr (specialised<D, NT>(PP)) {                                       \
+    if (pj == PP) return gather_halo<T, D, PP, GATHER, PRIMIN, NT>(a, pj, s, fs); \
   }
+  FV_GH(3)
+  FV_GH(5)
+  FV_GH(7)
+  FV_GH(8)
+  gather_halo<T, D, 0, GATHER, PRIMIN, NT>(a, pj, s, fs);
+#undef FV_GH
 }
 
 // State of the copy pipeline of one CTA.
@@ -327,7 +333,7 @@ struct NextPatch {
 
 // Inside a patch, after a barrier: wait for the bulk copy of the next patch
 // and start its halo gather, so both overlap the rest of this patch.
-template <typename T, int D, bool GATHER, bool PRIMIN>
+template <typename T, int D, bool GATHER, bool PRIMIN, int NT>
 __device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
                                          const NextPatch<T>& nx) {
   if (nx.j >= a.i_end) return;
@@ -340,20 +346,19 @@ __device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
     pp.timeout = true;
     return;
   }
-  gather_dispatch<T, D, GATHER, PRIMIN>(a, nx.p, nx.st, nx.fs);
+  gather_dispatch<T, D, GATHER, PRIMIN, NT>(a, nx.p, nx.st, nx.fs);
 }
 
 // ---------------------------------------------------------------------------
 // One patch: cells, faces, update.
 // ---------------------------------------------------------------------------
-template <typename T, int D, int P, bool GATHER, bool FUSED, bool PRIMIN>
+template <typename T, int D, int P, bool GATHER, bool FUSED, bool PRIMIN, int NT>
 __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, int64_t i,
                                               int64_t off, const Stage<T>& cur, T* G, T mhr,
                                               unsigned long long* red,
                                               unsigned long long& lam_next, Pipe& pp,
                                               const NextPatch<T>& nx) {
   constexpr int S = D + 2;
-  constexpr int NT = FV_NT;
   const Geom<D, P> g(p_rt);
   const int p = g.p;
   const int nface = g.nface(), nint = g.nint(), ptr = g.ptrans();
@@ -409,7 +414,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
       }
     }
     __syncthreads();
-    mid_hook<T, D, GATHER, PRIMIN>(a, pp, nx);
+    mid_hook<T, D, GATHER, PRIMIN, NT>(a, pp, nx);
   }
 
   // ---- faces: G = f_L + f_R - a (Q_R - Q_L), once per face -------------------
@@ -471,7 +476,7 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
     }
   }
   __syncthreads();
-  if constexpr (PRIMIN) mid_hook<T, D, GATHER, PRIMIN>(a, pp, nx);
+  if constexpr (PRIMIN) mid_hook<T, D, GATHER, PRIMIN, NT>(a, pp, nx);
 
   // ---- update: Q - (dt/2dx) sum_k (G_+ - G_-) -----------------------------------
   T* dst_base = a.out + off;
@@ -535,45 +540,44 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
   }
 }
 
-template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN, int NT>
 __device__ __forceinline__ void patch_dispatch(const StepParams<T>& a, int p, int64_t i,
                                                int64_t off, const Stage<T>& st, T* G, T hr,
                                                unsigned long long* red,
                                                unsigned long long& lam_next, Pipe& pp,
                                                const NextPatch<T>& nx) {
-#define FV_PC(PP) \
-  patch_compute<T, D, PP, GATHER, FUSED, PRIMIN>(a, p, i, off, st, G, hr, red, lam_next, pp, nx)
-  if constexpr (D == 3) {
-    switch (p) {
-      case 3: FV_PC(3); return;
-      case 5: FV_PC(5); return;
-      case 7: FV_PC(7); return;
-      default: FV_PC(0); return;
-    }
-  } else if constexpr (D == 2) {
-    switch (p) {
-      case 3: FV_PC(3); return;
-      case 5: FV_PC(5); return;
-      case 8: FV_PC(8); return;
-      case 17: FV_PC(17); return;
-      default: FV_PC(0); return;
-    }
-  } else {
-    FV_PC(0);
+#define FV_PC(PP)                                                                           \
+  if constexpr (specialised<D, NT>(PP)) {                                                   \
+    if (p == PP)                                                                            \
+      return patch_compute<T, D, PP, GATHER, FUSED, PRIMIN, NT>(a, p, i, off, st, G, hr, red, \
+                                                                lam_next, pp, nx);          \
   }
+  FV_PC(3)
+  FV_PC(5)
+  FV_PC(7)
+  FV_PC(8)
+  FV_PC(17)
+  patch_compute<T, D, 0, GATHER, FUSED, PRIMIN, NT>(a, p, i, off, st, G, hr, red, lam_next, pp,
+                                                    nx);
 #undef FV_PC
 }
 
-// Resident CTAs per SM the register allocation is sized for.
+// Resident CTAs per SM the register allocation is sized for, given as the
+// resident threads per SM (3 CTAs of 128 threads for FP64, 6 for FP32).
 #ifndef FV_MINBLOCKS_FP64
 #define FV_MINBLOCKS_FP64 3
 #endif
 #ifndef FV_MINBLOCKS_FP32
 #define FV_MINBLOCKS_FP32 6
 #endif
+template <typename T, int NT>
+constexpr int min_blocks() {
+  const int threads = 128 * (sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV_MINBLOCKS_FP32);
+  return threads / NT > 0 ? threads / NT : 1;
+}
 
-template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
-__global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV_MINBLOCKS_FP32)
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN, int NT>
+__global__ void __launch_bounds__(NT, (min_blocks<T, NT>()))
     step_kernel(StepParams<T> a) {
   static_assert(!PRIMIN || (GATHER && FUSED), "the primitive carry is a time-step mode");
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -634,7 +638,7 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV
     if (ok) {
       pp.parity ^= 1u;
       pp.pending = 0u;
-      gather_dispatch<T, D, GATHER, PRIMIN>(a, pc, stage_at(0), fsrc);
+      gather_dispatch<T, D, GATHER, PRIMIN, NT>(a, pc, stage_at(0), fsrc);
     } else {
       pp.timeout = true;
     }
@@ -660,14 +664,14 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV
       if (tid == 0) issue_stage<T, D, PRIMIN>(a, nx.pid, nx.p, nx.off, nx.st, &bar[nx.slot]);
       pp.pending |= 1u << nx.slot;
     }
-    patch_dispatch<T, D, GATHER, FUSED, PRIMIN>(a, pc, pidc, oc, stage_at(s), G, hr, red,
-                                                lam_next, pp, nx_mid);
+    patch_dispatch<T, D, GATHER, FUSED, PRIMIN, NT>(a, pc, pidc, oc, stage_at(s), G, hr, red,
+                                                    lam_next, pp, nx_mid);
     cp_async_wait_all();
     if (__syncthreads_or(pp.timeout)) break;
     if (single && nx.j < a.i_end) {
       if (tid == 0) issue_stage<T, D, PRIMIN>(a, nx.pid, nx.p, nx.off, nx.st, &bar[0]);
       pp.pending |= 1u;
-      mid_hook<T, D, GATHER, PRIMIN>(a, pp, nx);
+      mid_hook<T, D, GATHER, PRIMIN, NT>(a, pp, nx);
       cp_async_wait_all();
       if (__syncthreads_or(pp.timeout)) break;
     }
@@ -693,7 +697,7 @@ __global__ void __launch_bounds__(FV_NT, sizeof(T) == 8 ? FV_MINBLOCKS_FP64 : FV
     if (tid == 0) {
       unsigned long long m = red[0];
 #pragma unroll
-      for (int w = 1; w < FV_NT / 32; ++w) m = red[w] > m ? red[w] : m;
+      for (int w = 1; w < NT / 32; ++w) m = red[w] > m ? red[w] : m;
       atomicMax(a.lam_next, m);
     }
   }
@@ -707,20 +711,20 @@ inline size_t step_smem_bytes(int es, int pmax, int nstage) {
 
 // Raises the kernel's dynamic shared-memory limit on the current device once
 // (not per launch, so launches can be captured into CUDA graphs).
-template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN, int NT>
 static cudaError_t ensure_smem(size_t smem) {
   static int set_bytes[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && set_bytes[dev] >= (int)smem) return cudaSuccess;
-  e = cudaFuncSetAttribute(step_kernel<T, D, GATHER, FUSED, PRIMIN>,
+  e = cudaFuncSetAttribute(step_kernel<T, D, GATHER, FUSED, PRIMIN, NT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess && dev >= 0 && dev < 64) set_bytes[dev] = (int)smem;
   return e;
 }
 
-template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN, int NT>
 static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int grid) {
   StepParams<T> a;
   a.in = static_cast<const T*>(l.in);
@@ -755,45 +759,53 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.prim_out = static_cast<T*>(l.prim_out);
   a.prim_stride = l.prim_stride;
   const size_t smem = step_smem_bytes<D>((int)sizeof(T), l.pmax, a.nstage);
-  cudaError_t e = ensure_smem<T, D, GATHER, FUSED, PRIMIN>(smem);
+  cudaError_t e = ensure_smem<T, D, GATHER, FUSED, PRIMIN, NT>(smem);
   if (e != cudaSuccess) return e;
-  step_kernel<T, D, GATHER, FUSED, PRIMIN><<<grid, FV_NT, smem, h->stream>>>(a);
+  step_kernel<T, D, GATHER, FUSED, PRIMIN, NT><<<grid, NT, smem, h->stream>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN>
+template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN, int NT>
 static cudaError_t occupancy_t(int pmax, int nstage, int* bps) {
   const size_t smem = step_smem_bytes<D>((int)sizeof(T), pmax, nstage);
-  cudaError_t e = ensure_smem<T, D, GATHER, FUSED, PRIMIN>(smem);
+  cudaError_t e = ensure_smem<T, D, GATHER, FUSED, PRIMIN, NT>(smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      bps, step_kernel<T, D, GATHER, FUSED, PRIMIN>, FV_NT, smem);
+      bps, step_kernel<T, D, GATHER, FUSED, PRIMIN, NT>, NT, smem);
 }
 
-// Launch / occupancy of one precision, dispatched over d and the mode.
-template <typename T>
-cudaError_t launch_step_prec(const fv_batch* h, const UpdateLaunch& l, int grid) {
+// Launch / occupancy of one precision and CTA size, dispatched over d and
+// the mode (explicitly instantiated in the fv_update*.cu translation units).
+// d = 1 is built for 128 threads only.
+template <typename T, int NT, bool G_, bool F_, bool P_>
+static cudaError_t launch_by_d(const fv_batch* h, const UpdateLaunch& l, int grid) {
+  if (h->d == 2) return launch_step_t<T, 2, G_, F_, P_, NT>(h, l, grid);
+  if (h->d == 3) return launch_step_t<T, 3, G_, F_, P_, NT>(h, l, grid);
+  if constexpr (NT == 128) return launch_step_t<T, 1, G_, F_, P_, NT>(h, l, grid);
+  return cudaErrorInvalidConfiguration;
+}
+
+template <typename T, int NT, bool G_, bool F_, bool P_>
+static cudaError_t occupancy_by_d(int d, int pmax, int nstage, int* bps) {
+  if (d == 2) return occupancy_t<T, 2, G_, F_, P_, NT>(pmax, nstage, bps);
+  if (d == 3) return occupancy_t<T, 3, G_, F_, P_, NT>(pmax, nstage, bps);
+  if constexpr (NT == 128) return occupancy_t<T, 1, G_, F_, P_, NT>(pmax, nstage, bps);
+  return cudaErrorInvalidConfiguration;
+}
+
+template <typename T, int NT>
+cudaError_t launch_step_nt(const fv_batch* h, const UpdateLaunch& l, int grid) {
   const int mode = step_mode(l);
-#define FV_LAUNCH_D(G_, F_, P_)                                           \
-  (h->d == 1   ? launch_step_t<T, 1, G_, F_, P_>(h, l, grid)              \
-   : h->d == 2 ? launch_step_t<T, 2, G_, F_, P_>(h, l, grid)              \
-               : launch_step_t<T, 3, G_, F_, P_>(h, l, grid))
-  if (mode == kModePrim) return FV_LAUNCH_D(true, true, true);
-  if (mode == kModeStep) return FV_LAUNCH_D(true, true, false);
-  return FV_LAUNCH_D(false, false, false);
-#undef FV_LAUNCH_D
+  if (mode == kModePrim) return launch_by_d<T, NT, true, true, true>(h, l, grid);
+  if (mode == kModeStep) return launch_by_d<T, NT, true, true, false>(h, l, grid);
+  return launch_by_d<T, NT, false, false, false>(h, l, grid);
 }
 
-template <typename T>
-cudaError_t occupancy_prec(int d, int mode, int pmax, int nstage, int* bps) {
-#define FV_OCC_D(G_, F_, P_)                                            \
-  (d == 1   ? occupancy_t<T, 1, G_, F_, P_>(pmax, nstage, bps)          \
-   : d == 2 ? occupancy_t<T, 2, G_, F_, P_>(pmax, nstage, bps)          \
-            : occupancy_t<T, 3, G_, F_, P_>(pmax, nstage, bps))
-  if (mode == kModePrim) return FV_OCC_D(true, true, true);
-  if (mode == kModeStep) return FV_OCC_D(true, true, false);
-  return FV_OCC_D(false, false, false);
-#undef FV_OCC_D
+template <typename T, int NT>
+cudaError_t occupancy_nt(int d, int mode, int pmax, int nstage, int* bps) {
+  if (mode == kModePrim) return occupancy_by_d<T, NT, true, true, true>(d, pmax, nstage, bps);
+  if (mode == kModeStep) return occupancy_by_d<T, NT, true, true, false>(d, pmax, nstage, bps);
+  return occupancy_by_d<T, NT, false, false, false>(d, pmax, nstage, bps);
 }
 
 }  // namespace fv

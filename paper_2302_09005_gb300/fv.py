@@ -94,6 +94,10 @@ def _lib() -> ctypes.CDLL:
         L.fv_batch_plan.restype = c_int
         L.fv_batch_set_schedule.argtypes = [vp, c_int]
         L.fv_batch_set_schedule.restype = c_int
+        L.fv_batch_set_class_threads.argtypes = [vp, c_int, c_int]
+        L.fv_batch_set_class_threads.restype = c_int
+        L.fv_batch_class_threads.argtypes = [vp, c_int, ctypes.POINTER(c_int)]
+        L.fv_batch_class_threads.restype = c_int
         L.fv_batch_autotune.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl,
                                         ctypes.POINTER(c_int), ctypes.POINTER(dbl)]
         L.fv_batch_autotune.restype = c_int
@@ -275,6 +279,16 @@ def fv_batch_plan(h, patch_sizes, n_patches: int):
 
 def fv_batch_set_schedule(h, schedule: int):
     _check(h, _lib().fv_batch_set_schedule(h, schedule), "fv_batch_set_schedule")
+
+
+def fv_batch_set_class_threads(h, p: int, threads: int):
+    _check(h, _lib().fv_batch_set_class_threads(h, p, threads), "fv_batch_set_class_threads")
+
+
+def fv_batch_class_threads(h, p: int) -> int:
+    out = ctypes.c_int(0)
+    _check(h, _lib().fv_batch_class_threads(h, p, ctypes.byref(out)), "fv_batch_class_threads")
+    return int(out.value)
 
 
 def fv_batch_autotune(h, in_with_halo, scratch_out, patch_offsets, patch_sizes, neighbours,

@@ -136,3 +136,67 @@ def test_classes_schedule_flags_rejected_sizes(fv):
     ne = (sz[7] + 2) ** 3 * 5
     assert np.array_equal(out[off[7]:off[7] + ne].cpu().numpy(), q[off[7]:off[7] + ne])
     b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("d", [2, 3])
+def test_class_thread_mappings_bitwise_equal(fv, prec, d):
+    """Every CTA size of the size-class launches (a warp per patch up to
+    eight warps per patch) gives bitwise the same steps, in all three kernel
+    modes (update, time step, time step with the primitive carry)."""
+    torch = fvtest.torch_cuda()
+    n = 700
+    mix = ((3, 0.4), (5, 0.3), (7, 0.2), (4, 0.1)) if d == 3 else \
+        ((3, 0.3), (5, 0.3), (8, 0.2), (17, 0.1), (6, 0.1))
+    pmax = 7 if d == 3 else 17
+    sizes = inputs.uneven_sizes(n, seed=55, mix=mix)
+    dtype = np.float32 if prec else np.float64
+    q, off, sz = inputs.random_batch(n, sizes, d, seed=55, dtype=dtype)
+    nbr = inputs.self_periodic_neighbours(n, d)
+    toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
+    dx, cfl = 0.01, 0.4
+    mask = fvtest.interior_mask(off, sz, d, d + 2, len(q))
+    ref = None
+    for nt in (128, 32, 64, 256):
+        b = fv.Batch(d, precision=prec, max_patch_size=pmax)
+        fv.fv_batch_plan(b.h, tsz, n)
+        fv.fv_batch_set_schedule(b.h, fv.FV_SCHED_CLASSES)
+        for p, _ in mix:
+            fv.fv_batch_set_class_threads(b.h, p, nt)
+            assert fv.fv_batch_class_threads(b.h, p) == nt
+        x, y = fvtest.to_dev(q), fvtest.to_dev(q)
+        pa = torch.empty(n * b.prim_stride(), dtype=x.dtype, device="cuda")
+        pb = torch.empty_like(pa)
+        lam = torch.zeros(n, dtype=torch.float64, device="cuda")
+        u = x.clone()
+        b.update(x, u, toff, tsz, dx, 0.001, lambda_patch=lam)
+        b.halo_fill(x, toff, tsz, tnbr)
+        b.max_eigenvalue(x, toff, tsz, cfl, dx)
+        b.time_step_prim(x, y, None, pa, toff, tsz, tnbr, dx, cfl)
+        b.time_step_prim(y, x, pa, pb, toff, tsz, tnbr, dx, cfl)
+        assert b.status() == fv.FV_OK
+        got = (u.cpu().numpy()[mask], lam.cpu().numpy(), x.cpu().numpy()[mask],
+               fv.fv_read_dt(b.h))
+        b.close()
+        if ref is None:
+            ref = got
+            continue
+        assert np.array_equal(got[0], ref[0]), nt
+        assert np.array_equal(got[1], ref[1]), nt
+        assert np.array_equal(got[2], ref[2]), nt
+        assert got[3] == ref[3]
+
+
+def test_class_threads_arguments_are_checked(fv):
+    b = fv.Batch(3, max_patch_size=7)
+    for p, nt, status in ((0, 128, fv.FV_ERR_INVALID_ARG), (8, 128, fv.FV_ERR_INVALID_ARG),
+                          (5, 96, fv.FV_ERR_INVALID_ARG)):
+        with pytest.raises(fv.FvError) as e:
+            fv.fv_batch_set_class_threads(b.h, p, nt)
+        assert e.value.status == status
+    b.close()
+    b1 = fv.Batch(1, max_patch_size=8)
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_batch_set_class_threads(b1.h, 4, 32)
+    assert e.value.status == fv.FV_ERR_UNSUPPORTED
+    b1.close()

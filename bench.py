@@ -346,6 +346,7 @@ def run_ours(args, ws, rank, local):
         variants["batching_uneven_fp32"] = batching_variant(args, "f32")
         variants["precision_2d_4095"] = precision_variant(args)
         variants["learned_correction_1024"] = learned_variant(args)
+        variants["paper_shape_2d_p17_sweep"] = sweep_variant(args)
 
     peaks, peak_src = _peaks()
     if prec == "f64":
@@ -483,6 +484,64 @@ def batching_variant(args, prec: str, n: int = 200000, steps_per_graph: int = 20
             "class_threads_chosen": class_threads,
             "e2e": {"value": steps_per_graph * cells / (ems / 1e3), "unit": UNIT,
                     "h2d_bytes": q.nbytes, "d2h_bytes": q.nbytes}}
+
+
+def sweep_variant(args, p: int = 17, ns=(1, 4, 16, 64, 256, 1024, 4096, 16384, 65536),
+                  reps: int = 20):
+    """The paper's own benchmark shape: 2D Euler, patches of 17 x 17, N patches
+    per kernel invocation for a range of N; time per finite-volume (cell)
+    update, with the host<->device transfers of the batch included (as in the
+    paper's figure) and device-resident.  FP64, i.i.d. random states in every
+    cell (halos included), one fv_patch_update_batch per invocation."""
+    import torch
+    from paper_2302_09005_gb300 import fv, inputs
+    d = 2
+    stream = torch.cuda.Stream()
+    b = fv.Batch(d, max_patch_size=p, stream=stream)
+    dx, dt = 1.0 / 1024, 1e-4
+    rows = []
+    for n in ns:
+        q, off, sz = inputs.random_batch(n, p, d, seed=5)
+        hq = torch.from_numpy(q).pin_memory()
+        hout = torch.empty_like(hq).pin_memory()
+        x = hq.to("cuda")
+        y = x.clone()
+        toff, tsz = torch.from_numpy(off).cuda(), torch.from_numpy(sz).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                x.copy_(hq, non_blocking=True)
+                b.update(x, y, toff, tsz, dx, dt)
+                hout.copy_(y, non_blocking=True)
+        stream.synchronize()
+        e = _events(2)
+        with torch.cuda.stream(stream):
+            e[0][0].record(stream)
+            for _ in range(reps):
+                x.copy_(hq, non_blocking=True)
+                b.update(x, y, toff, tsz, dx, dt)
+                hout.copy_(y, non_blocking=True)
+            e[0][1].record(stream)
+            e[1][0].record(stream)
+            for _ in range(reps):
+                b.update(x, y, toff, tsz, dx, dt)
+            e[1][1].record(stream)
+        stream.synchronize()
+        cells = n * p ** d
+        ms_x = e[0][0].elapsed_time(e[0][1]) / reps
+        ms_d = e[1][0].elapsed_time(e[1][1]) / reps
+        rows.append({"N": n, "ns_per_cell_update_with_transfers": ms_x * 1e6 / cells,
+                     "ns_per_cell_update_device": ms_d * 1e6 / cells,
+                     "us_per_invocation_with_transfers": ms_x * 1e3,
+                     "us_per_invocation_device": ms_d * 1e3,
+                     "bytes_each_way": int(q.nbytes)})
+        del x, y, hq, hout
+    ok = b.status() == fv.FV_OK
+    b.close()
+    return {"what": "2D Euler FP64, p = 17, N patches per fv_patch_update_batch; time per "
+                    "cell update with host->device and device->host copies of the batch "
+                    "inside the timed region, and device-resident",
+            "status_ok": ok, "rows": rows}
 
 
 def precision_variant(args, N: int = 4095, p: int = 5, steps: int = 100):
@@ -735,22 +794,48 @@ def _traffic(workload):
     return None
 
 
-def cpu_baseline(workload: str, sample: int):
-    """The oracle as it stands, single-threaded, on the first ``sample``
-    patches of the same workload: CFL reduce + update (Eq. 3-5)."""
+def _oracle_step(q, off, sz, d, dx, cfl, threads: int):
+    """One oracle step (max-eigenvalue reduce, CFL dt, update) over the
+    patches, the patches split into `threads` contiguous chunks run by host
+    threads (the oracle's C calls release the interpreter lock); the oracle's
+    code is the same for any split."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    n = len(off)
+    bounds = [(n * k) // threads for k in range(threads + 1)]
+    chunks = [(bounds[k], bounds[k + 1]) for k in range(threads) if bounds[k + 1] > bounds[k]]
+    out = q.copy()
+    with ThreadPoolExecutor(max_workers=len(chunks)) as ex:
+        lams = list(ex.map(lambda c: oracle.max_eigenvalue(q, off[c[0]:c[1]], sz[c[0]:c[1]],
+                                                           d)[1], chunks))
+        dt = oracle.cfl_dt(max(lams), cfl, dx, d)
+        list(ex.map(lambda c: oracle.patch_update(q, off[c[0]:c[1]], sz[c[0]:c[1]], d, dx, dt,
+                                                  q_out=out), chunks))
+    return out
+
+
+def cpu_baseline(workload: str, sample: int):
+    """The oracle as it stands on the first ``sample`` patches of the same
+    workload, one step (CFL reduce + update, Eq. 3-5): on every host core
+    (patches split across threads), and on one core."""
     d, p, n, grid, prec = WORKLOADS[workload]
     from paper_2302_09005_gb300 import inputs
-    q, off, sz = inputs.random_batch(sample, p, d, seed=0)
+    multi = min(n, 4 * sample)  # all cores: a larger sample
+    q, off, sz = inputs.random_batch(multi, p, d, seed=0)
     dx, cfl = 1.0 / (grid[0] * p), 0.4
+    cores = os.cpu_count() or 1
     t = time.perf_counter()
-    _, lam = oracle.max_eigenvalue(q, off, sz, d)
-    dt = oracle.cfl_dt(lam, cfl, dx, d)
-    oracle.patch_update(q, off, sz, d, dx, dt)
+    _oracle_step(q, off, sz, d, dx, cfl, cores)
     el = time.perf_counter() - t
-    return {"value": sample * p ** d / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample} of {n} patches ({p}^{d}, FP64): max-eigenvalue reduce + "
-                      f"update, one step, {el:.2f} s"}
+    single = max(1, sample // 2)
+    t = time.perf_counter()
+    _oracle_step(q, off[:single], sz[:single], d, dx, cfl, 1)
+    el1 = time.perf_counter() - t
+    return {"value": multi * p ** d / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{multi} of {n} patches ({p}^{d}, FP64): max-eigenvalue reduce + "
+                      f"update, one step, {el:.2f} s on {cores} threads",
+            "single_core": {"value": single * p ** d / el1, "patches": single,
+                            "seconds": el1}}
 
 
 def run_reference(args, ws, rank):
@@ -765,11 +850,10 @@ def run_reference(args, ws, rank):
     sample = args.cpu_sample
     q, off, sz = inputs.random_batch(sample, p, d, seed=0)
     dx, cfl = 1.0 / (grid[0] * p), 0.4
+    cores = os.cpu_count() or 1
 
     def one():
-        _, lam = oracle.max_eigenvalue(q, off, sz, d)
-        dt = oracle.cfl_dt(lam, cfl, dx, d)
-        oracle.patch_update(q, off, sz, d, dx, dt)
+        _oracle_step(q, off, sz, d, dx, cfl, cores)
 
     for _ in range(args.warmup):
         one()
@@ -783,8 +867,9 @@ def run_reference(args, ws, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "d": d, "patch": p, "n_patches_per_gpu": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{sample} of {n} patches per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} of {n} patches per step, patches split "
+                                       f"across {cores} host threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -801,7 +886,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--variant", choices=["batching", "precision", "learned"], default=None,
+    ap.add_argument("--variant", choices=["batching", "precision", "learned", "sweep"],
+                    default=None,
                     help="run one variant on its own")
     ap.add_argument("--small", action="store_true", help="small case of --variant")
     args = ap.parse_args()
@@ -828,6 +914,9 @@ def run_variant(args):
     elif args.variant == "precision":
         res = precision_variant(args, N=1020 if args.small else 4095,
                                 steps=10 if args.small else 100)
+    elif args.variant == "sweep":
+        res = sweep_variant(args, ns=(1, 16, 256, 4096) if args.small else
+                            (1, 4, 16, 64, 256, 1024, 4096, 16384, 65536))
     elif args.variant == "learned":
         res = (learned_variant(args, Nc=256, steps=4, train_steps=200, batch=8192)
                if args.small else learned_variant(args))

@@ -174,6 +174,26 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
                                    double cfl, double dx, double* dt_out);
 
 /*
+ * fv_patch_update_local -- fv_patch_update_batch with a cell size and a time
+ * step per patch (the batch descriptor of Sec. 3 carries both per patch):
+ * patch i advances with Q - (dt_i / dx_i) sum (F_+ - F_-) (Eq. 3).
+ *   dx_patch      device double[n_patches]: cell size of each patch (> 0).
+ *   dt_patch      device double[n_patches]: with cfl <= 0 the time step of
+ *                 each patch (input); with cfl > 0 each patch takes its own
+ *                 CFL step dt_i = cfl * dx_i / (d * lambda_i), lambda_i the
+ *                 maximum of a over its faces (Eq. 5; the per-patch value of
+ *                 fv_max_eigenvalue_reduce), written here (output).
+ *   lambda_patch  nullable device double[n_patches]: lambda_i.
+ * Halos as for fv_patch_update_batch.  With all dx_i = dx and dt_i = dt the
+ * result is bitwise that of fv_patch_update_batch.  Both arrays 8-byte
+ * aligned (FV_ERR_ALIGNMENT), non-null (FV_ERR_INVALID_ARG).
+ */
+fv_status fv_patch_update_local(fv_batch* h, const void* in_with_halo, void* out,
+                               const int64_t* patch_offsets, const int32_t* patch_sizes,
+                               int64_t n_patches, const double* dx_patch, double* dt_patch,
+                               double cfl, double* lambda_patch);
+
+/*
  * fv_time_step -- one full explicit time step of a patch mesh in one kernel
  * launch: the update of fv_patch_update_batch (Eq. 3-5) with
  *   - dt = cfl * dx / (d * lambda) from the CFL condition on the current

@@ -230,6 +230,44 @@ fv_status fv_patch_update_batch(fv_batch* h, const void* in, void* out, const in
   return fv_patch_update_batch_ex(h, in, out, off, sizes, n, d, s, dx, dt, nullptr);
 }
 
+fv_status fv_patch_update_local(fv_batch* h, const void* in, void* out, const int64_t* off,
+                               const int32_t* sizes, int64_t n, const double* dx_patch,
+                               double* dt_patch, double cfl, double* lambda_patch) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  h->last_error[0] = 0;
+  if (cfl != cfl) return set_err(h, FV_ERR_INVALID_ARG, "cfl is NaN");
+  fv_status st = check_meta(h, in, off, sizes, n);
+  if (st != FV_OK) return st;
+  if (n == 0) return FV_OK;
+  if (!out || !dx_patch || !dt_patch)
+    return set_err(h, FV_ERR_INVALID_ARG, "null output, dx_patch or dt_patch");
+  if (!aligned16(out)) return set_err(h, FV_ERR_ALIGNMENT, "output not 16-byte aligned");
+  if (((uintptr_t)dx_patch & 7u) || ((uintptr_t)dt_patch & 7u))
+    return set_err(h, FV_ERR_ALIGNMENT, "dx_patch / dt_patch not 8-byte aligned");
+  if (in == out) return set_err(h, FV_ERR_INVALID_ARG, "in and out alias");
+  fv::UpdateLaunch l;
+  l.in = in;
+  l.out = out;
+  l.off = off;
+  l.sizes = sizes;
+  l.n = n;
+  l.pmax = h->max_patch_size;
+  l.gamma = h->gamma;
+  l.dx = 1.0;  // replaced per patch
+  l.dt = 1.0;
+  l.cfl = cfl;
+  l.dt_dev = h->d_dt;
+  l.lam_patch = lambda_patch;
+  l.dx_patch = dx_patch;
+  l.dt_patch = dt_patch;
+  l.local_cfl = cfl > 0.0;
+  l.status = h->d_status;
+  l.fused = false;
+  cudaError_t e = fv::launch_scheduled(h, l);
+  if (e != cudaSuccess) return cuda_err(h, e, "update kernel");
+  return FV_OK;
+}
+
 fv_status fv_halo_fill(fv_batch* h, void* q, const int64_t* off, const int32_t* sizes,
                        const int32_t* nbr, int64_t n) {
   if (!h) return FV_ERR_INVALID_ARG;

@@ -74,6 +74,9 @@ struct UpdateLaunch {
   bool fused = false;  // time-step mode: gather halos, dt from lam_in, reduce lam_next
   int nstage = 0;      // shared-memory stages (0: the handle's)
   int nt = 128;        // threads per CTA
+  const double* dx_patch = nullptr;  // update mode: per-patch cell sizes, or null
+  double* dt_patch = nullptr;        // with dx_patch: per-patch dt (in, or out with local_cfl)
+  bool local_cfl = false;
   const void* prim_in = nullptr;  // time step: carried primitives of `in`, or null
   void* prim_out = nullptr;       // time step: primitives of `out`, or null
   int64_t prim_stride = 0;        // elements per patch of the primitive buffers

@@ -72,6 +72,9 @@ struct StepParams {
   const float* corr;    // per-face flux corrections [patch][k][v][face], or null
   int64_t corr_stride;  // floats per patch of corr
   T one, mone, mzero;  // 1, -1, -0 as arguments (see Arith)
+  const double* dx_patch;  // update mode: per-patch cell size (or null: dx)
+  double* dt_patch;        // with dx_patch: per-patch dt (input, or output under local CFL)
+  int local_cfl;           // with dx_patch: dt_i = cfl dx_i / (d lambda_i) per patch
   const T* __restrict__ prim_in;  // carried primitives of `in` (primitive-carry mode)
   T* __restrict__ prim_out;       // primitives of `out` (time-step modes), or null
   int64_t prim_stride;            // elements per patch of prim_in / prim_out
@@ -475,8 +478,34 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
       Gk[v * nface + j] = gv;
     }
   }
+  // per-patch maximum of a over the faces (Algorithm 1 step 10)
+  const bool want_lam = a.lam_patch != nullptr || a.local_cfl;
+  if (want_lam) {
+    lmax = warp_max_u64(lmax);
+    if ((tid & 31) == 0) red[tid >> 5] = lmax;
+  }
   __syncthreads();
   if constexpr (PRIMIN) mid_hook<T, D, GATHER, PRIMIN, NT>(a, pp, nx);
+  unsigned long long lam_bits = 0ull;
+  if (want_lam) {
+    lam_bits = red[0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) lam_bits = red[w] > lam_bits ? red[w] : lam_bits;
+    if (tid == 0 && a.lam_patch != nullptr) a.lam_patch[i] = order_value<T>(lam_bits);
+  }
+  // per-patch cell size and time step (update mode): dt_i given, or from the
+  // patch's own CFL condition on its maximum wave speed
+  if (a.dx_patch != nullptr) {
+    const double dxi = a.dx_patch[i];
+    double dti;
+    if (a.local_cfl) {
+      dti = (a.cfl * dxi) / ((double)D * order_value<T>(lam_bits));
+      if (tid == 0) a.dt_patch[i] = dti;
+    } else {
+      dti = a.dt_patch[i];
+    }
+    mhr = neg_t((T)(0.5 * (dti / dxi)));
+  }
 
   // ---- update: Q - (dt/2dx) sum_k (G_+ - G_-) -----------------------------------
   T* dst_base = a.out + off;
@@ -527,17 +556,6 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
   }
 
   if (bad) atomicOr(a.status, ST_NONPHYSICAL);
-  if (a.lam_patch != nullptr) {
-    lmax = warp_max_u64(lmax);
-    if ((tid & 31) == 0) red[tid >> 5] = lmax;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned long long m = red[0];
-#pragma unroll
-      for (int w = 1; w < NT / 32; ++w) m = red[w] > m ? red[w] : m;
-      a.lam_patch[i] = order_value<T>(m);
-    }
-  }
 }
 
 template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN, int NT>
@@ -755,6 +773,9 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.one = T(1);
   a.mone = T(-1);
   a.mzero = T(-0.0);
+  a.dx_patch = l.dx_patch;
+  a.dt_patch = l.dt_patch;
+  a.local_cfl = l.local_cfl ? 1 : 0;
   a.prim_in = static_cast<const T*>(l.prim_in);
   a.prim_out = static_cast<T*>(l.prim_out);
   a.prim_stride = l.prim_stride;

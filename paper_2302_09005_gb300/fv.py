@@ -71,6 +71,8 @@ def _lib() -> ctypes.CDLL:
         L.fv_patch_update_batch_ex.argtypes = [vp, vp, vp, vp, vp, i64, c_int, c_int, dbl, dbl,
                                                ctypes.POINTER(fv_update_extras)]
         L.fv_halo_fill.argtypes = [vp, vp, vp, vp, vp, i64]
+        L.fv_patch_update_local.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, dbl, vp]
+        L.fv_patch_update_local.restype = c_int
         L.fv_max_eigenvalue_reduce.argtypes = [vp, vp, vp, vp, i64, vp, vp, dbl, dbl, vp]
         L.fv_conserved_totals.argtypes = [vp, vp, vp, vp, i64, vp]
         L.fv_get_dt_ptr.argtypes = [vp, ctypes.POINTER(vp)]
@@ -195,6 +197,14 @@ def fv_patch_update_batch_ex(h, in_with_halo, out, patch_offsets, patch_sizes, n
                                          _ptr(patch_sizes), n_patches, d, s, dx, dt,
                                          ctypes.byref(ex))
     _check(h, st, "fv_patch_update_batch_ex")
+
+
+def fv_patch_update_local(h, in_with_halo, out, patch_offsets, patch_sizes, n_patches: int,
+                          dx_patch, dt_patch, cfl: float = 0.0, lambda_patch=None):
+    st = _lib().fv_patch_update_local(h, _ptr(in_with_halo), _ptr(out), _ptr(patch_offsets),
+                                      _ptr(patch_sizes), n_patches, _ptr(dx_patch),
+                                      _ptr(dt_patch), cfl, _ptr(lambda_patch))
+    _check(h, st, "fv_patch_update_local")
 
 
 def fv_halo_fill(h, q_with_halo, patch_offsets, patch_sizes, neighbours, n_patches: int):

@@ -248,10 +248,11 @@ fv_status fv_time_step_prim(fv_batch* h, const void* in_with_halo, void* out,
 /*
  * fv_run_steps -- n_steps time steps from q0: fv_halo_fill and
  * fv_max_eigenvalue_reduce on q0, then fv_time_step_prim ping-ponging
- * between q0 and q1, the primitives carried from step to step in two buffers
- * the handle allocates on first use (2 * n_patches * fv_prim_stride
- * elements, kept until fv_batch_destroy; growing them drops the cached
- * graphs).  The result is in q0 if n_steps is even, else in q1.
+ * between q0 and q1.  FP64 handles carry the primitives from step to step in
+ * two buffers the handle allocates on first use (2 * n_patches *
+ * fv_prim_stride elements, kept until fv_batch_destroy; growing them drops
+ * the cached graphs); FP32 handles run without the carry (faster there).
+ * The result is in q0 if n_steps is even, else in q1.
  * use_graph != 0 captures the whole sequence into a CUDA graph the first
  * time a given set of arguments is seen, caches the instantiated graph in
  * the handle (keyed by every pointer and value argument) and replays it;

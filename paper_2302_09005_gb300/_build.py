@@ -92,3 +92,20 @@ def source_hash() -> str:
             hsh.update(os.path.basename(f).encode())
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]
+
+
+# Sources of the patch update / time-step kernel itself (device code and the
+# headers it includes); host-side API changes leave its counters valid.
+STEP_KERNEL_SOURCES = ("fv_step.cuh", "fv_device.cuh", "fv_ptx.cuh", "fv_update.cu",
+                       "fv_update_f32.cu", "fv_update_nt.cu", "fv_update_nt_f32.cu")
+
+
+def step_kernel_hash() -> str:
+    """Hash of the step kernel's sources (keys the committed ncu traffic)."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            hsh.update(name.encode())
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]

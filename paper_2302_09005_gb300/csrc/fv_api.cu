@@ -438,9 +438,12 @@ fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* off, cons
   h->last_error[0] = 0;
   if (n_steps < 0) return set_err(h, FV_ERR_INVALID_ARG, "n_steps < 0");
   if (q0 == q1) return set_err(h, FV_ERR_INVALID_ARG, "q0 and q1 alias");
-  // the primitive carry: two buffers, grown (never shrunk) before any capture;
-  // graphs that refer to the old buffers are dropped when they move
-  if (n_steps > 1 && n > 0) {
+  // the primitive carry (FP64: it saves FP64-pipe work; FP32 kernels are
+  // issue- and memory-bound and run faster without its extra bytes): two
+  // buffers, grown (never shrunk) before any capture; graphs that refer to
+  // the old buffers are dropped when they move
+  const bool carry = h->prec == FV_FP64 && n_steps > 1;
+  if (carry && n > 0) {
     const size_t es = h->prec == FV_FP64 ? 8 : 4;
     const int64_t need = n * fv::prim_stride_elems(h->d, h->prec, h->max_patch_size);
     if (need > h->prim_cap) {
@@ -465,8 +468,8 @@ fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* off, cons
     void* b = q1;
     for (int k = 0; k < n_steps && s == FV_OK; ++k) {
       // step k reads the primitives step k-1 left and hands on its own
-      const void* pin = k == 0 ? nullptr : h->d_prim[(k - 1) & 1];
-      void* pout = k + 1 < n_steps ? h->d_prim[k & 1] : nullptr;
+      const void* pin = (!carry || k == 0) ? nullptr : h->d_prim[(k - 1) & 1];
+      void* pout = (carry && k + 1 < n_steps) ? h->d_prim[k & 1] : nullptr;
       s = time_step_impl(h, a, b, off, sizes, nbr, n, dx, cfl, nullptr, nullptr, pin, pout);
       std::swap(a, b);
     }

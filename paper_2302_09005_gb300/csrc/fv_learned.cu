@@ -4,9 +4,10 @@
 //   correction  every face of every patch gets C = sd_y * net((S - mu)/sd),
 //               S the 4-cell stencil Q_{i-2..i+1} normal to the face in the
 //               face's normal frame (rho, j_n, j_t, E), net the 16 -> 64 -> 64
-//               -> 4 GELU network, evaluated by one warp per 16 faces on the
-//               tensor cores (BF16 mma.sync, FP32 accumulation; hidden
-//               activations stay in registers between layers).  The update
+//               -> 4 GELU network, evaluated 128 faces at a time on the
+//               5th-generation tensor cores (tcgen05.mma, BF16 operands in
+//               shared memory, FP32 accumulators in tensor memory; one thread
+//               per face for the stencil, bias, GELU and output).  The update
 //               adds C to the face flux once per face, so both cells see the
 //               same flux and the totals are conserved.  A face shared by two
 //               patches gets the same C in both (same stencil, same arithmetic).
@@ -25,10 +26,15 @@
 #include "fv_device.cuh"
 #include "fv_internal.h"
 #include "fv_mma.cuh"
+#include "fv_ptx.cuh"
+#include "fv_tc.cuh"
 
 namespace fv {
 
 constexpr int kLNT = 128;  // threads per CTA of the learned kernels
+// Clock cycles a CTA waits for its MMAs before it reports FV_ERR_TIMEOUT
+// (about one second at 2 GHz).
+constexpr long long kTcWaitLimit = 2000000000ll;
 constexpr int kLPmax = 16;  // largest patch of the learned kernels
 
 __host__ __device__ inline int64_t corr_stride_for(int pmax) {
@@ -121,176 +127,204 @@ __device__ __forceinline__ int phys_comp(int k, int vn) {
 }
 
 // ---------------------------------------------------------------------------
-// Correction kernel
+// Correction kernel: the network on the 5th-generation tensor cores
 // ---------------------------------------------------------------------------
-struct NetSmem {
-  uint16_t w1[64 * 16];
-  uint16_t w2[64 * 64];
-  uint16_t w3[8 * 64];  // rows 4..7 zero
-  float b1[64], b2[64], b3[8];
-  float mu[16], sd[16], sdy[4];
+// A CTA of 128 threads takes tiles of 128 face slots (slot = patch * fmax +
+// face, fmax the faces of a patch of the handle's largest size; slots past a
+// smaller patch's faces are idle rows).  Thread t owns row t of the tile: it
+// gathers its face's stencil, normalises it into row t of A1 (BF16, shared
+// memory); one thread issues the MMAs (tcgen05, FP32 accumulators in tensor
+// memory, D row t = TMEM lane t), and thread t reads its row back, adds the
+// bias, applies GELU and writes row t of the next layer's A operand:
+//   D1 = A1[128x16] W1^T (N = 64), D2 = A2[128x64] W2^T (N = 64),
+//   D3 = A3[128x64] W3^T (N = 16, rows 4..15 of W3 zero).
+// D1, D2 and D3 share 64 TMEM columns; A3 reuses A2's buffer (each MMA has
+// completed before its operands are overwritten).
+constexpr int kTcRows = 128;  // faces per tile: the MMA's M
+constexpr int kTcCols = 64;   // TMEM columns of a CTA
+
+struct TcSmem {
+  alignas(128) unsigned char a1[kTcRows * 16 * 2];
+  alignas(128) unsigned char a2[kTcRows * 64 * 2];
+  alignas(128) unsigned char w1[64 * 16 * 2];
+  alignas(128) unsigned char w2[64 * 64 * 2];
+  alignas(128) unsigned char w3[16 * 64 * 2];
+  float b1[64], b2[64], b3[4];
+  float mu[16], rsd[16], sdy[4];
+  alignas(8) uint64_t bar;
+  uint32_t tmem;
 };
 
-__device__ void load_net(const float* params, const float* norm, NetSmem& s) {
-  for (int i = threadIdx.x; i < 64 * 16; i += kLNT) s.w1[i] = f32_to_bf16(params[kOffW1 + i]);
-  for (int i = threadIdx.x; i < 64 * 64; i += kLNT) s.w2[i] = f32_to_bf16(params[kOffW2 + i]);
-  for (int i = threadIdx.x; i < 8 * 64; i += kLNT)
-    s.w3[i] = i < 4 * 64 ? f32_to_bf16(params[kOffW3 + i]) : (uint16_t)0;
-  for (int i = threadIdx.x; i < 64; i += kLNT) {
-    s.b1[i] = params[kOffB1 + i];
-    s.b2[i] = params[kOffB2 + i];
-  }
-  if (threadIdx.x < 8) s.b3[threadIdx.x] = threadIdx.x < 4 ? params[kOffB3 + threadIdx.x] : 0.f;
-  if (threadIdx.x < 16) {
-    s.mu[threadIdx.x] = norm[threadIdx.x];
-    s.sd[threadIdx.x] = norm[16 + threadIdx.x];
-  }
-  if (threadIdx.x < 4) s.sdy[threadIdx.x] = norm[32 + threadIdx.x];
+__device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v) {
+  uint4 u;
+  u.x = pack_bf16(v[0], v[1]);
+  u.y = pack_bf16(v[2], v[3]);
+  u.z = pack_bf16(v[4], v[5]);
+  u.w = pack_bf16(v[6], v[7]);
+  *reinterpret_cast<uint4*>(dst) = u;
 }
 
-// Normalised feature phi of face f (k, b, tr) from the stage.
-__device__ __forceinline__ float feature(const NetSmem& s, const float* stage, int p, int k,
-                                         int b, int tr, int phi) {
-  const int c = phi >> 2, vn = phi & 3;
-  const int along = b + c;  // stage coordinate along k of stencil cell c
-  const int X = k == 0 ? along : tr + 2;
-  const int Y = k == 0 ? tr + 2 : along;
-  const float v = stage[(Y * (p + 4) + X) * 4 + phys_comp(k, vn)];
-  return (v - s.mu[phi]) / s.sd[phi];
+// Row `row` of a 64-wide hidden layer: TMEM accumulators + bias -> GELU ->
+// BF16 into the K-major A tile of the next layer.
+__device__ __forceinline__ void hidden_row(uint32_t trow, const float* bias, unsigned char* a,
+                                           int row) {
+#pragma unroll
+  for (int c = 0; c < 64; c += 16) {
+    float v[16];
+    tc_ld16(trow + c, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = gelu_f(v[i] + bias[c + i]);
+    store_bf16x8(a + tc_kmajor_offset(row, c, 64), v);
+    store_bf16x8(a + tc_kmajor_offset(row, c + 8, 64), v + 8);
+  }
 }
 
-// One warp: corrections of faces [f0base, f0base + 16).
-__device__ __forceinline__ void net_tile(const NetSmem& s, const float* stage, int p, int nf1,
-                                         int fbase, float (&out)[2][2], int (&kk_out)[2],
-                                         int (&j_out)[2]) {
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int nfaces = 2 * nf1;
-  int fk[2], fb[2], ftr[2];
-  bool ok[2];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int f = fbase + g + 8 * r;
-    ok[r] = f < nfaces;
-    const int fc = ok[r] ? f : 0;
-    fk[r] = fc / nf1;
-    const int j = fc - fk[r] * nf1;
-    fb[r] = j / p;
-    ftr[r] = j - fb[r] * p;
-    kk_out[r] = ok[r] ? fk[r] : -1;
-    j_out[r] = j;
-  }
-  auto F = [&](int r, int phi) -> float {
-    return ok[r] ? feature(s, stage, p, fk[r], fb[r], ftr[r], phi) : 0.f;
-  };
-  uint32_t a[4];
-  a[0] = pack_bf16(F(0, 2 * t), F(0, 2 * t + 1));
-  a[1] = pack_bf16(F(1, 2 * t), F(1, 2 * t + 1));
-  a[2] = pack_bf16(F(0, 2 * t + 8), F(0, 2 * t + 9));
-  a[3] = pack_bf16(F(1, 2 * t + 8), F(1, 2 * t + 9));
-  // layer 1: 16 -> 64
-  float acc[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    const uint16_t* w = s.w1 + (nt * 8 + g) * 16;
-    const uint32_t b[2] = {*reinterpret_cast<const uint32_t*>(w + 2 * t),
-                           *reinterpret_cast<const uint32_t*>(w + 2 * t + 8)};
-    mma_16816(acc[nt], a, b);
-  }
-  uint32_t h[4][4];
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int nt = 2 * kk + half;
-      const int n = nt * 8 + 2 * t;
-      const float z0 = gelu_f(acc[nt][0] + s.b1[n]), z1 = gelu_f(acc[nt][1] + s.b1[n + 1]);
-      const float z2 = gelu_f(acc[nt][2] + s.b1[n]), z3 = gelu_f(acc[nt][3] + s.b1[n + 1]);
-      h[kk][2 * half] = pack_bf16(z0, z1);
-      h[kk][2 * half + 1] = pack_bf16(z2, z3);
-    }
-  }
-  // layer 2: 64 -> 64
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const uint16_t* w = s.w2 + (nt * 8 + g) * 64 + kk * 16;
-      const uint32_t b[2] = {*reinterpret_cast<const uint32_t*>(w + 2 * t),
-                             *reinterpret_cast<const uint32_t*>(w + 2 * t + 8)};
-      const uint32_t ak[4] = {h[kk][0], h[kk][1], h[kk][2], h[kk][3]};
-      mma_16816(acc[nt], ak, b);
-    }
-  }
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int nt = 2 * kk + half;
-      const int n = nt * 8 + 2 * t;
-      const float z0 = gelu_f(acc[nt][0] + s.b2[n]), z1 = gelu_f(acc[nt][1] + s.b2[n + 1]);
-      const float z2 = gelu_f(acc[nt][2] + s.b2[n]), z3 = gelu_f(acc[nt][3] + s.b2[n + 1]);
-      h[kk][2 * half] = pack_bf16(z0, z1);
-      h[kk][2 * half + 1] = pack_bf16(z2, z3);
-    }
-  }
-  // layer 3: 64 -> 4 (padded to 8)
-  float y[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    const uint16_t* w = s.w3 + g * 64 + kk * 16;
-    const uint32_t b[2] = {*reinterpret_cast<const uint32_t*>(w + 2 * t),
-                           *reinterpret_cast<const uint32_t*>(w + 2 * t + 8)};
-    const uint32_t ak[4] = {h[kk][0], h[kk][1], h[kk][2], h[kk][3]};
-    mma_16816(y, ak, b);
-  }
-  // lanes t = 0, 1 hold output columns 2t, 2t+1 of rows g (y[0..1]), g+8 (y[2..3])
-  const int c0 = 2 * t;
-  out[0][0] = c0 < 4 ? (y[0] + s.b3[c0]) * s.sdy[c0] : 0.f;
-  out[0][1] = c0 < 4 ? (y[1] + s.b3[c0 + 1]) * s.sdy[c0 + 1] : 0.f;
-  out[1][0] = c0 < 4 ? (y[2] + s.b3[c0]) * s.sdy[c0] : 0.f;
-  out[1][1] = c0 < 4 ? (y[3] + s.b3[c0 + 1]) * s.sdy[c0 + 1] : 0.f;
+// All threads: operands visible to the tensor cores, TMEM reads done; then
+// thread 0 issues.
+__device__ __forceinline__ void tc_handoff() {
+  fence_proxy_async_smem();
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kLNT) corr_kernel(MeshView<T> m, int pmax, const float* params,
-                                                    const float* norm, float* corr,
-                                                    int64_t stride) {
-  __shared__ NetSmem s;
-  __shared__ float stage[(kLPmax + 4) * (kLPmax + 4) * 4];
-  load_net(params, norm, s);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = lane & 3;
-  for (int64_t pid = blockIdx.x; pid < m.n; pid += gridDim.x) {
-    const int p = m.sizes[pid];
-    if (p < 1 || p > pmax) {
-      if (threadIdx.x == 0) atomicOr(m.status, ST_BAD_PATCH);
-      continue;
-    }
-    __syncthreads();  // stage reuse, and the network loaded
-    fill_stage(m, pid, p, stage);
-    __syncthreads();
-    const int nf1 = (p + 1) * p;
-    const int ntiles = (2 * nf1 + 15) / 16;
-    for (int tile = warp; tile < ntiles; tile += kLNT / 32) {
-      float out[2][2];
-      int kf[2], jf[2];
-      net_tile(s, stage, p, nf1, tile * 16, out, kf, jf);
-      if (t < 2) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          if (kf[r] < 0) continue;
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int vn = 2 * t + c;
-            corr[pid * stride + (kf[r] * 4 + phys_comp(kf[r], vn)) * nf1 + jf[r]] = out[r][c];
-          }
-        }
+__global__ void __launch_bounds__(kTcRows, 4)
+    corr_kernel(MeshView<T> m, int pmax, const float* params, const float* norm, float* corr,
+                int64_t stride) {
+  __shared__ TcSmem s;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights (BF16, K-major tiles), biases, normalisation
+  for (int i = tid; i < 64 * 16; i += kTcRows)
+    *reinterpret_cast<uint16_t*>(s.w1 + tc_kmajor_offset(i >> 4, i & 15, 16)) =
+        f32_to_bf16(params[kOffW1 + i]);
+  for (int i = tid; i < 64 * 64; i += kTcRows)
+    *reinterpret_cast<uint16_t*>(s.w2 + tc_kmajor_offset(i >> 6, i & 63, 64)) =
+        f32_to_bf16(params[kOffW2 + i]);
+  for (int i = tid; i < 16 * 64; i += kTcRows)
+    *reinterpret_cast<uint16_t*>(s.w3 + tc_kmajor_offset(i >> 6, i & 63, 64)) =
+        i < 4 * 64 ? f32_to_bf16(params[kOffW3 + i]) : (uint16_t)0;
+  if (tid < 64) {
+    s.b1[tid] = params[kOffB1 + tid];
+    s.b2[tid] = params[kOffB2 + tid];
+  }
+  if (tid < 4) {
+    s.b3[tid] = params[kOffB3 + tid];
+    s.sdy[tid] = norm[32 + tid];
+  }
+  if (tid < 16) {
+    s.mu[tid] = norm[tid];
+    s.rsd[tid] = 1.0f / norm[16 + tid];
+  }
+  if (tid == 0) {
+    mbar_init(&s.bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tc_alloc(&s.tmem, kTcCols);
+  tc_handoff();
+  const uint32_t tm = s.tmem;
+  const uint32_t trow = tm + ((uint32_t)(warp * 32) << 16);  // this warp's TMEM lanes
+  const int64_t fmax = 2ll * (pmax + 1) * pmax;
+  const int64_t nslots = m.n * fmax;
+  const int64_t ntiles = (nslots + kTcRows - 1) / kTcRows;
+  constexpr uint32_t kId64 = tc_idesc_bf16(kTcRows, 64), kId16 = tc_idesc_bf16(kTcRows, 16);
+  uint32_t parity = 0;
+  bool failed = false;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // ---- this thread's face: slot -> (patch, direction, face)
+    const int64_t slot = tile * kTcRows + tid;
+    const int64_t pid = slot / fmax;
+    const int lf = (int)(slot - pid * fmax);
+    bool act = slot < nslots;
+    int p = 1, nf1 = 2, k = 0, j = 0, b = 0, tr = 0;
+    if (act) {
+      p = m.sizes[pid];
+      if (p < 1 || p > pmax) {
+        if (lf == 0) atomicOr(m.status, ST_BAD_PATCH);
+        act = false;
+      } else {
+        nf1 = (p + 1) * p;
+        act = lf < 2 * nf1;
       }
     }
+    if (act) {
+      k = lf / nf1;
+      j = lf - k * nf1;
+      b = j / p;
+      tr = j - b * p;
+    }
+    // ---- normalised stencil Q_{b-1..b+2} in the face's normal frame -> A1 row
+    float x[16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (act) {
+        const int along = b - 1 + c;
+        int neg;
+        const T* src = cell_source(m, pid, p, k == 0 ? along : tr + 1, k == 0 ? tr + 1 : along,
+                                   neg);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (u == neg) ? -(float)src[u] : (float)src[u];
+      }
+#pragma unroll
+      for (int vn = 0; vn < 4; ++vn) {
+        const int phi = 4 * c + vn;
+        x[phi] = act ? (v[phys_comp(k, vn)] - s.mu[phi]) * s.rsd[phi] : 0.f;
+      }
+    }
+    store_bf16x8(s.a1 + tc_kmajor_offset(tid, 0, 16), x);
+    store_bf16x8(s.a1 + tc_kmajor_offset(tid, 8, 16), x + 8);
+    tc_handoff();
+    // ---- layer 1: 16 -> 64
+    if (tid == 0) {
+      tc_mma_bf16(tm, tc_smem_desc(s.a1, 128, 256), tc_smem_desc(s.w1, 128, 256), kId64, 0);
+      tc_commit(&s.bar);
+    }
+    failed |= !mbar_wait_bounded(&s.bar, parity, kTcWaitLimit);
+    parity ^= 1u;
+    tc_fence_after_sync();
+    hidden_row(trow, s.b1, s.a2, tid);
+    tc_handoff();
+    // ---- layer 2: 64 -> 64
+    if (tid == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, 1024),
+                    tc_smem_desc(s.w2 + kk * 256, 128, 1024), kId64, kk > 0);
+      tc_commit(&s.bar);
+    }
+    failed |= !mbar_wait_bounded(&s.bar, parity, kTcWaitLimit);
+    parity ^= 1u;
+    tc_fence_after_sync();
+    hidden_row(trow, s.b2, s.a2, tid);
+    tc_handoff();
+    // ---- layer 3: 64 -> 4 (N = 16)
+    if (tid == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, 1024),
+                    tc_smem_desc(s.w3 + kk * 256, 128, 1024), kId16, kk > 0);
+      tc_commit(&s.bar);
+    }
+    failed |= !mbar_wait_bounded(&s.bar, parity, kTcWaitLimit);
+    parity ^= 1u;
+    tc_fence_after_sync();
+    float y[4];
+    tc_ld4(trow, y);
+    if (act) {
+#pragma unroll
+      for (int vn = 0; vn < 4; ++vn)
+        corr[pid * stride + (k * 4 + phys_comp(k, vn)) * nf1 + j] = (y[vn] + s.b3[vn]) * s.sdy[vn];
+    }
+    tc_fence_before_sync();
+    if (__syncthreads_or(failed)) break;
   }
+  // a wait that gave up: report; the TMEM is released either way
+  if (failed && tid == 0) atomicOr(m.status, ST_TIMEOUT);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  if (warp == 0) tc_dealloc(tm, kTcCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,16 +536,19 @@ fv_status fv_flux_correction(fv_batch* h, const void* q, const int64_t* off, con
   if (n == 0) return FV_OK;
   if (!q || !off || !sizes || !nbr || !params || !norm || !corr)
     return lerr(h, FV_ERR_INVALID_ARG, "null pointer");
-  const int grid = (int)(n < (int64_t)h->num_sms * 8 ? n : (int64_t)h->num_sms * 8);
   const int64_t stride = fv::corr_stride_for(h->max_patch_size);
+  // tiles of 128 face slots; four CTAs per SM (4 x 64 TMEM columns of 512)
+  const int64_t ntiles = (n * (stride / 4) + fv::kTcRows - 1) / fv::kTcRows;
+  const int64_t gmax = (int64_t)h->num_sms * 4;
+  const int grid = (int)(ntiles < gmax ? ntiles : gmax);
   if (h->prec == FV_FP64) {
     fv::MeshView<double> m{static_cast<const double*>(q), off, sizes, nbr, n, h->d_status};
-    fv::corr_kernel<double><<<grid, fv::kLNT, 0, h->stream>>>(m, h->max_patch_size, params, norm,
-                                                              corr, stride);
+    fv::corr_kernel<double><<<grid, fv::kTcRows, 0, h->stream>>>(m, h->max_patch_size, params,
+                                                                 norm, corr, stride);
   } else {
     fv::MeshView<float> m{static_cast<const float*>(q), off, sizes, nbr, n, h->d_status};
-    fv::corr_kernel<float><<<grid, fv::kLNT, 0, h->stream>>>(m, h->max_patch_size, params, norm,
-                                                             corr, stride);
+    fv::corr_kernel<float><<<grid, fv::kTcRows, 0, h->stream>>>(m, h->max_patch_size, params,
+                                                                norm, corr, stride);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FV_OK : lerr(h, FV_ERR_CUDA, cudaGetErrorString(e));

@@ -39,14 +39,31 @@ __device__ __forceinline__ uint16_t f32_to_bf16(float x) {
   return *reinterpret_cast<const uint16_t*>(&v);
 }
 
-// gelu(z) = z Phi(z), Phi the standard normal distribution function.
-__device__ __forceinline__ float gelu_f(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+// gelu(z) = z Phi(z), Phi the standard normal distribution function,
+// evaluated on the GPU in its tanh form
+//   gelu(z) ~ z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
+// with the hardware tanh (one special-function instruction instead of the
+// polynomial of erf).  The tanh form stays within 5e-4 of z Phi(z) (2e-4
+// relative, the worst near z = 2.7) and the hardware tanh within 2^-11
+// relative; both below the BF16 rounding the activations get next (2^-9
+// relative).  Training uses the same form and its
+// exact derivative, so the network is trained for what it evaluates.
+__device__ __forceinline__ float tanh_hw(float u) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return t;
 }
-// gelu'(z) = Phi(z) + z phi(z).
+__device__ __forceinline__ float gelu_f(float z) {
+  const float u = z * fmaf(0.0356774081f, z * z, 0.7978845608f);
+  const float h = 0.5f * z;
+  return fmaf(h, tanh_hw(u), h);
+}
+// d/dz of the tanh form: (1 + t)/2 + z/2 (1 - t^2) sqrt(2/pi) (1 + 3 0.044715 z^2).
 __device__ __forceinline__ float gelu_prime_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-         z * 0.39894228040143268f * __expf(-0.5f * z * z);
+  const float z2 = z * z;
+  const float t = tanh_hw(z * fmaf(0.0356774081f, z2, 0.7978845608f));
+  const float du = fmaf(0.1070322244f, z2, 0.7978845608f);
+  return fmaf(0.5f * z * du, fmaf(-t, t, 1.0f), fmaf(0.5f, t, 0.5f));
 }
 
 // Layout of the flat parameter vector of the 16 -> 64 -> 64 -> 4 network:

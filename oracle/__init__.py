@@ -12,6 +12,8 @@ Contents:
     "Riemann Solvers and Numerical Methods for Fluid Dynamics", ch. 4), used
     only to verify the oracle.
   * ``mlp.py`` -- FP64 forward/backward of the learned face-flux correction.
+  * ``amr.py`` -- halos of patches on 3:1 refined meshes (mean of the
+    neighbouring solution over each halo cell).
 
 Every function cites the passage of the paper it follows.  Functions without
 an independent pin say "parity unpinned" in their docstring.

@@ -282,3 +282,37 @@ def shear_layer(N: int, *, seed: int = 0, amp: float = 0.01, gamma: float = GAMM
     v = np.broadcast_to(v1[None, :], (N, N))
     vel = np.stack([u, v], axis=-1)
     return conserved_from_primitive(rho, vel, np.full((N, N), 2.5), gamma)
+
+
+def amr_mesh(d: int, p: int, base_level: int, refine=(), *, seed: int = 0, dtype=np.float64,
+             align_bytes: int = 16, halo: int = 1):
+    """A 3:1 refined patch mesh on the unit domain [0, 1]^d.
+
+    The domain is a tree: a tree cell of level l has edge 3^-l and splits into
+    3^d children of level l + 1.  Every tree cell of ``base_level`` (3^l per
+    axis, integer coordinates c) carries a patch of p^d cells, except the
+    cells listed in ``refine`` (coordinates at ``base_level``), which are
+    replaced by their 3^d children (coordinates 3 c + a, a in {0, 1, 2}^d).
+    Every cell, halo included, holds a random state (``random_cells``).
+
+    Returns (q, off, sizes, level int32[n], coord int32[n, d]); patches are the
+    unrefined base cells in index order (x fastest), then the children of each
+    refined cell."""
+    refine = {tuple(int(v) for v in c) for c in refine}
+    nb = 3 ** base_level
+    levels, coords = [], []
+    for idx in np.ndindex(*(nb,) * d):
+        c = tuple(reversed(idx))  # x fastest
+        if c not in refine:
+            levels.append(base_level)
+            coords.append(c)
+    for c in sorted(refine, key=lambda t: tuple(reversed(t))):
+        for a in np.ndindex(*(3,) * d):
+            child = tuple(3 * c[m] + a[d - 1 - m] for m in range(d))
+            levels.append(base_level + 1)
+            coords.append(child)
+    n = len(levels)
+    q, off, sizes = random_batch(n, p, d, seed=seed, dtype=dtype, align_bytes=align_bytes,
+                                 halo=halo)
+    return (q, off, sizes, np.asarray(levels, dtype=np.int32),
+            np.asarray(coords, dtype=np.int32).reshape(n, d))

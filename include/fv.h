@@ -194,6 +194,34 @@ fv_status fv_patch_update_local(fv_batch* h, const void* in_with_halo, void* out
                                double cfl, double* lambda_patch);
 
 /*
+ * Halos on a 3:1 refined mesh (the spacetree of Sec. 2 splits a cube into
+ * three parts per axis; each cube carries a patch of p^d cells).  Patch i
+ * sits on tree cell coord[i*d .. i*d+d-1] (x first, each in [0, 3^level))
+ * of level level[i] (0..11) of the unit domain; all patches have size p.
+ * A face-halo cell receives the mean of the neighbouring solution over its
+ * region: the neighbour's cell (same level), the coarser neighbour's cell
+ * that contains it (constant prolongation), or the mean of the 3^d finer
+ * cells it covers (restriction); beyond a non-periodic domain edge the
+ * rules of fv_halo_fill (boundary 0: periodic, -1 outflow, -2 wall).
+ * Neighbouring tree cells may differ by one level (FV_ERR_INVALID_ARG
+ * otherwise); meshes with more than one level need p >= 3
+ * (FV_ERR_UNSUPPORTED).
+ * fv_amr_plan_create -- builds the plan on the host (level, coord,
+ *   patch_offsets: HOST arrays; offsets as for the other calls, 16-byte
+ *   multiples) and copies it to the device; synchronous.
+ * fv_amr_halo_fill -- fills the face halos of q_with_halo (device, the
+ *   layout of the plan's offsets) on the handle's stream; interior cells are
+ *   read, halo cells written.
+ * fv_amr_plan_destroy -- frees the plan.
+ */
+typedef struct fv_amr_plan fv_amr_plan; /* opaque */
+fv_status fv_amr_plan_create(fv_batch* h, fv_amr_plan** plan, int64_t n_patches,
+                             const int32_t* level, const int32_t* coord,
+                             const int64_t* patch_offsets, int p, int boundary);
+fv_status fv_amr_halo_fill(fv_batch* h, const fv_amr_plan* plan, void* q_with_halo);
+fv_status fv_amr_plan_destroy(fv_amr_plan* plan);
+
+/*
  * fv_time_step -- one full explicit time step of a patch mesh in one kernel
  * launch: the update of fv_patch_update_batch (Eq. 3-5) with
  *   - dt = cfl * dx / (d * lambda) from the CFL condition on the current

@@ -73,6 +73,12 @@ def _lib() -> ctypes.CDLL:
         L.fv_halo_fill.argtypes = [vp, vp, vp, vp, vp, i64]
         L.fv_patch_update_local.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, dbl, vp]
         L.fv_patch_update_local.restype = c_int
+        L.fv_amr_plan_create.argtypes = [vp, ctypes.POINTER(vp), i64, vp, vp, vp, c_int, c_int]
+        L.fv_amr_plan_create.restype = c_int
+        L.fv_amr_halo_fill.argtypes = [vp, vp, vp]
+        L.fv_amr_halo_fill.restype = c_int
+        L.fv_amr_plan_destroy.argtypes = [vp]
+        L.fv_amr_plan_destroy.restype = c_int
         L.fv_max_eigenvalue_reduce.argtypes = [vp, vp, vp, vp, i64, vp, vp, dbl, dbl, vp]
         L.fv_conserved_totals.argtypes = [vp, vp, vp, vp, i64, vp]
         L.fv_get_dt_ptr.argtypes = [vp, ctypes.POINTER(vp)]
@@ -205,6 +211,38 @@ def fv_patch_update_local(h, in_with_halo, out, patch_offsets, patch_sizes, n_pa
                                       _ptr(patch_sizes), n_patches, _ptr(dx_patch),
                                       _ptr(dt_patch), cfl, _ptr(lambda_patch))
     _check(h, st, "fv_patch_update_local")
+
+
+class AmrPlan:
+    """Owns an fv_amr_plan: halos of a 3:1 refined mesh (host level / coord /
+    offset arrays, numpy)."""
+
+    def __init__(self, h, level, coord, patch_offsets, p: int, boundary: int = 0):
+        import numpy as np
+        self._level = np.ascontiguousarray(level, dtype=np.int32)
+        self._coord = np.ascontiguousarray(coord, dtype=np.int32)
+        self._off = np.ascontiguousarray(patch_offsets, dtype=np.int64)
+        self.h = h
+        self.plan = ctypes.c_void_p()
+        st = _lib().fv_amr_plan_create(h, ctypes.byref(self.plan), len(self._off),
+                                       self._level.ctypes.data, self._coord.ctypes.data,
+                                       self._off.ctypes.data, p, boundary)
+        _check(h, st, "fv_amr_plan_create")
+
+    def fill(self, q_with_halo):
+        _check(self.h, _lib().fv_amr_halo_fill(self.h, self.plan, _ptr(q_with_halo)),
+               "fv_amr_halo_fill")
+
+    def close(self):
+        if self.plan:
+            _lib().fv_amr_plan_destroy(self.plan)
+            self.plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fv_halo_fill(h, q_with_halo, patch_offsets, patch_sizes, neighbours, n_patches: int):

@@ -352,6 +352,7 @@ def run_ours(args, ws, rank, local):
         variants["precision_2d_4095"] = precision_variant(args)
         variants["learned_correction_1024"] = learned_variant(args)
         variants["paper_shape_2d_p17_sweep"] = sweep_variant(args)
+        variants["amr_3d_two_levels"] = amr_variant(args)
 
     peaks, peak_src = _peaks()
     if prec == "f64":
@@ -550,6 +551,61 @@ def sweep_variant(args, p: int = 17, ns=(1, 4, 16, 64, 256, 1024, 4096, 16384, 6
                     "cell update with host->device and device->host copies of the batch "
                     "inside the timed region, and device-resident",
             "status_ok": ok, "rows": rows}
+
+
+def amr_variant(args, d: int = 3, p: int = 5, base_level: int = 3, reps: int = 10):
+    """A 3:1 refined 3D mesh: every tree cell of level 3 (27^3) carries a 5^3
+    patch except a central 5^3 block of tree cells, refined into level-4
+    patches; FP64.  Times the refined-mesh halo fill (copies, prolongation,
+    restriction) and a refined-mesh step (halo fill + update with per-patch
+    cell sizes and one dt)."""
+    import torch
+    from paper_2302_09005_gb300 import fv, inputs
+    nb = 3 ** base_level
+    mid = nb // 2
+    refine = [(x, y, z) for x in range(mid - 2, mid + 3) for y in range(mid - 2, mid + 3)
+              for z in range(mid - 2, mid + 3)]
+    q, off, sz, level, coord = inputs.amr_mesh(d, p, base_level, refine, seed=9)
+    n = len(off)
+    stream = torch.cuda.Stream()
+    b = fv.Batch(d, max_patch_size=p, stream=stream)
+    plan = fv.AmrPlan(b.h, level, coord, off, p, 0)
+    x = torch.from_numpy(q).cuda()
+    y = x.clone()
+    toff, tsz = torch.from_numpy(off).cuda(), torch.from_numpy(sz).cuda()
+    dx = torch.from_numpy(1.0 / (3.0 ** level * p)).cuda()
+    dt = torch.full((n,), 0.1 / (3.0 ** (base_level + 1) * p), dtype=torch.float64,
+                    device="cuda")
+    torch.cuda.synchronize()
+    e = _events(2)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            plan.fill(x)
+        e[0][0].record(stream)
+        for _ in range(reps):
+            plan.fill(x)
+        e[0][1].record(stream)
+        e[1][0].record(stream)
+        for _ in range(reps):
+            plan.fill(x)
+            fv.fv_patch_update_local(b.h, x, y, toff, tsz, n, dx, dt)
+        e[1][1].record(stream)
+    stream.synchronize()
+    ok = b.status() == fv.FV_OK
+    ms_fill = e[0][0].elapsed_time(e[0][1]) / reps
+    ms_step = e[1][0].elapsed_time(e[1][1]) / reps
+    plan.close()
+    b.close()
+    halo_cells = n * 2 * d * p ** (d - 1)
+    cells = n * p ** d
+    n_fine = int(np.sum(level > base_level))
+    # algorithmic bytes of the fill: every halo cell written, its sources read
+    # (restriction: 27 fine cells for the coarse halo cells next to finer ones)
+    return {"what": f"3D FP64, {n} patches of {p}^3 ({n - n_fine} of level {base_level}, "
+                    f"{n_fine} of level {base_level + 1}), periodic",
+            "status_ok": ok, "halo_cells": halo_cells,
+            "ms_halo_fill": ms_fill, "halo_cells_per_s": halo_cells / (ms_fill / 1e3),
+            "ms_step": ms_step, "value": cells / (ms_step / 1e3), "unit": UNIT}
 
 
 def precision_variant(args, N: int = 4095, p: int = 5, steps: int = 100):
@@ -894,7 +950,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--variant", choices=["batching", "precision", "learned", "sweep"],
+    ap.add_argument("--variant", choices=["batching", "precision", "learned", "sweep", "amr"],
                     default=None,
                     help="run one variant on its own")
     ap.add_argument("--small", action="store_true", help="small case of --variant")
@@ -925,6 +981,8 @@ def run_variant(args):
     elif args.variant == "sweep":
         res = sweep_variant(args, ns=(1, 16, 256, 4096) if args.small else
                             (1, 4, 16, 64, 256, 1024, 4096, 16384, 65536))
+    elif args.variant == "amr":
+        res = amr_variant(args, base_level=2 if args.small else 3)
     elif args.variant == "learned":
         res = (learned_variant(args, Nc=256, steps=4, train_steps=200, batch=8192)
                if args.small else learned_variant(args))

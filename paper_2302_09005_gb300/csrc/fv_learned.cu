@@ -155,6 +155,24 @@ struct TcSmem {
   uint32_t tmem;
 };
 
+// A stencil value as float.  FP64 states are narrowed by repacking the bits
+// with integer operations (sign, rebased exponent, leading 23 fraction bits;
+// truncation, values outside the float range flushed to 0 / infinity):
+// the FP64 pipe, which the conversion instruction would use, is the scarce
+// unit of this GPU, and the value is rounded to BF16 next anyway (2^-8 vs the
+// 2^-23 of the truncation).
+__device__ __forceinline__ float narrow(float v) { return v; }
+__device__ __forceinline__ float narrow(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  unsigned bits = sign | ((unsigned)e << 23) | mant;
+  bits = e <= 0 ? sign : bits;
+  bits = e >= 255 ? (sign | 0x7F800000u) : bits;
+  return __uint_as_float(bits);
+}
+
 __device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v) {
   uint4 u;
   u.x = pack_bf16(v[0], v[1]);
@@ -264,7 +282,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
         const T* src = cell_source(m, pid, p, k == 0 ? along : tr + 1, k == 0 ? tr + 1 : along,
                                    neg);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = (u == neg) ? -(float)src[u] : (float)src[u];
+        for (int u = 0; u < 4; ++u) v[u] = (u == neg) ? -narrow(src[u]) : narrow(src[u]);
       }
 #pragma unroll
       for (int vn = 0; vn < 4; ++vn) {
@@ -537,9 +555,10 @@ fv_status fv_flux_correction(fv_batch* h, const void* q, const int64_t* off, con
   if (!q || !off || !sizes || !nbr || !params || !norm || !corr)
     return lerr(h, FV_ERR_INVALID_ARG, "null pointer");
   const int64_t stride = fv::corr_stride_for(h->max_patch_size);
-  // tiles of 128 face slots; four CTAs per SM (4 x 64 TMEM columns of 512)
+  // tiles of 128 face slots; up to six CTAs per SM (shared memory bound; 6 x 64
+  // TMEM columns of 512)
   const int64_t ntiles = (n * (stride / 4) + fv::kTcRows - 1) / fv::kTcRows;
-  const int64_t gmax = (int64_t)h->num_sms * 4;
+  const int64_t gmax = (int64_t)h->num_sms * 6;
   const int grid = (int)(ntiles < gmax ? ntiles : gmax);
   if (h->prec == FV_FP64) {
     fv::MeshView<double> m{static_cast<const double*>(q), off, sizes, nbr, n, h->d_status};

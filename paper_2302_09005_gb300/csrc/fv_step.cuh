@@ -355,6 +355,20 @@ __device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
 // ---------------------------------------------------------------------------
 // One patch: cells, faces, update.
 // ---------------------------------------------------------------------------
+// Whether the face loop of a compile-time patch size runs in warp slots (one
+// direction per warp and iteration) rather than over all faces flat: when it
+// keeps at least as many lanes busy (to 2 %).
+template <int D, int P, int NT>
+__host__ __device__ constexpr bool kWarpSlots() {
+  if (P <= 0 || D == 1) return false;
+  const int nface = (P + 1) * (D == 2 ? P : P * P);
+  const int slot_lanes = D * ((nface + 31) / 32) * 32;
+  const int total = D * nface;
+  const int flat_full = total / NT, flat_rest = total - flat_full * NT;
+  const int flat_lanes = flat_full * NT + (flat_rest + 31) / 32 * 32;
+  return 100 * total / slot_lanes + 2 >= 100 * total / flat_lanes;
+}
+
 template <typename T, int D, int P, bool GATHER, bool FUSED, bool PRIMIN, int NT>
 __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, int64_t i,
                                               int64_t off, const Stage<T>& cur, T* G, T mhr,
@@ -421,12 +435,9 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
   }
 
   // ---- faces: G = f_L + f_R - a (Q_R - Q_L), once per face -------------------
-  unsigned long long lmax = 0ull;
-  FV_PRAGMA_UNROLL(FV_UNROLL_FACES)
-  for (int t = tid; t < D * nface; t += NT) {
-    const int k = t / nface;
-    const int j = t - k * nface;
-    const int b = j / ptr;  // the face lies between cells b and b+1 along k
+  // Face (k, j) of the patch, j = tr + ptr b: between cells b and b+1 along k.
+  auto face = [&](const int k, const int j, unsigned long long& lmax) {
+    const int b = j / ptr;
     const int tr = j - b * ptr;
     const int cl = g.cell_kt(k, b, tr);
     const int cr = cl + g.stride(k);
@@ -476,6 +487,35 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
       if (a.corr != nullptr)
         gv = ar.add(gv, T(2) * (T)a.corr[i * a.corr_stride + (k * S + v) * nface + j]);
       Gk[v * nface + j] = gv;
+    }
+  };
+  unsigned long long lmax = 0ull;
+  if constexpr (kWarpSlots<D, P, NT>()) {
+    // warp slots: a warp takes 32 faces of one direction, so k is the same in
+    // every lane and compiles to constants (strides, cell indexing, the
+    // momentum with the pressure term)
+    const int spk = (nface + 31) >> 5;  // slots per direction
+    const int lane = tid & 31;
+    for (int ws = tid >> 5; ws < D * spk; ws += NT / 32) {
+      const int k = ws / spk;
+      const int j = (ws - k * spk) * 32 + lane;
+      if (j < nface) {
+        if (k == 0) {
+          face(0, j, lmax);
+        } else if constexpr (D >= 2) {
+          if (k == 1) {
+            face(1, j, lmax);
+          } else if constexpr (D == 3) {
+            face(2, j, lmax);
+          }
+        }
+      }
+    }
+  } else {
+    FV_PRAGMA_UNROLL(FV_UNROLL_FACES)
+    for (int t = tid; t < D * nface; t += NT) {
+      const int k = t / nface;
+      face(k, t - k * nface, lmax);
     }
   }
   // per-patch maximum of a over the faces (Algorithm 1 step 10)

@@ -245,6 +245,20 @@ __device__ __forceinline__ void face_sources(const StepParams<T>& a, int64_t j, 
   fs[f] = r;
 }
 
+// Whether the halo gather of a compile-time patch size runs in warp slots
+// (one face per warp and iteration): when its warp iterations are not more
+// than 1.25 times those of the flat loop (each slot iteration is much cheaper:
+// constant indexing, one source).
+template <int D, int P, int NT>
+__host__ __device__ constexpr bool kGatherSlots() {
+  if (P <= 0 || D == 1) return false;
+  const int ptr = D == 2 ? P : P * P;
+  const int slot_iters = 2 * D * ((ptr + 31) / 32);
+  const int total = 2 * D * ptr;
+  const int flat_iters = (total / NT) * (NT / 32) + ((total % NT) + 31) / 32;
+  return 4 * slot_iters <= 5 * flat_iters;
+}
+
 // All threads: fetch the face-halo cells of a patch that do not come with its
 // bulk copy, from the sources resolved by face_sources, as cp.async element
 // copies (a wall's negated normal momentum with a plain load and store); when
@@ -258,32 +272,60 @@ __device__ __forceinline__ void gather_halo(const StepParams<T>& a, int pj, cons
   const Geom<D, P> g(pj);
   const int p = g.p;
   const int ptr = g.ptrans();
-  for (int hc = threadIdx.x; hc < 2 * D * ptr; hc += NT) {
-    const int f = hc / ptr;
-    const int r = hc - f * ptr;
-    const int k = f >> 1;
-    const FaceSrc m = fs[f];
+  // halo cell r of face f (direction k = f / 2) from its source m
+  auto cell = [&](const int k, const int f, const int r, const FaceSrc& m) {
     const int cd = g.cell_kt(k, (f & 1) ? p + 1 : 0, r);
     const int cs = g.cell_kt(k, m.ck, r);
     T* dst = s.box + cd * S;
     const T* src = a.in + m.off + (int64_t)cs * S;
+    T* pd = s.hp + f * 4 * ptr + r;
+    const T* ps = nullptr;
+    if constexpr (PRIMIN)
+      ps = a.prim_in + (int64_t)m.pidx * a.prim_stride + g.icell_kt(k, m.ck - 1, r);
+    if (!m.neg) {
 #pragma unroll
-    for (int v = 0; v < S; ++v) {
-      if (m.neg && v == 1 + k)
-        dst[v] = neg_t(__ldg(src + v));
-      else
-        cp_async_elem(dst + v, src + v);
+      for (int v = 0; v < S; ++v) cp_async_elem(dst + v, src + v);
+      if constexpr (PRIMIN) cp_async_elem(pd, ps + k * g.nint());
+    } else {  // wall: the normal momentum and velocity mirrored
+#pragma unroll
+      for (int v = 0; v < S; ++v) {
+        if (v == 1 + k)
+          dst[v] = neg_t(__ldg(src + v));
+        else
+          cp_async_elem(dst + v, src + v);
+      }
+      if constexpr (PRIMIN) pd[0] = neg_t(__ldg(ps + k * g.nint()));
     }
     if constexpr (PRIMIN) {
-      const int nint = g.nint();
-      const T* ps = a.prim_in + (int64_t)m.pidx * a.prim_stride + g.icell_kt(k, m.ck - 1, r);
-      T* pd = s.hp + f * 4 * ptr + r;
-      if (m.neg)
-        pd[0] = neg_t(__ldg(ps + k * nint));
-      else
-        cp_async_elem(pd, ps + k * nint);
 #pragma unroll
-      for (int v = 1; v < 4; ++v) cp_async_elem(pd + v * ptr, ps + (D + v - 1) * nint);
+      for (int v = 1; v < 4; ++v) cp_async_elem(pd + v * ptr, ps + (D + v - 1) * g.nint());
+    }
+  };
+  if constexpr (kGatherSlots<D, P, NT>()) {
+    // warp slots: a warp fetches cells of one face (one source, one
+    // direction: compile-time indexing, uniform branches)
+    const int spf = (ptr + 31) >> 5;  // slots per face
+    const int lane = threadIdx.x & 31;
+    for (int ws = threadIdx.x >> 5; ws < 2 * D * spf; ws += NT / 32) {
+      const int f = ws / spf;
+      const int r = (ws - f * spf) * 32 + lane;
+      const FaceSrc m = fs[f];
+      if (r < ptr) {
+        if (f < 2) {
+          cell(0, f, r, m);
+        } else if constexpr (D >= 2) {
+          if (f < 4) {
+            cell(1, f, r, m);
+          } else if constexpr (D == 3) {
+            cell(2, f, r, m);
+          }
+        }
+      }
+    }
+  } else {
+    for (int hc = threadIdx.x; hc < 2 * D * ptr; hc += NT) {
+      const int f = hc / ptr;
+      cell(f >> 1, f, hc - f * ptr, fs[f]);
     }
   }
   cp_async_commit();

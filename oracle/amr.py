@@ -52,7 +52,7 @@ def amr_halo_fill(q, off, p: int, d: int, level, coord, boundary: int = 0, halo:
         """Mean of the piecewise-constant solution over the box [lo, hi)
         (inside the domain: a periodic image is wrapped in first)."""
         vol = np.prod(hi - lo)
-        acc = np.zeros(s)
+        parts = []  # (value, overlap volume)
         olo = np.maximum(lo[None, :], org)
         ohi = np.minimum(hi[None, :], org + p * span[:, None])
         for j in np.nonzero(np.all(ohi > olo, axis=1))[0]:
@@ -63,7 +63,12 @@ def amr_halo_fill(q, off, p: int, d: int, level, coord, boundary: int = 0, halo:
                 clo = org[j] + cl * span[j]
                 w = np.prod(np.minimum(clo + span[j], hi) - np.maximum(clo, lo))
                 if w > 0:
-                    acc += interiors[j][tuple(cl[::-1])] * w
+                    parts.append((interiors[j][tuple(cl[::-1])], w))
+        if len(parts) == 1 and parts[0][1] == vol:  # one cell covers it: its value
+            return parts[0][0].copy()
+        acc = np.zeros(s)
+        for v, w in parts:
+            acc += v * w
         return acc / vol
 
     for i in range(n):

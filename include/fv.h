@@ -174,6 +174,32 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
                                    double cfl, double dx, double* dt_out);
 
 /*
+ * fv_patch_update_host -- fv_patch_update_batch on patches in HOST memory:
+ * the paper's offload pattern (the engine ships a batch of patches with
+ * their halos to the GPU for every update and takes the results back).  The
+ * batch is cut into chunks of chunk_patches consecutive patches (<= 0: about
+ * 64 MB per chunk); the copy in of a chunk, the update of the previous one
+ * and the copy out of the one before overlap (two copy streams, the
+ * handle's stream for the update, two device staging slots the handle keeps
+ * until fv_batch_destroy).
+ *   host_in, host_out  host buffers (pinned for overlap; pageable works,
+ *                      slower), the layout of fv_patch_update_batch; the
+ *                      interior cells of host_out receive Q^{n+1}, its halo
+ *                      cells a copy of host_in's.
+ *   patch_offsets, patch_sizes  HOST arrays; offsets must ascend without
+ *                      overlap (FV_ERR_INVALID_ARG), 16-byte multiples
+ *                      (FV_ERR_ALIGNMENT); sizes in 1..max_patch_size
+ *                      (FV_ERR_BAD_PATCH).
+ *   dx, dt             as for fv_patch_update_batch (dt <= 0: the device
+ *                      time step slot).
+ * Synchronous: returns when host_out holds the whole result.  Starts after
+ * the work already enqueued on the handle's stream.
+ */
+fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
+                               const int64_t* patch_offsets, const int32_t* patch_sizes,
+                               int64_t n_patches, double dx, double dt, int64_t chunk_patches);
+
+/*
  * fv_patch_update_local -- fv_patch_update_batch with a cell size and a time
  * step per patch (the batch descriptor of Sec. 3 carries both per patch):
  * patch i advances with Q - (dt_i / dx_i) sum (F_+ - F_-) (Eq. 3).

@@ -165,6 +165,7 @@ fv_status fv_batch_destroy(fv_batch* h) {
   cudaError_t e = cudaStreamSynchronize(h->stream);
   graph_cache_clear(h);
   fv::plan_free(h);
+  fv::host_stage_free(h);
   for (void* pbuf : h->d_prim)
     if (pbuf) cudaFree(pbuf);
   cudaError_t e2 = cudaFree(h->ws);

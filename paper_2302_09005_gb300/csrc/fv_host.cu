@@ -1,0 +1,238 @@
+// fv_host.cu -- the batched update with the patches in host memory: the
+// paper's offload pattern (the engine keeps the patches and their halos on
+// the host and ships a batch to the GPU for every update, Sec. 3) as a
+// pipeline.  The batch is cut into chunks of consecutive patches; chunk c is
+// copied host -> device on one copy stream, updated on the handle's stream
+// and copied device -> host on a second copy stream, so the copies of
+// neighbouring chunks overlap each other and the update of the chunk between
+// them.  Two device staging slots (input and output buffers, metadata) are
+// reused alternately; events order the reuse.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "fv_internal.h"
+
+struct fv_host_stage {
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_h2d[2] = {nullptr, nullptr};   // slot's input (and metadata) on the device
+  cudaEvent_t ev_comp[2] = {nullptr, nullptr};  // slot's update done
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};  // slot's output back on the host
+  bool used[2] = {false, false};
+  void* d_in[2] = {nullptr, nullptr};
+  void* d_out[2] = {nullptr, nullptr};
+  size_t bytes = 0;  // capacity of each buffer
+  int64_t* d_off[2] = {nullptr, nullptr};
+  int32_t* d_sz[2] = {nullptr, nullptr};
+  int64_t* h_off[2] = {nullptr, nullptr};  // pinned: rebased offsets of the chunk
+  int32_t* h_sz[2] = {nullptr, nullptr};
+  int64_t meta_cap = 0;
+};
+
+namespace fv {
+
+void host_stage_free(fv_batch* h) {
+  auto* st = static_cast<fv_host_stage*>(h->host_stage);
+  if (!st) return;
+  if (st->h2d) cudaStreamSynchronize(st->h2d);
+  if (st->d2h) cudaStreamSynchronize(st->d2h);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(st->d_in[k]);
+    cudaFree(st->d_out[k]);
+    cudaFree(st->d_off[k]);
+    cudaFree(st->d_sz[k]);
+    cudaFreeHost(st->h_off[k]);
+    cudaFreeHost(st->h_sz[k]);
+    if (st->ev_h2d[k]) cudaEventDestroy(st->ev_h2d[k]);
+    if (st->ev_comp[k]) cudaEventDestroy(st->ev_comp[k]);
+    if (st->ev_free[k]) cudaEventDestroy(st->ev_free[k]);
+  }
+  if (st->h2d) cudaStreamDestroy(st->h2d);
+  if (st->d2h) cudaStreamDestroy(st->d2h);
+  delete st;
+  h->host_stage = nullptr;
+}
+
+}  // namespace fv
+
+namespace {
+
+fv_status herr(fv_batch* h, fv_status st, const char* msg) {
+  snprintf(h->last_error, sizeof(h->last_error), "%s", msg);
+  return st;
+}
+
+// Grows the staging of a handle to chunks of `bytes` bytes and `npatch`
+// patches (never shrinks).
+cudaError_t stage_reserve(fv_batch* h, size_t bytes, int64_t npatch) {
+  auto* st = static_cast<fv_host_stage*>(h->host_stage);
+  cudaError_t e = cudaSuccess;
+  if (!st) {
+    st = new (std::nothrow) fv_host_stage();
+    if (!st) return cudaErrorMemoryAllocation;
+    h->host_stage = st;
+    e = cudaStreamCreateWithFlags(&st->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st->d2h, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&st->ev_h2d[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->ev_comp[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->ev_free[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (bytes > st->bytes) {
+    for (int k = 0; k < 2; ++k) {
+      if (st->used[k]) cudaEventSynchronize(st->ev_free[k]);
+      cudaFree(st->d_in[k]);
+      cudaFree(st->d_out[k]);
+      st->d_in[k] = st->d_out[k] = nullptr;
+    }
+    st->bytes = 0;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaMalloc(&st->d_in[k], bytes);
+      if (e == cudaSuccess) e = cudaMalloc(&st->d_out[k], bytes);
+    }
+    if (e != cudaSuccess) return e;
+    st->bytes = bytes;
+  }
+  if (npatch > st->meta_cap) {
+    for (int k = 0; k < 2; ++k) {
+      if (st->used[k]) cudaEventSynchronize(st->ev_free[k]);
+      cudaFree(st->d_off[k]);
+      cudaFree(st->d_sz[k]);
+      cudaFreeHost(st->h_off[k]);
+      cudaFreeHost(st->h_sz[k]);
+      st->d_off[k] = nullptr;
+      st->d_sz[k] = nullptr;
+      st->h_off[k] = nullptr;
+      st->h_sz[k] = nullptr;
+    }
+    st->meta_cap = 0;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaMalloc(&st->d_off[k], sizeof(int64_t) * (size_t)npatch);
+      if (e == cudaSuccess) e = cudaMalloc(&st->d_sz[k], sizeof(int32_t) * (size_t)npatch);
+      if (e == cudaSuccess) e = cudaMallocHost(&st->h_off[k], sizeof(int64_t) * (size_t)npatch);
+      if (e == cudaSuccess) e = cudaMallocHost(&st->h_sz[k], sizeof(int32_t) * (size_t)npatch);
+    }
+    if (e != cudaSuccess) return e;
+    st->meta_cap = npatch;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
+                               const int64_t* off, const int32_t* sizes, int64_t n, double dx,
+                               double dt, int64_t chunk_patches) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  h->last_error[0] = 0;
+  if (n < 0) return herr(h, FV_ERR_INVALID_ARG, "n_patches < 0");
+  if (n == 0) return FV_OK;
+  if (!host_in || !host_out || !off || !sizes)
+    return herr(h, FV_ERR_INVALID_ARG, "null pointer");
+  if (host_in == host_out) return herr(h, FV_ERR_INVALID_ARG, "in and out alias");
+  if (!(dx > 0.0) || dt != dt) return herr(h, FV_ERR_INVALID_ARG, "dx must be > 0, dt not NaN");
+  const size_t es = h->prec == FV_FP64 ? 8 : 4;
+  const int vec = (int)(16 / es);
+  const int d = h->d, s = h->s;
+  // patch extents; offsets must ascend (consecutive patches form a chunk)
+  auto len = [&](int64_t i) -> int64_t {
+    int64_t e = 1;
+    for (int m = 0; m < d; ++m) e *= sizes[i] + 2;
+    return e * s;
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    if (sizes[i] < 1 || sizes[i] > h->max_patch_size)
+      return herr(h, FV_ERR_BAD_PATCH, "patch size outside 1..max_patch_size");
+    if (off[i] < 0 || off[i] % vec) return herr(h, FV_ERR_ALIGNMENT, "patch offset");
+    if (i > 0 && off[i] < off[i - 1] + len(i - 1))
+      return herr(h, FV_ERR_INVALID_ARG, "patch offsets must ascend without overlap");
+  }
+  int64_t chunk = chunk_patches;
+  if (chunk <= 0) {  // about 64 MB per chunk
+    const int64_t per = len(0) * (int64_t)es;
+    chunk = (64ll << 20) / (per > 0 ? per : 1);
+    if (chunk < 1) chunk = 1;
+  }
+  if (chunk > n) chunk = n;
+  const int64_t nchunks = (n + chunk - 1) / chunk;
+  // the largest chunk in bytes (16-byte rounded)
+  size_t maxb = 0;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int64_t p0 = c * chunk, p1 = p0 + chunk < n ? p0 + chunk : n;
+    const size_t b = (size_t)(off[p1 - 1] + len(p1 - 1) - off[p0]) * es;
+    maxb = b > maxb ? b : maxb;
+  }
+  maxb = (maxb + 15) & ~(size_t)15;
+  cudaError_t e = stage_reserve(h, maxb, chunk);
+  if (e != cudaSuccess) return herr(h, FV_ERR_CUDA, cudaGetErrorString(e));
+  auto* st = static_cast<fv_host_stage*>(h->host_stage);
+  // the chunks start once the work already on the handle's stream is done
+  e = cudaEventRecord(st->ev_comp[0], h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st->h2d, st->ev_comp[0], 0);
+  for (int64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
+    const int k = (int)(c & 1);
+    const int64_t p0 = c * chunk, p1 = p0 + chunk < n ? p0 + chunk : n;
+    const int64_t nc = p1 - p0;
+    const int64_t base = off[p0];
+    const size_t bytes = (size_t)(off[p1 - 1] + len(p1 - 1) - base) * es;
+    // the slot's pinned metadata is free once its previous upload is done
+    if (st->used[k]) e = cudaEventSynchronize(st->ev_h2d[k]);
+    if (e != cudaSuccess) break;
+    for (int64_t i = 0; i < nc; ++i) {
+      st->h_off[k][i] = off[p0 + i] - base;
+      st->h_sz[k][i] = sizes[p0 + i];
+    }
+    // host -> device, once the slot's previous output has left
+    if (st->used[k]) e = cudaStreamWaitEvent(st->h2d, st->ev_free[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st->d_in[k], static_cast<const char*>(host_in) + base * es, bytes,
+                          cudaMemcpyHostToDevice, st->h2d);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st->d_off[k], st->h_off[k], sizeof(int64_t) * nc,
+                          cudaMemcpyHostToDevice, st->h2d);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st->d_sz[k], st->h_sz[k], sizeof(int32_t) * nc, cudaMemcpyHostToDevice,
+                          st->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(st->ev_h2d[k], st->h2d);
+    // update: the halo cells travel with the chunk; interior cells replaced
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, st->ev_h2d[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st->d_out[k], st->d_in[k], bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) {
+      fv::UpdateLaunch l;
+      l.in = st->d_in[k];
+      l.out = st->d_out[k];
+      l.off = st->d_off[k];
+      l.sizes = st->d_sz[k];
+      l.n = nc;
+      l.n_elems = (int64_t)(bytes / es);
+      l.pmax = h->max_patch_size;
+      l.gamma = h->gamma;
+      l.dx = dx;
+      l.dt = dt;
+      l.dt_dev = h->d_dt;
+      l.status = h->d_status;
+      l.fused = false;
+      e = fv::launch_scheduled(h, l);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(st->ev_comp[k], h->stream);
+    // device -> host
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st->d2h, st->ev_comp[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<char*>(host_out) + base * es, st->d_out[k], bytes,
+                          cudaMemcpyDeviceToHost, st->d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(st->ev_free[k], st->d2h);
+    st->used[k] = true;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->d2h);
+  if (e != cudaSuccess) return herr(h, FV_ERR_CUDA, cudaGetErrorString(e));
+  return FV_OK;
+}
+
+}  // extern "C"

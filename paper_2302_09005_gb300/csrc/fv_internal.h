@@ -44,6 +44,7 @@ struct fv_batch {
   int occ_cache[3][64][4] = {{{0}}};         // CTAs per SM by (kernel mode, p, CTA size)
   int cls_nt[64] = {0};                      // CTA size of the size-class launches (0: 128)
   int cls_only = -1;                         // autotuner: launch only this class (-1: all)
+  void* host_stage = nullptr;                // fv_patch_update_host: streams, staging buffers
   int smem_optin = 0;                        // opt-in shared memory per CTA
   char last_error[512] = {0};
 };
@@ -119,6 +120,8 @@ cudaError_t occupancy_nt(int d, int mode, int pmax, int nstage, int* bps);
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l);
 // Frees the schedule plan of a handle.
 void plan_free(fv_batch* h);
+// Frees the host-offload staging of a handle (fv_host.cu).
+void host_stage_free(fv_batch* h);
 
 struct EigLaunch {
   const void* q;

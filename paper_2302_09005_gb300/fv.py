@@ -71,6 +71,8 @@ def _lib() -> ctypes.CDLL:
         L.fv_patch_update_batch_ex.argtypes = [vp, vp, vp, vp, vp, i64, c_int, c_int, dbl, dbl,
                                                ctypes.POINTER(fv_update_extras)]
         L.fv_halo_fill.argtypes = [vp, vp, vp, vp, vp, i64]
+        L.fv_patch_update_host.argtypes = [vp, vp, vp, vp, vp, i64, dbl, dbl, i64]
+        L.fv_patch_update_host.restype = c_int
         L.fv_patch_update_local.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, dbl, vp]
         L.fv_patch_update_local.restype = c_int
         L.fv_amr_plan_create.argtypes = [vp, ctypes.POINTER(vp), i64, vp, vp, vp, c_int, c_int]
@@ -203,6 +205,20 @@ def fv_patch_update_batch_ex(h, in_with_halo, out, patch_offsets, patch_sizes, n
                                          _ptr(patch_sizes), n_patches, d, s, dx, dt,
                                          ctypes.byref(ex))
     _check(h, st, "fv_patch_update_batch_ex")
+
+
+def fv_patch_update_host(h, host_in, host_out, patch_offsets, patch_sizes, n_patches: int,
+                         dx: float, dt: float, chunk_patches: int = 0):
+    """host_in / host_out: host tensors (pinned for overlap) or numpy arrays;
+    patch_offsets / patch_sizes: host int64 / int32 arrays."""
+    import numpy as np
+    off = np.ascontiguousarray(np.asarray(patch_offsets), dtype=np.int64)
+    sz = np.ascontiguousarray(np.asarray(patch_sizes), dtype=np.int32)
+    def hptr(x):
+        return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+    st = _lib().fv_patch_update_host(h, hptr(host_in), hptr(host_out), off.ctypes.data,
+                                     sz.ctypes.data, n_patches, dx, dt, chunk_patches)
+    _check(h, st, "fv_patch_update_host")
 
 
 def fv_patch_update_local(h, in_with_halo, out, patch_offsets, patch_sizes, n_patches: int,

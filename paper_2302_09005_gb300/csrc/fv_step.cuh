@@ -397,6 +397,16 @@ __device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
 // ---------------------------------------------------------------------------
 // One patch: cells, faces, update.
 // ---------------------------------------------------------------------------
+// Whether the face loop walks lines of cells (pencils): each cell loaded once
+// for its two faces along the line, far fewer instructions per face but one
+// thread per line, so fewer busy lanes.  For FP32, which the instruction
+// count limits; FP64 is limited by its arithmetic pipe, which idle lanes
+// would waste.
+template <typename T, int D, int P, int NT>
+__host__ __device__ constexpr bool kPencilFaces() {
+  return sizeof(T) == 4 && P > 0 && D >= 2;
+}
+
 // Whether the face loop of a compile-time patch size runs in warp slots (one
 // direction per warp and iteration) rather than over all faces flat: when it
 // keeps at least as many lanes busy (to 2 %).
@@ -477,31 +487,39 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
   }
 
   // ---- faces: G = f_L + f_R - a (Q_R - Q_L), once per face -------------------
-  // Face (k, j) of the patch, j = tr + ptr b: between cells b and b+1 along k.
-  auto face = [&](const int k, const int j, unsigned long long& lmax) {
-    const int b = j / ptr;
-    const int tr = j - b * ptr;
-    const int cl = g.cell_kt(k, b, tr);
-    const int cr = cl + g.stride(k);
-    // primitives of the two cells: face-halo block at the patch boundary,
-    // interior block inside
-    const bool hl = b == 0, hrt = b == p;
-    const int icl = g.icell_kt(k, hl ? 0 : b - 1, tr);
-    const int icr = g.icell_kt(k, hrt ? p - 1 : b, tr);
-    const T* ul = hl ? hp + 8 * k * ptr + tr : ip + k * nint + icl;
-    const T* pl = hl ? hp + (8 * k + 1) * ptr + tr : ip + D * nint + icl;
-    const int sl = hl ? ptr : nint;
-    const T* ur = hrt ? hp + (8 * k + 4) * ptr + tr : ip + k * nint + icr;
-    const T* pr = hrt ? hp + (8 * k + 5) * ptr + tr : ip + D * nint + icr;
-    const int sr = hrt ? ptr : nint;
-    const T uL = ul[0], pL = pl[0], cL = pl[sl], eL = pl[2 * sl];
-    const T uR = ur[0], pR = pr[0], cR = pr[sr], eR = pr[2 * sr];
-    T qL[S], qR[S];
+  // Cell b (halo-inclusive, 0..p+1) along k at transverse index tr: its state
+  // and the primitives of direction k (face-halo block at the patch
+  // boundary, interior block inside).
+  struct CellK {
+    T q[S];
+    T u, pr, c, e;
+  };
+  // (lo / hi: whether b may be the lower / upper halo cell, constants at the
+  // call sites)
+  auto load_cell = [&](const int k, const int b, const int tr, CellK& x, const bool lo,
+                       const bool hi) {
+    const int cid = g.cell_kt(k, b, tr);
 #pragma unroll
-    for (int v = 0; v < S; ++v) {
-      qL[v] = st[cl * S + v];
-      qR[v] = st[cr * S + v];
-    }
+    for (int v = 0; v < S; ++v) x.q[v] = st[cid * S + v];
+    const bool h0 = lo && b == 0, h1 = hi && b == p + 1;
+    const int ic = g.icell_kt(k, h0 ? 0 : (h1 ? p - 1 : b - 1), tr);
+    const T* pu = h0 ? hp + 8 * k * ptr + tr
+                     : (h1 ? hp + (8 * k + 4) * ptr + tr : ip + k * nint + ic);
+    const T* pp_ = h0 ? hp + (8 * k + 1) * ptr + tr
+                      : (h1 ? hp + (8 * k + 5) * ptr + tr : ip + D * nint + ic);
+    const int sp = (h0 || h1) ? ptr : nint;
+    x.u = pu[0];
+    x.pr = pp_[0];
+    x.c = pp_[sp];
+    x.e = pp_[2 * sp];
+  };
+  // The flux of face j (k) between cells L and R, stored into G.
+  auto flux = [&](const int k, const int j, const CellK& L, const CellK& R,
+                  unsigned long long& lmax) {
+    const T uL = L.u, pL = L.pr, cL = L.c, eL = L.e;
+    const T uR = R.u, pR = R.pr, cR = R.c, eR = R.e;
+    const T* qL = L.q;
+    const T* qR = R.q;
     // a = max(|u_k| + c) over the two cells (Eq. 5)
     const T am = max_by_bits(ar.add(abs_t(uL), cL), ar.add(abs_t(uR), cR));
     const unsigned long long ab = order_bits(am);
@@ -531,8 +549,49 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
       Gk[v * nface + j] = gv;
     }
   };
+  // Face (k, j) of the patch, j = tr + ptr b: between cells b and b+1 along k.
+  auto face = [&](const int k, const int j, unsigned long long& lmax) {
+    const int b = j / ptr;
+    const int tr = j - b * ptr;
+    CellK L, R;
+    load_cell(k, b, tr, L, true, false);
+    load_cell(k, b + 1, tr, R, false, true);
+    flux(k, j, L, R, lmax);
+  };
+  // All faces of one line of cells along k (transverse index tr), walking b:
+  // every cell is loaded once and serves its two faces.
+  auto pencil = [&](const int k, const int tr, unsigned long long& lmax) {
+    CellK A, B;
+    load_cell(k, 0, tr, A, true, false);
+    for (int b = 0; b <= p; b += 2) {
+      load_cell(k, b + 1, tr, B, false, true);
+      flux(k, tr + ptr * b, A, B, lmax);
+      if (b + 1 > p) break;
+      load_cell(k, b + 2, tr, A, false, true);
+      flux(k, tr + ptr * (b + 1), B, A, lmax);
+    }
+  };
   unsigned long long lmax = 0ull;
-  if constexpr (kWarpSlots<D, P, NT>()) {
+  if constexpr (kPencilFaces<T, D, P, NT>()) {
+    // pencils in warp slots: a warp takes 32 lines of one direction
+    const int spk = (ptr + 31) >> 5;
+    const int lane = tid & 31;
+    for (int ws = tid >> 5; ws < D * spk; ws += NT / 32) {
+      const int k = ws / spk;
+      const int tr = (ws - k * spk) * 32 + lane;
+      if (tr < ptr) {
+        if (k == 0) {
+          pencil(0, tr, lmax);
+        } else if constexpr (D >= 2) {
+          if (k == 1) {
+            pencil(1, tr, lmax);
+          } else if constexpr (D == 3) {
+            pencil(2, tr, lmax);
+          }
+        }
+      }
+    }
+  } else if constexpr (kWarpSlots<D, P, NT>()) {
     // warp slots: a warp takes 32 faces of one direction, so k is the same in
     // every lane and compiles to constants (strides, cell indexing, the
     // momentum with the pressure term)

@@ -54,7 +54,8 @@ def run_update(fv, q, off, sz, d, dx, dt, *, prec=0, pmax=0, want_lambda=False, 
 @pytest.mark.parametrize("d,p,n,seed", [(2, 3, 64, 0), (3, 5, 200, 1), (2, 5, 150, 2),
                                         (2, 8, 60, 3), (3, 3, 300, 4), (3, 7, 40, 5),
                                         (2, 17, 12, 6), (2, 4, 33, 7), (3, 4, 17, 8),
-                                        (1, 6, 40, 9), (3, 1, 50, 10), (2, 1, 9, 11)])
+                                        (1, 6, 40, 9), (3, 1, 50, 10), (2, 1, 9, 11),
+                                        (3, 8, 12, 12), (2, 16, 10, 13)])
 def test_update_fp64_matches_oracle(fv, d, p, n, seed):
     s = d + 2
     q, off, sz = fvtest.random_batch(n, p, d, seed)
@@ -83,7 +84,7 @@ def test_update_ragged_sizes_one_launch(fv):
     assert np.allclose(lam, lam_ref, rtol=TOL_MAX, atol=0)
 
 
-@pytest.mark.parametrize("d,p,n", [(2, 3, 64), (3, 5, 100), (2, 5, 80)])
+@pytest.mark.parametrize("d,p,n", [(2, 3, 64), (3, 5, 100), (2, 5, 80), (3, 8, 12), (2, 17, 9)])
 def test_update_fp32_within_1e5(fv, d, p, n):
     s = d + 2
     q32, off, sz = fvtest.random_batch(n, p, d, 13, np.float32)

@@ -59,7 +59,8 @@ def run_carry(fv, b, q, toff, tsz, tnbr, dx, cfl, steps, prec, lam=None):
 @pytest.mark.parametrize("d,p,grid,periodic,bnd", [
     (3, 5, (6, 5, 4), True, -1), (2, 3, (8, 8), True, -1), (2, 5, (5, 4), False, -1),
     (3, 3, (3, 4, 3), False, -2), (2, 8, (3, 3), False, -2), (1, 4, (9,), True, -1),
-    (1, 6, (5,), False, -2), (3, 4, (3, 3, 3), True, -1)])
+    (1, 6, (5,), False, -2), (3, 4, (3, 3, 3), True, -1), (3, 8, (2, 3, 2), True, -1),
+    (2, 17, (3, 2), False, -2)])
 def test_carry_equals_plain_time_steps_bitwise(fv, prec, d, p, grid, periodic, bnd):
     torch = fvtest.torch_cuda()
     dtype = np.float32 if prec else np.float64

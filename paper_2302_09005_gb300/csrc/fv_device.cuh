@@ -152,8 +152,11 @@ __device__ __forceinline__ Arith<T> plain_arith() {
 // result (measured by fv_selftest_math against the IEEE operations), far
 // inside the 1e-12 tolerance of the update.  Arguments outside the float
 // exponent range (and zero, negative, non-finite values) take the IEEE
-// operation.  The FP32 path keeps the IEEE forms: it is bound by memory
-// traffic and instruction issue, not by FP32 arithmetic.
+// operation.  The FP32 forms are the special-function unit's approximations
+// themselves (one instruction each, within about an ulp and two ulps): the
+// FP32 path is bound by instruction issue, where the IEEE sequences cost
+// about ten instructions per cell each, and its error target (1e-5 after a
+// step) is far above an ulp of FP32.
 // ---------------------------------------------------------------------------
 
 // Double -> float carrying the double's leading 20 fraction bits (truncated);
@@ -183,7 +186,9 @@ __device__ __forceinline__ double recip(double a, const Arith<double>& ar = plai
   return fma(y, t, y);
 }
 __device__ __forceinline__ float recip(float a, const Arith<float>& = plain_arith<float>()) {
-  return 1.0f / a;
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
 }
 
 __device__ __forceinline__ double sqrt_t(double x, const Arith<double>& ar = plain_arith<double>()) {
@@ -198,7 +203,9 @@ __device__ __forceinline__ double sqrt_t(double x, const Arith<double>& ar = pla
   return fma(s0, t, s0);
 }
 __device__ __forceinline__ float sqrt_t(float x, const Arith<float>& = plain_arith<float>()) {
-  return sqrtf(x);
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 // ---------------------------------------------------------------------------

@@ -44,6 +44,9 @@ struct fv_batch {
   int occ_cache[3][64][4] = {{{0}}};         // CTAs per SM by (kernel mode, p, CTA size)
   int cls_nt[64] = {0};                      // CTA size of the size-class launches (0: 128)
   int cls_only = -1;                         // autotuner: launch only this class (-1: all)
+  int cls_real[64] = {0};                    // class c holds one valid size (not the rejects)
+  int occ_pairs[3] = {0, 0, 0};              // CTAs per SM of the FP32 pairs kernel, by mode
+  int64_t pairs_launches = 0;                // launches that used the FP32 pairs kernel
   void* host_stage = nullptr;                // fv_patch_update_host: streams, staging buffers
   int smem_optin = 0;                        // opt-in shared memory per CTA
   char last_error[512] = {0};
@@ -81,6 +84,7 @@ struct UpdateLaunch {
   const void* prim_in = nullptr;  // time step: carried primitives of `in`, or null
   void* prim_out = nullptr;       // time step: primitives of `out`, or null
   int64_t prim_stride = 0;        // elements per patch of the primitive buffers
+  int uniform_p = 0;              // every patch of the launch has this size (0: unknown)
 };
 
 // Kernel modes: update (halos filled by the caller), time step (halo gather,
@@ -116,6 +120,12 @@ template <typename T, int NT>
 cudaError_t launch_step_nt(const fv_batch* h, const UpdateLaunch& l, int grid);
 template <typename T, int NT>
 cudaError_t occupancy_nt(int d, int mode, int pmax, int nstage, int* bps);
+// The FP32 kernel for launches of one 3D patch size (fv_pairs.cu): whether a
+// size class / a launch can use it, its launch and its occupancy.
+bool pairs_class(const fv_batch* h, int p);
+bool pairs_eligible(const fv_batch* h, const UpdateLaunch& l);
+cudaError_t launch_pairs(const fv_batch* h, const UpdateLaunch& l, int grid);
+cudaError_t pairs_occupancy(int mode, int* blocks_per_sm);
 // Launches the update / time-step kernel(s) under the handle's schedule.
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l);
 // Frees the schedule plan of a handle.

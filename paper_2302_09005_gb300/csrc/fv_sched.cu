@@ -60,6 +60,22 @@ static int grid_for(const fv_batch* h, int64_t count, int bps) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// A launch of patches of one size: the FP32 pairs kernel where it applies.
+static cudaError_t launch_one_size(fv_batch* h, const UpdateLaunch& l, int64_t count,
+                                   bool* done) {
+  *done = false;
+  if (!pairs_eligible(h, l)) return cudaSuccess;
+  const int f = step_mode(l);
+  int& bps = h->occ_pairs[f];
+  if (bps == 0) {
+    cudaError_t e = pairs_occupancy(f, &bps);
+    if (e != cudaSuccess) return e;
+  }
+  *done = true;
+  ++h->pairs_launches;
+  return launch_pairs(h, l, grid_for(h, count, bps));
+}
+
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
   const bool plan_ok = h->d_order != nullptr && h->plan_n == l.n && h->plan_sizes == l.sizes;
   const int f = step_mode(l);
@@ -72,6 +88,13 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
       lc.i_begin = h->cls_begin[c];
       lc.i_end = h->cls_end[c];
       lc.pmax = h->cls_p[c];
+      if (h->cls_real[c]) {
+        lc.uniform_p = lc.pmax;
+        bool done = false;
+        cudaError_t e = launch_one_size(h, lc, cnt, &done);
+        if (e != cudaSuccess) return e;
+        if (done) continue;
+      }
       lc.nstage = stages_for(h, lc.pmax);
       const int pi = lc.pmax < 64 ? lc.pmax : 63;
       lc.nt = h->cls_nt[pi] > 0 ? h->cls_nt[pi] : 128;
@@ -84,6 +107,14 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+  }
+  if (plan_ok && h->ncls == 1 && h->cls_real[0]) {  // a planned batch of one size
+    UpdateLaunch lu = l;
+    lu.uniform_p = h->cls_p[0];
+    lu.pmax = h->cls_p[0];
+    bool done = false;
+    cudaError_t e = launch_one_size(h, lu, l.n, &done);
+    if (e != cudaSuccess || done) return e;
   }
   int& bps = h->blocks_per_sm[f];
   if (bps == 0) {
@@ -147,6 +178,7 @@ fv_status fv_batch_plan(fv_batch* h, const int32_t* sizes, int64_t n) {
     start[p] = pos;
     if (host[p] > 0) {
       h->cls_p[h->ncls] = p;
+      h->cls_real[h->ncls] = 1;
       h->cls_begin[h->ncls] = (int64_t)pos;
       h->cls_end[h->ncls] = (int64_t)(pos + host[p]);
       ++h->ncls;
@@ -156,6 +188,7 @@ fv_status fv_batch_plan(fv_batch* h, const int32_t* sizes, int64_t n) {
   start[pmax + 1] = pos;
   if (host[pmax + 1] > 0) {  // rejected sizes: the kernels flag and skip them
     h->cls_p[h->ncls] = pmax;
+    h->cls_real[h->ncls] = 0;
     h->cls_begin[h->ncls] = (int64_t)pos;
     h->cls_end[h->ncls] = (int64_t)(pos + host[pmax + 1]);
     ++h->ncls;
@@ -195,6 +228,12 @@ fv_status fv_batch_set_class_threads(fv_batch* h, int p, int threads) {
 fv_status fv_batch_class_threads(const fv_batch* h, int p, int* threads) {
   if (!h || !threads || p < 1 || p >= 64) return FV_ERR_INVALID_ARG;
   *threads = h->cls_nt[p] > 0 ? h->cls_nt[p] : 128;
+  return FV_OK;
+}
+
+fv_status fv_batch_pairs_launches(const fv_batch* h, int64_t* launches) {
+  if (!h || !launches) return FV_ERR_INVALID_ARG;
+  *launches = h->pairs_launches;
   return FV_OK;
 }
 
@@ -248,6 +287,7 @@ fv_status fv_batch_autotune(fv_batch* h, const void* in, void* scratch_out, cons
   // 1. the CTA size of each size class (one-class launches)
   h->sched = FV_SCHED_CLASSES;
   for (int c = 0; c < h->ncls && st == FV_OK; ++c) {
+    if (h->cls_real[c] && fv::pairs_class(h, h->cls_p[c])) continue;  // fixed 128 threads
     const int pi = h->cls_p[c] < 64 ? h->cls_p[c] : 63;
     const int keep = h->cls_nt[pi];
     double best_c = 1e300;

@@ -199,17 +199,14 @@ __device__ __forceinline__ void issue_stage(const StepParams<T>& a, int64_t pid,
   if constexpr (PRIMIN) bulk_copy_g2s(st.ip, a.prim_in + pid * a.prim_stride, pbytes, bar);
 }
 
-// Threads 0 .. 2d-1: resolve the sources of the 2d faces of patch j once (the
-// neighbour table and the neighbour's metadata are read and checked here, not
-// per halo element).  Time-step modes follow the rules of fv_halo_fill;
-// update mode with d = 1 re-reads the patch's own halo cells.
+// The source of the halo cells of face f of patch j (the neighbour table and
+// the neighbour's metadata are read and checked here once, not per halo
+// element).  Time-step modes follow the rules of fv_halo_fill; update mode
+// with d = 1 re-reads the patch's own halo cells.
 template <typename T, int D, bool GATHER>
-__device__ __forceinline__ void face_sources(const StepParams<T>& a, int64_t j, int pj,
-                                             int64_t offj, FaceSrc* fs) {
-  if constexpr (!GATHER && D != 1) return;
+__device__ __forceinline__ FaceSrc face_source(const StepParams<T>& a, int64_t j, int pj,
+                                               int64_t offj, int f) {
   constexpr int VEC = 16 / sizeof(T);
-  const int f = threadIdx.x;
-  if (f >= 2 * D) return;
   const int side = f & 1;
   FaceSrc r;
   r.off = offj;
@@ -242,7 +239,17 @@ __device__ __forceinline__ void face_sources(const StepParams<T>& a, int64_t j, 
       atomicOr(a.status, ST_BAD_PATCH);
     }
   }
-  fs[f] = r;
+  return r;
+}
+
+// Threads 0 .. 2d-1: the sources of the 2d faces of patch j.
+template <typename T, int D, bool GATHER>
+__device__ __forceinline__ void face_sources(const StepParams<T>& a, int64_t j, int pj,
+                                             int64_t offj, FaceSrc* fs) {
+  if constexpr (!GATHER && D != 1) return;
+  const int f = threadIdx.x;
+  if (f >= 2 * D) return;
+  fs[f] = face_source<T, D, GATHER>(a, j, pj, offj, f);
 }
 
 // Whether the halo gather of a compile-time patch size runs in warp slots

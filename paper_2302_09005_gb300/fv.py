@@ -108,6 +108,8 @@ def _lib() -> ctypes.CDLL:
         L.fv_batch_set_class_threads.restype = c_int
         L.fv_batch_class_threads.argtypes = [vp, c_int, ctypes.POINTER(c_int)]
         L.fv_batch_class_threads.restype = c_int
+        L.fv_batch_pairs_launches.argtypes = [vp, ctypes.POINTER(i64)]
+        L.fv_batch_pairs_launches.restype = c_int
         L.fv_batch_autotune.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl,
                                         ctypes.POINTER(c_int), ctypes.POINTER(dbl)]
         L.fv_batch_autotune.restype = c_int
@@ -352,6 +354,13 @@ def fv_batch_set_class_threads(h, p: int, threads: int):
 def fv_batch_class_threads(h, p: int) -> int:
     out = ctypes.c_int(0)
     _check(h, _lib().fv_batch_class_threads(h, p, ctypes.byref(out)), "fv_batch_class_threads")
+    return int(out.value)
+
+
+def fv_batch_pairs_launches(h) -> int:
+    """Launches of the handle that ran on the FP32 kernel for one patch size."""
+    out = ctypes.c_int64(0)
+    _check(h, _lib().fv_batch_pairs_launches(h, ctypes.byref(out)), "fv_batch_pairs_launches")
     return int(out.value)
 
 

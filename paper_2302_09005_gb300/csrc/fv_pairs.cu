@@ -9,23 +9,24 @@
 //    completion) as cells of 5 unknowns; the halo cells from the neighbours
 //    are gathered with cp.async.  The cells then convert once, to shared
 //    structure-of-arrays form: the state (rho, j, E) and the primitives
-//    (u, p, c, E + p) of every interior and face-halo cell, each quantity a
-//    box of x rows padded to a multiple of four floats with cell x at
-//    column x + 1, so that a thread reads a whole x row of a quantity with
-//    128-bit loads, and two x-neighbours with one 64-bit load;
+//    (u_y, u_z, p, c) of the interior and face-halo cells the y and z
+//    faces and the update read, laid out so that two x-neighbours come with
+//    one 64-bit load and the lanes of a warp hit distinct banks;
 //  * packed arithmetic: two x-neighbouring cells (or faces) are computed
 //    together with the f32x2 instructions (fv_x2.cuh): one instruction for
 //    both elements, each rounded as the scalar operation;
 //  * fixed indexing: every patch of the launch has the same size, so each
 //    thread's cells, faces and shared-memory offsets are computed once per
 //    launch, before the patch loop;
-//  * roles: all warps convert the cells (x pairs); warp 0 then walks the x
-//    lines of cells (a row in registers, every face once, scalar), warp 1
-//    the y and z lines in x pairs (packed), each keeping the flux difference
-//    G+ - G- of every cell of its line, while warps 2 and 3 gather the halo
-//    cells of the next patch; warps 0-2 then update the cells in x pairs
-//    (three differences per unknown, fixed order x, y, z) and convert the
-//    new state for the next CFL maximum;
+//  * roles: all warps convert the cells (x pairs); the items of the interior
+//    rows also compute the x faces between their cells and the next item's
+//    (neighbours exchange cells with warp shuffles) and keep the flux
+//    difference G+ - G- of each cell in registers; warps 0 and 1 then walk
+//    the y and z lines in x-pairs, each line in two halves on two lanes,
+//    while warps 2 and 3 gather the halo cells of the next patch; the
+//    interior-row threads then update their pairs (three differences per
+//    unknown, fixed order x, y, z) and convert the new state for the next
+//    CFL maximum;
 //  * two box buffers: a patch's bulk copy starts two patches ahead, its
 //    halo gather one patch ahead.
 #include "fv_step.cuh"
@@ -46,25 +47,33 @@ struct PairGeom {
   static_assert(P % 2 == 1 && P >= 3, "odd patch sizes");
   static constexpr int S = 5;                       // unknowns (3D Euler)
   static constexpr int NE = P + 2;                  // box cells per axis
-  static constexpr int PX = (P + 3 + 3) / 4 * 4;    // SoA row pitch (cell x at column x + 1)
-  static constexpr int NSL = PX * NE * NE;          // floats per SoA quantity
+  // SoA layout: cells x = 1 .. P+1 of a row (x = 0 and -1 never leave
+  // registers) at columns x - 1; rows of RP floats, planes of PZ floats.
+  // PZ is the smallest pitch >= RP * NE with PZ = -RP (mod 32): the P rows
+  // of a y line pair, or of a z line pair, then fall on distinct banks.
+  static constexpr int RP = P + 1;
+  static constexpr int PZ = RP * NE + ((32 - RP) - (RP * NE) % 32 + 64) % 32;
+  static constexpr int NSL = PZ * NE;               // floats per SoA quantity
   static constexpr int HP = (P + 1) / 2;            // x pairs of interior cells per row
   static constexpr int DP = 2 * HP;                 // flux-difference slots per row
   static constexpr int NROW = P * P;                // interior x rows
-  static constexpr int NDG = 3 * S * NROW * DP;     // flux differences [k][v][row][slot]
+  static constexpr int NDG = 2 * S * NROW * DP;     // y, z flux differences [k-1][v][row][slot]
   static constexpr int BOX = NE * NE * NE * S;      // cells of the staged box
   static constexpr int BOXP = (BOX + 3) / 4 * 4;
-  // conversion items: x pairs of the interior rows (with their x halos) and
-  // of the face-halo rows
-  static constexpr int NA = NROW * (HP + 1) + 4 * P * HP;
-  static constexpr int NYZ = 2 * P * HP;            // y and z line pairs
+  // conversion items: x pairs of the interior rows (with their x halos),
+  // which also compute the x faces, then those of the face-halo rows
+  static constexpr int NRI = NROW * (HP + 1);       // interior-row items
+  static constexpr int NA = NRI + 4 * P * HP;
+  static constexpr int NHL = P * HP;                // y (or z) line pairs
+  static constexpr int HA = (P + 1) / 2;            // faces of the first half of a line
   static constexpr int NC = NROW * HP;              // update items
   static constexpr int NT = 128;
   static constexpr int RA = (NA + NT - 1) / NT;     // conversion rounds
-  // SoA quantities: state, velocities, p, c, E + p
-  static constexpr int AQ = 0, AU = 5, APR = 8, ACS = 9, AEP = 10, NARR = 11;
+  // SoA quantities: state, u_y, u_z, p, c (E + p is recomputed from E and p
+  // where it is read: the same add as in the conversion, the same bits)
+  static constexpr int AQ = 0, AUY = 5, APR = 7, ACS = 8, NARR = 9;
   static constexpr int SMEM = kHdrBytes + 4 * (2 * BOXP + NARR * NSL + NDG);
-  static_assert(NROW <= 32 && NYZ <= 32 && NC <= 96, "roles sized for P <= 5");
+  static_assert(NRI <= NT && NHL <= 16 && NC <= 96 && RA == 2, "roles sized for P = 5");
 };
 
 __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
@@ -116,7 +125,7 @@ constexpr unsigned kBadChk = 0x7F7FFFFFu;
 // A conversion item: two x-neighbouring cells of the box.
 struct ItemA {
   int aos;    // float offset of the first cell in the staged box
-  int slot;   // SoA column of the first cell (even)
+  int slot;   // SoA slot of the first cell (even), or -1: not stored
   int valid;  // bit 0 / bit 1: the first / second cell is needed; 0: no item
 };
 template <int P>
@@ -148,25 +157,63 @@ __device__ __forceinline__ ItemA item_a(int t) {
   }
   const int x0 = 2 * j - 1;
   it.aos = (x0 + G::NE * (y + G::NE * z)) * G::S;
-  it.slot = 2 * j + G::PX * (y + G::NE * z);
+  it.slot = j > 0 ? 2 * j - 2 + G::RP * y + G::PZ * z : -1;  // x = -1, 0: registers only
   it.valid = (vlo ? 1 : 0) | (vhi ? 2 : 0);
   return it;
 }
+
+// Two cells (or x-neighbouring lines) of a direction k as pairs: state with
+// the momenta as (first transverse, normal, second transverse), and the
+// primitives u_k, p, c, E + p.
+struct Cell2 {
+  f2 q0, qt1, qn, qt2, q4, u, p, c, e;
+};
+// The face fluxes G = 2F of two faces at once (Eq. 4, 5), in the operation
+// order of the general kernel (fv_step.cuh).  g: rho, first transverse,
+// normal, second transverse momentum, E.  bl / bh: bits of a per half.
+__device__ __forceinline__ void flux2(const Cell2& L, const Cell2& R, f2 (&g)[5], unsigned& bl,
+                                      unsigned& bh) {
+  float uLl, uLh, cLl, cLh, uRl, uRh, cRl, cRh;
+  f2_unpack(L.u, uLl, uLh);
+  f2_unpack(L.c, cLl, cLh);
+  f2_unpack(R.u, uRl, uRh);
+  f2_unpack(R.c, cRl, cRh);
+  bl = umax(wave_bits(uLl, cLl), wave_bits(uRl, cRl));
+  bh = umax(wave_bits(uLh, cLh), wave_bits(uRh, cRh));
+  const f2 am = f2_pack(__uint_as_float(bl), __uint_as_float(bh));
+  const f2 sL = add2(L.u, am), sR = sub2(R.u, am), ps = add2(L.p, R.p);
+  g[0] = fma2(L.q0, sL, mul2(R.q0, sR));
+  g[1] = fma2(L.qt1, sL, mul2(R.qt1, sR));
+  g[2] = fma2(L.qn, sL, fma2(R.qn, sR, ps));
+  g[3] = fma2(L.qt2, sL, mul2(R.qt2, sR));
+  g[4] = fma2(am, sub2(L.q4, R.q4), fma2(L.e, L.u, mul2(R.e, R.u)));
+}
+
+// A patch of the processing sequence: position, index, element offset.
+struct Pat {
+  long long pos, pid, off;
+};
+constexpr int kInfoOff = 448;  // shared slot of the patch two ahead
+static_assert(kFaceSrcOff + 2 * 6 * (int)sizeof(FaceSrc) <= kInfoOff &&
+                  kInfoOff + (int)sizeof(Pat) <= kHdrBytes,
+              "header layout");
 
 // The copy pipeline: two box buffers, each filled by a bulk copy (completion
 // on its own mbarrier) and then by the halo gather.  The copy of a patch
 // starts two patches ahead, as soon as its buffer has been converted; its
 // halo cells are gathered one patch ahead, by warps 2 and 3 while warps 0
-// and 1 compute the face fluxes.
+// and 1 compute the y and z face fluxes.
 template <int P, bool STEP>
 __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepParams<float> a) {
   using G = PairGeom<P>;
-  constexpr int S = G::S, NE = G::NE, PX = G::PX, NSL = G::NSL, HP = G::HP, DP = G::DP,
-                NROW = G::NROW;
+  constexpr int S = G::S, NE = G::NE, RP = G::RP, PZ = G::PZ, NSL = G::NSL, HP = G::HP,
+                DP = G::DP, NROW = G::NROW;
+  constexpr unsigned FULL = 0xFFFFFFFFu;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // one per box buffer
   unsigned long long* red = reinterpret_cast<unsigned long long*>(smem_raw + kRedOff);
   FaceSrc* fs = reinterpret_cast<FaceSrc*>(smem_raw + kFaceSrcOff);  // [buffer][face]
+  Pat* info = reinterpret_cast<Pat*>(smem_raw + kInfoOff);
   float* const box0 = reinterpret_cast<float*>(smem_raw + kHdrBytes);
   float* const soa = box0 + 2 * G::BOXP;
   float* const dg = soa + G::NARR * NSL;
@@ -193,22 +240,18 @@ __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepPara
   }
   __syncthreads();
 
-  auto pid_of = [&](int64_t pos) -> int64_t {
-    return a.order != nullptr ? (int64_t)a.order[pos] : pos;
-  };
-  struct Pat {
-    int64_t pos, pid, off;
-  };
-  // the first valid position at or after `pos` (this CTA's stride)
-  auto next_valid = [&](int64_t pos) -> Pat {
+  // the first valid position at or after `pos` (this CTA's stride); patches
+  // that are invalid or of another size are reported and skipped
+  auto next_valid = [&](long long pos) -> Pat {
     Pat r{pos, 0, 0};
-    int pj = 0;
     while (r.pos < a.i_end) {
-      r.pid = pid_of(r.pos);
-      if (patch_ok<float, 3>(a, r.pid, pj, r.off)) {
-        if (pj == P) break;
-        if (tid == 0) atomicOr(a.status, ST_BAD_PATCH);
-      }
+      r.pid = a.order != nullptr ? (long long)a.order[r.pos] : r.pos;
+      int pj = 0;
+      int64_t offj = 0;
+      const bool ok = patch_ok<float, 3>(a, r.pid, pj, offj);
+      r.off = offj;
+      if (ok && pj == P) break;
+      atomicOr(a.status, ST_BAD_PATCH);
       r.pos += gridDim.x;
     }
     return r;
@@ -267,7 +310,7 @@ __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepPara
   };
 
   Pat cur = next_valid(a.i_begin + blockIdx.x);
-  Pat nx1 = next_valid(cur.pos + gridDim.x);
+  Pat nx1 = cur.pos < a.i_end ? next_valid(cur.pos + gridDim.x) : cur;
   int s = 0;  // buffer of the current patch
   if (cur.pos < a.i_end) {
     if (tid == 0) issue_box(cur, 0);
@@ -282,194 +325,186 @@ __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepPara
   timeout = __syncthreads_or(timeout);
   if (timeout) cur.pos = a.i_end;
 
-  // per-thread indexing, fixed for the launch
-  ItemA ia[G::RA];
-#pragma unroll
-  for (int r = 0; r < G::RA; ++r) ia[r] = item_a<P>(tid + r * G::NT);
+  // this thread's conversion items; the interior-row ones (round 0, t < NRI)
+  // also compute the faces of the row between their cells and the next item's
+  const ItemA ia0 = item_a<P>(tid), ia1 = item_a<P>(tid + G::NT);
+  const bool xrow = tid < G::NRI;
+  const int xr = tid / (HP + 1), xj = tid - (tid / (HP + 1)) * (HP + 1);
+  const unsigned mflo = (xrow && xj >= 1) ? kMagMask : 0u;      // face x0 | x0+1 exists
+  const unsigned mfhi = (xrow && xj <= HP - 1) ? kMagMask : 0u;  // face x0+1 | x0+2 exists
 
   while (cur.pos < a.i_end) {
-    const Pat nx2 = nx1.pos < a.i_end ? next_valid(nx1.pos + gridDim.x) : nx1;
     float* const box = box0 + s * G::BOXP;
+    unsigned lmax = 0u;
+    f2 dgx[5];  // x flux differences of this thread's update pair
 
-    // ---- cells: state and primitives to SoA, two x-neighbours per item ----
+    // ---- cells: state and primitives to SoA, two x-neighbours per item;
+    //      the x faces of the interior rows ------------------------------------
+    {
+      f2 q[5];
 #pragma unroll
-    for (int r = 0; r < G::RA; ++r) {
-      const ItemA it = ia[r];
-      if (it.valid) {
-        f2 q[5];
-#pragma unroll
-        for (int v = 0; v < S; ++v) q[v] = f2_pack(box[it.aos + v], box[it.aos + S + v]);
-        const Prim2 w = prims2(q, gm1, gam, mhalf, (it.valid & 1) ? ~0u : 0u,
-                               (it.valid & 2) ? ~0u : 0u, chk);
-        float* d = soa + it.slot;
+      for (int v = 0; v < S; ++v) q[v] = f2_pack(box[ia0.aos + v], box[ia0.aos + S + v]);
+      const Prim2 w = prims2(q, gm1, gam, mhalf, (ia0.valid & 1) ? ~0u : 0u,
+                             (ia0.valid & 2) ? ~0u : 0u, chk);
+      if (ia0.slot >= 0) {
+        float* d = soa + ia0.slot;
 #pragma unroll
         for (int v = 0; v < S; ++v) st2(d + (G::AQ + v) * NSL, q[v]);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) st2(d + (G::AU + m) * NSL, w.u[m]);
+        st2(d + G::AUY * NSL, w.u[1]);
+        st2(d + (G::AUY + 1) * NSL, w.u[2]);
         st2(d + G::APR * NSL, w.p);
         st2(d + G::ACS * NSL, w.c);
-        st2(d + G::AEP * NSL, w.e);
       }
+      // faces (x0 | x0+1) and (x0+1 | x0+2): left cells = this pair, right
+      // cells = (second cell, the next item's first cell)
+      auto nxt = [&](f2 v) {
+        float lo, hi;
+        f2_unpack(v, lo, hi);
+        return f2_pack(hi, __shfl_down_sync(FULL, lo, 1));
+      };
+      const Cell2 L{q[0], q[2], q[1], q[3], q[4], w.u[0], w.p, w.c, w.e};
+      const Cell2 R{nxt(q[0]), nxt(q[2]), nxt(q[1]), nxt(q[3]), nxt(q[4]),
+                    nxt(w.u[0]), nxt(w.p), nxt(w.c), nxt(w.e)};
+      f2 g[5];
+      unsigned bl, bh;
+      flux2(L, R, g, bl, bh);
+      lmax = umax(lmax, bl & mflo);
+      lmax = umax(lmax, bh & mfhi);
+      // flux differences of cells x0 (G(x0+1/2) - G(x0-1/2), the latter the
+      // previous item's second face) and x0+1, kept for the update of this
+      // pair, which this thread does (with the pair's state)
+      constexpr int PV[5] = {0, 2, 1, 3, 4};  // unknown of g[i]
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        float gl, gh;
+        f2_unpack(g[i], gl, gh);
+        const float gprev = __shfl_up_sync(FULL, gh, 1);
+        dgx[PV[i]] = f2_pack(sub_rn(gl, gprev), sub_rn(gh, gl));
+      }
+    }
+    if (ia1.valid) {
+      f2 q[5];
+#pragma unroll
+      for (int v = 0; v < S; ++v) q[v] = f2_pack(box[ia1.aos + v], box[ia1.aos + S + v]);
+      const Prim2 w = prims2(q, gm1, gam, mhalf, (ia1.valid & 1) ? ~0u : 0u,
+                             (ia1.valid & 2) ? ~0u : 0u, chk);
+      float* d = soa + ia1.slot;
+#pragma unroll
+      for (int v = 0; v < S; ++v) st2(d + (G::AQ + v) * NSL, q[v]);
+      st2(d + G::AUY * NSL, w.u[1]);
+      st2(d + (G::AUY + 1) * NSL, w.u[2]);
+      st2(d + G::APR * NSL, w.p);
+      st2(d + G::ACS * NSL, w.c);
     }
     __syncthreads();  // buffer s is converted: the copy two patches ahead may start
 
-    if (nx2.pos < a.i_end) {
-      if (tid == 0) issue_box(nx2, s);
-      pending |= 1u << s;
-    }
-
-    // ---- faces: flux differences G+ - G- of every cell, per direction -------
-    unsigned lmax = 0u;
-    if (warp == 0) {
-      if (lane < NROW) {
-        // x line: the row's cells x = 0 .. P+1 in registers (columns 1 .. P+2)
-        const int rb = PX * ((1 + lane % P) + NE * (1 + lane / P));
-        float c[9][PX];
+    // ---- y (warp 0) and z (warp 1) faces: half lines of x-neighbouring line
+    //      pairs; warps 2, 3: the next patch's halo cells ----------------------
+    if (warp < 2) {
+      const int k = 1 + warp;
+      const int h = lane >> 4, rem = lane & 15;
+      const bool act = rem < G::NHL;
+      const int t = rem / HP, j = rem - (rem / HP) * HP;
+      const int s0 = 2 * j + (k == 1 ? PZ * (1 + t) : RP * (1 + t));
+      const int st = k == 1 ? RP : PZ;                // SoA step along the line
+      const int r0 = k == 1 ? P * t : t;              // interior row of cell b = 1
+      const int rs = k == 1 ? 1 : P;                  // row step along the line
+      const unsigned hmask = 2 + 2 * j <= P ? kMagMask : 0u;  // second line real
+      const int vn = 1 + k, vt2 = k == 1 ? 3 : 2;     // normal / 2nd transverse momentum
+      auto load = [&](int b) {
+        const float* sp = soa + s0 + b * st;
+        const f2 e4 = ld2(sp + (G::AQ + 4) * NSL), pr = ld2(sp + G::APR * NSL);
+        return Cell2{ld2(sp + G::AQ * NSL), ld2(sp + (G::AQ + 1) * NSL),
+                     ld2(sp + (G::AQ + vn) * NSL), ld2(sp + (G::AQ + vt2) * NSL),
+                     e4, ld2(sp + (G::AUY + k - 1) * NSL),
+                     pr, ld2(sp + G::ACS * NSL), add2(e4, pr)};
+      };
+      auto store_dg = [&](int b, const f2 (&gpl)[5], const f2 (&gmi)[5]) {
+        float* d = dg + ((k - 1) * S * NROW + r0 + (b - 1) * rs) * DP + 2 * j;
+        st2(d, sub2(gpl[0], gmi[0]));
+        st2(d + 1 * NROW * DP, sub2(gpl[1], gmi[1]));
+        st2(d + vn * NROW * DP, sub2(gpl[2], gmi[2]));
+        st2(d + vt2 * NROW * DP, sub2(gpl[3], gmi[3]));
+        st2(d + 4 * NROW * DP, sub2(gpl[4], gmi[4]));
+      };
+      f2 gfirst[5], glast[5];
 #pragma unroll
-        for (int qi = 0; qi < 9; ++qi) {
-          const int arr = qi < 5 ? G::AQ + qi : (qi == 5 ? G::AU : G::APR + (qi - 6));
+      for (int v = 0; v < 5; ++v) glast[v] = gfirst[v] = 0ull;
+      if (act) {
+        // half 0: faces 0 .. HA-1 (cells 0 .. HA); half 1: faces HA .. P
+        const int b0 = h ? G::HA : 0;
+        Cell2 Lc = load(b0);
 #pragma unroll
-          for (int c4 = 0; c4 < PX / 4; ++c4) {
-            const float4 v4 = *reinterpret_cast<const float4*>(soa + arr * NSL + rb + 4 * c4);
-            c[qi][4 * c4] = v4.x;
-            c[qi][4 * c4 + 1] = v4.y;
-            c[qi][4 * c4 + 2] = v4.z;
-            c[qi][4 * c4 + 3] = v4.w;
-          }
-        }
-        float gp[5], dgp[5];  // previous face's G; flux difference of an even slot
-        float* const drow = dg + lane * DP;
-#pragma unroll
-        for (int f = 0; f <= P; ++f) {
-          const int L = f + 1, R = f + 2;  // columns of the face's two cells
-          const float uL = c[5][L], pL = c[6][L], cL = c[7][L], eL = c[8][L];
-          const float uR = c[5][R], pR = c[6][R], cR = c[7][R], eR = c[8][R];
-          const unsigned amb = umax(wave_bits(uL, cL), wave_bits(uR, cR));
-          lmax = umax(lmax, amb & kMagMask);
-          const float am = __uint_as_float(amb);
-          const float sL = add_rn(uL, am), sR = sub_rn(uR, am), ps = add_rn(pL, pR);
-          float g[5];
-          g[0] = fmaf(c[0][L], sL, mul_rn(c[0][R], sR));
-          g[1] = fmaf(c[1][L], sL, fmaf(c[1][R], sR, ps));
-          g[2] = fmaf(c[2][L], sL, mul_rn(c[2][R], sR));
-          g[3] = fmaf(c[3][L], sL, mul_rn(c[3][R], sR));
-          g[4] = fmaf(am, sub_rn(c[4][L], c[4][R]), fmaf(eL, uL, mul_rn(eR, uR)));
-          if (f > 0) {
-            // cell x = f (slot f - 1): slots are stored in pairs; the last
-            // cell's pair holds a zero for the column beyond the row
-            const int sl = f - 1;
-#pragma unroll
-            for (int v = 0; v < S; ++v) {
-              const float dv = sub_rn(g[v], gp[v]);
-              if (sl % 2 == 0) {
-                if (sl == P - 1)
-                  st2(drow + v * NROW * DP + sl, f2_pack(dv, 0.0f));
-                else
-                  dgp[v] = dv;
-              } else {
-                st2(drow + v * NROW * DP + sl - 1, f2_pack(dgp[v], dv));
-              }
-            }
-          }
-#pragma unroll
-          for (int v = 0; v < S; ++v) gp[v] = g[v];
-        }
-      }
-    } else if (warp == 1) {
-      if (lane < G::NYZ) {
-        // y or z line pair: cells b = 0 .. P+1 of two x-neighbouring lines
-        const int k = lane < P * HP ? 1 : 2;
-        const int rem = lane - (k - 1) * P * HP;
-        const int t = rem / HP, j = rem - t * HP;
-        const int s0 = 2 + 2 * j + (k == 1 ? PX * NE * (1 + t) : PX * (1 + t));
-        const int st = k == 1 ? PX : PX * NE;           // SoA step along the line
-        const int r0 = k == 1 ? P * t : t;              // interior row of cell b = 1
-        const int rs = k == 1 ? 1 : P;                  // row step along the line
-        const unsigned hmask = 2 + 2 * j <= P ? kMagMask : 0u;  // second line real
-        const int vn = 1 + k, vt2 = k == 1 ? 3 : 2;     // normal / 2nd transverse momentum
-        struct C2 {
-          f2 q0, qt1, qn, qt2, q4, u, p, c, e;
-        };
-        auto load = [&](int b) {
-          const float* sp = soa + s0 + b * st;
-          C2 x;
-          x.q0 = ld2(sp + G::AQ * NSL);
-          x.qt1 = ld2(sp + (G::AQ + 1) * NSL);
-          x.qn = ld2(sp + (G::AQ + vn) * NSL);
-          x.qt2 = ld2(sp + (G::AQ + vt2) * NSL);
-          x.q4 = ld2(sp + (G::AQ + 4) * NSL);
-          x.u = ld2(sp + (G::AU + k) * NSL);
-          x.p = ld2(sp + G::APR * NSL);
-          x.c = ld2(sp + G::ACS * NSL);
-          x.e = ld2(sp + G::AEP * NSL);
-          return x;
-        };
-        float* const dbase = dg + (k * S * NROW + r0) * DP + 2 * j;
-        C2 Lc = load(0);
-        f2 gp[5];
-#pragma unroll
-        for (int f = 0; f <= P; ++f) {
-          const C2 Rc = load(f + 1);
-          float uLl, uLh, cLl, cLh, uRl, uRh, cRl, cRh;
-          f2_unpack(Lc.u, uLl, uLh);
-          f2_unpack(Lc.c, cLl, cLh);
-          f2_unpack(Rc.u, uRl, uRh);
-          f2_unpack(Rc.c, cRl, cRh);
-          const unsigned bl = umax(wave_bits(uLl, cLl), wave_bits(uRl, cRl));
-          const unsigned bh = umax(wave_bits(uLh, cLh), wave_bits(uRh, cRh));
+        for (int f = 0; f < G::HA; ++f) {
+          const Cell2 Rc = load(b0 + f + 1);
+          f2 g[5];
+          unsigned bl, bh;
+          flux2(Lc, Rc, g, bl, bh);
           lmax = umax(lmax, bl & kMagMask);
           lmax = umax(lmax, bh & hmask);
-          const f2 am = f2_pack(__uint_as_float(bl), __uint_as_float(bh));
-          const f2 sL = add2(Lc.u, am), sR = sub2(Rc.u, am), ps = add2(Lc.p, Rc.p);
-          f2 g[5];  // unknowns 0, 1 (x momentum), normal, second transverse, 4
-          g[0] = fma2(Lc.q0, sL, mul2(Rc.q0, sR));
-          g[1] = fma2(Lc.qt1, sL, mul2(Rc.qt1, sR));
-          g[2] = fma2(Lc.qn, sL, fma2(Rc.qn, sR, ps));
-          g[3] = fma2(Lc.qt2, sL, mul2(Rc.qt2, sR));
-          g[4] = fma2(am, sub2(Lc.q4, Rc.q4), fma2(Lc.e, Lc.u, mul2(Rc.e, Rc.u)));
-          if (f > 0) {
-            // cell b = f of both lines: G(face f) - G(face f - 1)
-            float* d = dbase + (f - 1) * rs * DP;
-            st2(d, sub2(g[0], gp[0]));
-            st2(d + 1 * NROW * DP, sub2(g[1], gp[1]));
-            st2(d + vn * NROW * DP, sub2(g[2], gp[2]));
-            st2(d + vt2 * NROW * DP, sub2(g[3], gp[3]));
-            st2(d + 4 * NROW * DP, sub2(g[4], gp[4]));
+          if (f > 0)
+            store_dg(b0 + f, g, glast);
+          else {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) gfirst[v] = g[v];
           }
 #pragma unroll
-          for (int v = 0; v < S; ++v) gp[v] = g[v];
+          for (int v = 0; v < 5; ++v) glast[v] = g[v];
           Lc = Rc;
         }
       }
-    } else if (nx1.pos < a.i_end) {
-      // the next patch: its box (copied a patch ago), its halo cells
-      if (wait_box(s ^ 1) && STEP) gather(nx1, s ^ 1);
+      // cell HA: G(face HA) (half 1's first) - G(face HA-1) (half 0's last)
+      f2 gother[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        float lo, hi;
+        f2_unpack(glast[v], lo, hi);
+        gother[v] = f2_pack(__shfl_xor_sync(FULL, lo, 16), __shfl_xor_sync(FULL, hi, 16));
+      }
+      if (act && h == 1) store_dg(G::HA, gfirst, gother);
+    } else {
+      if (nx1.pos < a.i_end) {
+        if (wait_box(s ^ 1) && STEP) gather(nx1, s ^ 1);
+      }
+      if (tid == 96) {
+        // the patch two ahead: find it, start its copy into buffer s
+        const Pat nx2 = nx1.pos < a.i_end ? next_valid(nx1.pos + gridDim.x) : nx1;
+        *info = nx2;
+        if (nx2.pos < a.i_end) issue_box(nx2, s);
+      }
     }
-    if (want_lam && warp < 2) {
+    if (want_lam) {
       const unsigned long long m = warp_max_u64((unsigned long long)lmax);
       if (lane == 0) red[warp] = m;
     }
     __syncthreads();  // flux differences complete
 
-    if (want_lam && tid == 0)
-      a.lam_patch[cur.pid] = order_value<float>(red[0] > red[1] ? red[0] : red[1]);
+    const Pat nx2 = *info;
+    if (nx2.pos < a.i_end) pending |= 1u << s;
+    if (want_lam && tid == 0) {
+      unsigned long long mm = red[0];
+#pragma unroll
+      for (int w = 1; w < 4; ++w) mm = red[w] > mm ? red[w] : mm;
+      a.lam_patch[cur.pid] = order_value<float>(mm);
+    }
 
-    // ---- update: Q - (dt / 2dx) sum_k (G+ - G-), x pairs of cells ----------
-    if (tid < G::NC) {
-      const int r = tid / HP, j = tid - (tid / HP) * HP;
+    // ---- update: Q - (dt / 2dx) sum_k (G+ - G-), x pairs of cells, by the
+    //      threads whose conversion item was the pair (interior rows, j >= 1)
+    if (xrow && xj >= 1) {
+      const int r = xr, j = xj - 1;
       const int y = 1 + r % P, z = 1 + r / P;
       const bool hi = 2 + 2 * j <= P;  // the second cell is a cell of the patch
       const unsigned mhi = hi ? ~0u : 0u;
       f2 acc[5];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int v = 0; v < S; ++v) acc[v] = dgx[v];
 #pragma unroll
-        for (int v = 0; v < S; ++v) {
-          const f2 d2 = ld2(dg + ((k * S + v) * NROW + r) * DP + 2 * j);
-          acc[v] = k == 0 ? d2 : add2(acc[v], d2);
-        }
+      for (int k = 1; k < 3; ++k) {
+#pragma unroll
+        for (int v = 0; v < S; ++v)
+          acc[v] = add2(acc[v], ld2(dg + (((k - 1) * S + v) * NROW + r) * DP + 2 * j));
       }
-      const int slot = 2 + 2 * j + PX * (y + NE * z);
+      const int slot = 2 * j + RP * y + PZ * z;
       f2 qn[5];
 #pragma unroll
       for (int v = 0; v < S; ++v) qn[v] = fma2(mhr2, acc[v], ld2(soa + (G::AQ + v) * NSL + slot));

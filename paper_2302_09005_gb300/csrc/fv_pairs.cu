@@ -256,9 +256,18 @@ __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepPara
     }
     return r;
   };
+  // the bulk copy of a patch into buffer b: in a time step only the span from
+  // the first to the last interior cell (16-byte bounds; the face-halo cells
+  // come from the gather), else the whole box but its ragged tail (which lies
+  // in the last corner cell, never read)
   auto issue_box = [&](const Pat& pt, int b) {
-    issue_stage<float, 3, false>(a, pt.pid, P, pt.off,
-                                 Stage<float>{box0 + b * G::BOXP, nullptr, nullptr}, &bar[b]);
+    constexpr uint32_t lo = STEP ? ((1 + NE + NE * NE) * S * 4) & ~15u : 0u;
+    constexpr uint32_t hi =
+        STEP ? ((P + NE * P + NE * NE * P + 1) * S * 4 + 15) & ~15u : (G::BOX * 4) & ~15u;
+    static_assert(hi <= G::BOX * 4 + 12 && hi <= G::BOXP * 4, "copy inside the box");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(&bar[b], hi - lo);
+    bulk_copy_g2s(box0 + b * G::BOXP + lo / 4, a.in + pt.off + lo / 4, hi - lo, &bar[b]);
   };
   // warps 2, 3: the halo cells of faces 3 (w - 2) .. 3 (w - 2) + 2 of a patch
   // staged in buffer b, from sources resolved here (lanes 0-2)

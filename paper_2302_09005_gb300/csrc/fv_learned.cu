@@ -28,6 +28,7 @@
 #include "fv_mma.cuh"
 #include "fv_ptx.cuh"
 #include "fv_tc.cuh"
+#include "fv_x2.cuh"
 
 namespace fv {
 
@@ -129,31 +130,54 @@ __device__ __forceinline__ int phys_comp(int k, int vn) {
 // ---------------------------------------------------------------------------
 // Correction kernel: the network on the 5th-generation tensor cores
 // ---------------------------------------------------------------------------
-// A CTA of 128 threads takes tiles of 128 face slots (slot = patch * fmax +
+// A CTA of 256 threads takes tiles of 128 face slots (slot = patch * fmax +
 // face, fmax the faces of a patch of the handle's largest size; slots past a
-// smaller patch's faces are idle rows).  Thread t owns row t of the tile: it
-// gathers its face's stencil, normalises it into row t of A1 (BF16, shared
-// memory); one thread issues the MMAs (tcgen05, FP32 accumulators in tensor
-// memory, D row t = TMEM lane t), and thread t reads its row back, adds the
-// bias, applies GELU and writes row t of the next layer's A operand:
+// smaller patch's faces are idle rows), in two warp groups:
+//   producers (warps 4-7)  thread 128 + t gathers the stencil of row t of the
+//                          next tile, normalises it into row t of that tile's
+//                          A1 buffer (BF16, K-major, two buffers) and records
+//                          the row's face;
+//   consumers (warps 0-3)  thread 0 issues the MMAs (tcgen05, FP32
+//                          accumulators in tensor memory, D row t = TMEM lane
+//                          t, which warp t / 32 may read); thread t reads its
+//                          row back, adds the bias, applies GELU and writes
+//                          row t of the next layer's A operand:
 //   D1 = A1[128x16] W1^T (N = 64), D2 = A2[128x64] W2^T (N = 64),
 //   D3 = A3[128x64] W3^T (N = 16, rows 4..15 of W3 zero).
+// The stencil loads of one tile (through the neighbour table) overlap the
+// MMA / GELU chain of the previous one.  Named barriers hand the A1 buffers
+// over: FULL[b] (producers arrive, consumers wait) and EMPTY[b] (consumers
+// arrive once the MMA that read the buffer has completed, producers wait).
 // D1, D2 and D3 share 64 TMEM columns; A3 reuses A2's buffer (each MMA has
 // completed before its operands are overwritten).
 constexpr int kTcRows = 128;  // faces per tile: the MMA's M
 constexpr int kTcCols = 64;   // TMEM columns of a CTA
+constexpr int kCorrNT = 256;  // consumers + producers
 
 struct TcSmem {
-  alignas(128) unsigned char a1[kTcRows * 16 * 2];
+  alignas(128) unsigned char a1[2][kTcRows * 16 * 2];
   alignas(128) unsigned char a2[kTcRows * 64 * 2];
   alignas(128) unsigned char w1[64 * 16 * 2];
   alignas(128) unsigned char w2[64 * 64 * 2];
   alignas(128) unsigned char w3[16 * 64 * 2];
-  float b1[64], b2[64], b3[4];
+  alignas(16) float b1[64];
+  alignas(16) float b2[64];
+  float b3[4];
   float mu[16], rsd[16], sdy[4];
+  int64_t fpid[2][kTcRows];  // face of each row: patch, or -1 (idle row)
+  int fkj[2][kTcRows];       // j | nf1 << 10 | k << 20
   alignas(8) uint64_t bar;
   uint32_t tmem;
 };
+
+// Named barriers (0 is __syncthreads): FULL[b], EMPTY[b], the consumers'.
+constexpr int kBarFull = 1, kBarEmpty = 3, kBarCons = 5;
+__device__ __forceinline__ void nbar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
 // A stencil value as float.  FP64 states are narrowed by repacking the bits
 // with integer operations (sign, rebased exponent, leading 23 fraction bits;
@@ -182,6 +206,20 @@ __device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v)
   *reinterpret_cast<uint4*>(dst) = u;
 }
 
+// gelu_f (fv_mma.cuh) on two values with the packed FP32 instructions: the
+// same operations, each half rounded as the scalar one (the same bits), at
+// half the instruction issue; the tanh stays one special-function
+// instruction per value.
+__device__ __forceinline__ f2 gelu2(f2 z) {
+  const f2 c3 = f2_pack(0.0356774081f, 0.0356774081f), c1 = f2_pack(0.7978845608f, 0.7978845608f);
+  const f2 half = f2_pack(0.5f, 0.5f);
+  const f2 u = mul2(z, fma2(c3, mul2(z, z), c1));
+  const f2 h = mul2(half, z);
+  float ul, uh;
+  f2_unpack(u, ul, uh);
+  return fma2(h, f2_pack(tanh_hw(ul), tanh_hw(uh)), h);
+}
+
 // Row `row` of a 64-wide hidden layer: TMEM accumulators + bias -> GELU ->
 // BF16 into the K-major A tile of the next layer.
 __device__ __forceinline__ void hidden_row(uint32_t trow, const float* bias, unsigned char* a,
@@ -191,35 +229,39 @@ __device__ __forceinline__ void hidden_row(uint32_t trow, const float* bias, uns
     float v[16];
     tc_ld16(trow + c, v);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = gelu_f(v[i] + bias[c + i]);
+    for (int i = 0; i < 16; i += 2) {
+      const f2 g = gelu2(add2(f2_pack(v[i], v[i + 1]),
+                              *reinterpret_cast<const f2*>(bias + c + i)));
+      f2_unpack(g, v[i], v[i + 1]);
+    }
     store_bf16x8(a + tc_kmajor_offset(row, c, 64), v);
     store_bf16x8(a + tc_kmajor_offset(row, c + 8, 64), v + 8);
   }
 }
 
-// All threads: operands visible to the tensor cores, TMEM reads done; then
+// Consumers: operands visible to the tensor cores, TMEM reads done; then
 // thread 0 issues.
-__device__ __forceinline__ void tc_handoff() {
+__device__ __forceinline__ void tc_handoff_cons() {
   fence_proxy_async_smem();
   tc_fence_before_sync();
-  __syncthreads();
+  nbar_sync(kBarCons, kTcRows);
   tc_fence_after_sync();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTcRows, 4)
+__global__ void __launch_bounds__(kCorrNT, 4)
     corr_kernel(MeshView<T> m, int pmax, const float* params, const float* norm, float* corr,
                 int64_t stride) {
   __shared__ TcSmem s;
   const int tid = threadIdx.x, warp = tid >> 5;
   // weights (BF16, K-major tiles), biases, normalisation
-  for (int i = tid; i < 64 * 16; i += kTcRows)
+  for (int i = tid; i < 64 * 16; i += kCorrNT)
     *reinterpret_cast<uint16_t*>(s.w1 + tc_kmajor_offset(i >> 4, i & 15, 16)) =
         f32_to_bf16(params[kOffW1 + i]);
-  for (int i = tid; i < 64 * 64; i += kTcRows)
+  for (int i = tid; i < 64 * 64; i += kCorrNT)
     *reinterpret_cast<uint16_t*>(s.w2 + tc_kmajor_offset(i >> 6, i & 63, 64)) =
         f32_to_bf16(params[kOffW2 + i]);
-  for (int i = tid; i < 16 * 64; i += kTcRows)
+  for (int i = tid; i < 16 * 64; i += kCorrNT)
     *reinterpret_cast<uint16_t*>(s.w3 + tc_kmajor_offset(i >> 6, i & 63, 64)) =
         i < 4 * 64 ? f32_to_bf16(params[kOffW3 + i]) : (uint16_t)0;
   if (tid < 64) {
@@ -239,106 +281,131 @@ __global__ void __launch_bounds__(kTcRows, 4)
     fence_mbar_init();
   }
   if (warp == 0) tc_alloc(&s.tmem, kTcCols);
-  tc_handoff();
+  fence_proxy_async_smem();
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
   const uint32_t tm = s.tmem;
-  const uint32_t trow = tm + ((uint32_t)(warp * 32) << 16);  // this warp's TMEM lanes
   const int64_t fmax = 2ll * (pmax + 1) * pmax;
   const int64_t nslots = m.n * fmax;
   const int64_t ntiles = (nslots + kTcRows - 1) / kTcRows;
   constexpr uint32_t kId64 = tc_idesc_bf16(kTcRows, 64), kId16 = tc_idesc_bf16(kTcRows, 16);
-  uint32_t parity = 0;
   bool failed = false;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // ---- this thread's face: slot -> (patch, direction, face)
-    const int64_t slot = tile * kTcRows + tid;
-    const int64_t pid = slot / fmax;
-    const int lf = (int)(slot - pid * fmax);
-    bool act = slot < nslots;
-    int p = 1, nf1 = 2, k = 0, j = 0, b = 0, tr = 0;
-    if (act) {
-      p = m.sizes[pid];
-      if (p < 1 || p > pmax) {
-        if (lf == 0) atomicOr(m.status, ST_BAD_PATCH);
-        act = false;
-      } else {
-        nf1 = (p + 1) * p;
-        act = lf < 2 * nf1;
-      }
-    }
-    if (act) {
-      k = lf / nf1;
-      j = lf - k * nf1;
-      b = j / p;
-      tr = j - b * p;
-    }
-    // ---- normalised stencil Q_{b-1..b+2} in the face's normal frame -> A1 row
-    float x[16];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
+
+  if (warp >= 4) {
+    // ---- producers: stencils of the tiles, one tile ahead of the consumers
+    const int row = tid - kTcRows;
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      if (it >= 2) nbar_sync(kBarEmpty + b, kCorrNT);
+      const int64_t slot = tile * kTcRows + row;
+      const int64_t pid = slot / fmax;
+      const int lf = (int)(slot - pid * fmax);
+      bool act = slot < nslots;
+      int p = 1, nf1 = 2, k = 0, j = 0, bb = 0, tr = 0;
       if (act) {
-        const int along = b - 1 + c;
-        int neg;
-        const T* src = cell_source(m, pid, p, k == 0 ? along : tr + 1, k == 0 ? tr + 1 : along,
-                                   neg);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = (u == neg) ? -narrow(src[u]) : narrow(src[u]);
+        p = m.sizes[pid];
+        if (p < 1 || p > pmax) {
+          if (lf == 0) atomicOr(m.status, ST_BAD_PATCH);
+          act = false;
+        } else {
+          nf1 = (p + 1) * p;
+          act = lf < 2 * nf1;
+        }
       }
+      if (act) {
+        k = lf / nf1;
+        j = lf - k * nf1;
+        bb = j / p;
+        tr = j - bb * p;
+      }
+      // normalised stencil Q_{b-1..b+2} in the face's normal frame -> A1 row
+      float x[16];
 #pragma unroll
-      for (int vn = 0; vn < 4; ++vn) {
-        const int phi = 4 * c + vn;
-        x[phi] = act ? (v[phys_comp(k, vn)] - s.mu[phi]) * s.rsd[phi] : 0.f;
+      for (int c = 0; c < 4; ++c) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (act) {
+          const int along = bb - 1 + c;
+          int neg;
+          const T* src = cell_source(m, pid, p, k == 0 ? along : tr + 1,
+                                     k == 0 ? tr + 1 : along, neg);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = (u == neg) ? -narrow(src[u]) : narrow(src[u]);
+        }
+#pragma unroll
+        for (int vn = 0; vn < 4; ++vn) {
+          const int phi = 4 * c + vn;
+          x[phi] = act ? (v[phys_comp(k, vn)] - s.mu[phi]) * s.rsd[phi] : 0.f;
+        }
+      }
+      store_bf16x8(s.a1[b] + tc_kmajor_offset(row, 0, 16), x);
+      store_bf16x8(s.a1[b] + tc_kmajor_offset(row, 8, 16), x + 8);
+      s.fpid[b][row] = act ? pid : -1;
+      s.fkj[b][row] = j | (nf1 << 10) | (k << 20);
+      fence_proxy_async_smem();
+      nbar_arrive(kBarFull + b, kCorrNT);
+    }
+  } else {
+    // ---- consumers: the network on the tensor cores, one row per thread
+    const uint32_t trow = tm + ((uint32_t)(warp * 32) << 16);  // this warp's TMEM lanes
+    uint32_t parity = 0;
+    int it = 0;
+    auto mma_wait = [&]() {
+      failed |= !mbar_wait_bounded(&s.bar, parity, kTcWaitLimit);
+      parity ^= 1u;
+      tc_fence_after_sync();
+    };
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      tc_fence_before_sync();
+      nbar_sync(kBarFull + b, kCorrNT);  // A1[b] written (and the last tile's D3 read)
+      tc_fence_after_sync();
+      const bool run = !failed;  // a wait that gave up stops the tensor work
+      // ---- layer 1: 16 -> 64
+      if (tid == 0 && run) {
+        tc_mma_bf16(tm, tc_smem_desc(s.a1[b], 128, 256), tc_smem_desc(s.w1, 128, 256), kId64, 0);
+        tc_commit(&s.bar);
+      }
+      if (run) mma_wait();
+      // A1[b] has been read: the producers may refill it (if they will)
+      if (tile + 2 * gridDim.x < ntiles) nbar_arrive(kBarEmpty + b, kCorrNT);
+      if (run) hidden_row(trow, s.b1, s.a2, tid);
+      tc_handoff_cons();
+      // ---- layer 2: 64 -> 64
+      if (tid == 0 && run && !failed) {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, 1024),
+                      tc_smem_desc(s.w2 + kk * 256, 128, 1024), kId64, kk > 0);
+        tc_commit(&s.bar);
+      }
+      if (run) mma_wait();
+      if (run) hidden_row(trow, s.b2, s.a2, tid);
+      tc_handoff_cons();
+      // ---- layer 3: 64 -> 4 (N = 16)
+      if (tid == 0 && run && !failed) {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, 1024),
+                      tc_smem_desc(s.w3 + kk * 256, 128, 1024), kId16, kk > 0);
+        tc_commit(&s.bar);
+      }
+      if (run) mma_wait();
+      float y[4] = {0.f, 0.f, 0.f, 0.f};
+      if (run) tc_ld4(trow, y);
+      const int64_t pid = s.fpid[b][tid];
+      if (run && pid >= 0) {
+        const int fkj = s.fkj[b][tid];
+        const int j = fkj & 1023, nf1 = (fkj >> 10) & 1023, k = fkj >> 20;
+#pragma unroll
+        for (int vn = 0; vn < 4; ++vn)
+          corr[pid * stride + (k * 4 + phys_comp(k, vn)) * nf1 + j] = (y[vn] + s.b3[vn]) * s.sdy[vn];
       }
     }
-    store_bf16x8(s.a1 + tc_kmajor_offset(tid, 0, 16), x);
-    store_bf16x8(s.a1 + tc_kmajor_offset(tid, 8, 16), x + 8);
-    tc_handoff();
-    // ---- layer 1: 16 -> 64
-    if (tid == 0) {
-      tc_mma_bf16(tm, tc_smem_desc(s.a1, 128, 256), tc_smem_desc(s.w1, 128, 256), kId64, 0);
-      tc_commit(&s.bar);
-    }
-    failed |= !mbar_wait_bounded(&s.bar, parity, kTcWaitLimit);
-    parity ^= 1u;
-    tc_fence_after_sync();
-    hidden_row(trow, s.b1, s.a2, tid);
-    tc_handoff();
-    // ---- layer 2: 64 -> 64
-    if (tid == 0) {
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, 1024),
-                    tc_smem_desc(s.w2 + kk * 256, 128, 1024), kId64, kk > 0);
-      tc_commit(&s.bar);
-    }
-    failed |= !mbar_wait_bounded(&s.bar, parity, kTcWaitLimit);
-    parity ^= 1u;
-    tc_fence_after_sync();
-    hidden_row(trow, s.b2, s.a2, tid);
-    tc_handoff();
-    // ---- layer 3: 64 -> 4 (N = 16)
-    if (tid == 0) {
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, 1024),
-                    tc_smem_desc(s.w3 + kk * 256, 128, 1024), kId16, kk > 0);
-      tc_commit(&s.bar);
-    }
-    failed |= !mbar_wait_bounded(&s.bar, parity, kTcWaitLimit);
-    parity ^= 1u;
-    tc_fence_after_sync();
-    float y[4];
-    tc_ld4(trow, y);
-    if (act) {
-#pragma unroll
-      for (int vn = 0; vn < 4; ++vn)
-        corr[pid * stride + (k * 4 + phys_comp(k, vn)) * nf1 + j] = (y[vn] + s.b3[vn]) * s.sdy[vn];
-    }
-    tc_fence_before_sync();
-    if (__syncthreads_or(failed)) break;
   }
   // a wait that gave up: report; the TMEM is released either way
-  if (failed && tid == 0) atomicOr(m.status, ST_TIMEOUT);
+  if (failed) atomicOr(m.status, ST_TIMEOUT);
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
@@ -555,18 +622,18 @@ fv_status fv_flux_correction(fv_batch* h, const void* q, const int64_t* off, con
   if (!q || !off || !sizes || !nbr || !params || !norm || !corr)
     return lerr(h, FV_ERR_INVALID_ARG, "null pointer");
   const int64_t stride = fv::corr_stride_for(h->max_patch_size);
-  // tiles of 128 face slots; up to six CTAs per SM (shared memory bound; 6 x 64
-  // TMEM columns of 512)
+  // tiles of 128 face slots; up to four CTAs of 256 threads per SM (registers
+  // and shared memory; 4 x 64 TMEM columns of 512)
   const int64_t ntiles = (n * (stride / 4) + fv::kTcRows - 1) / fv::kTcRows;
-  const int64_t gmax = (int64_t)h->num_sms * 6;
+  const int64_t gmax = (int64_t)h->num_sms * 4;
   const int grid = (int)(ntiles < gmax ? ntiles : gmax);
   if (h->prec == FV_FP64) {
     fv::MeshView<double> m{static_cast<const double*>(q), off, sizes, nbr, n, h->d_status};
-    fv::corr_kernel<double><<<grid, fv::kTcRows, 0, h->stream>>>(m, h->max_patch_size, params,
+    fv::corr_kernel<double><<<grid, fv::kCorrNT, 0, h->stream>>>(m, h->max_patch_size, params,
                                                                  norm, corr, stride);
   } else {
     fv::MeshView<float> m{static_cast<const float*>(q), off, sizes, nbr, n, h->d_status};
-    fv::corr_kernel<float><<<grid, fv::kTcRows, 0, h->stream>>>(m, h->max_patch_size, params,
+    fv::corr_kernel<float><<<grid, fv::kCorrNT, 0, h->stream>>>(m, h->max_patch_size, params,
                                                                 norm, corr, stride);
   }
   cudaError_t e = cudaGetLastError();

@@ -178,9 +178,9 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
  * the paper's offload pattern (the engine ships a batch of patches with
  * their halos to the GPU for every update and takes the results back).  The
  * batch is cut into chunks of chunk_patches consecutive patches (<= 0: about
- * 64 MB per chunk); the copy in of a chunk, the update of the previous one
+ * 128 MB per chunk); the copy in of a chunk, the update of the previous one
  * and the copy out of the one before overlap (two copy streams, the
- * handle's stream for the update, two device staging slots the handle keeps
+ * handle's stream for the update, three device staging slots the handle keeps
  * until fv_batch_destroy).
  *   host_in, host_out  host buffers (pinned for overlap; pageable works,
  *                      slower), the layout of fv_patch_update_batch; the

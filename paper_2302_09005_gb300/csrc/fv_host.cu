@@ -5,8 +5,9 @@
 // copied host -> device on one copy stream, updated on the handle's stream
 // and copied device -> host on a second copy stream, so the copies of
 // neighbouring chunks overlap each other and the update of the chunk between
-// them.  Two device staging slots (input and output buffers, metadata) are
-// reused alternately; events order the reuse.
+// them.  Three device staging slots (chunk buffer, metadata) are
+// reused in turn, so the upload of a chunk need not wait for the download of
+// the chunk before it (full-duplex link); events order the reuse.
 #include <stdio.h>
 #include <string.h>
 
@@ -15,19 +16,20 @@
 
 #include "fv_internal.h"
 
+constexpr int kHostSlots = 3;
+
 struct fv_host_stage {
   cudaStream_t h2d = nullptr, d2h = nullptr;
-  cudaEvent_t ev_h2d[2] = {nullptr, nullptr};   // slot's input (and metadata) on the device
-  cudaEvent_t ev_comp[2] = {nullptr, nullptr};  // slot's update done
-  cudaEvent_t ev_free[2] = {nullptr, nullptr};  // slot's output back on the host
-  bool used[2] = {false, false};
-  void* d_in[2] = {nullptr, nullptr};
-  void* d_out[2] = {nullptr, nullptr};
+  cudaEvent_t ev_h2d[kHostSlots] = {};   // slot's input (and metadata) on the device
+  cudaEvent_t ev_comp[kHostSlots] = {};  // slot's update done
+  cudaEvent_t ev_free[kHostSlots] = {};  // slot's output back on the host
+  bool used[kHostSlots] = {};
+  void* d_in[kHostSlots] = {};  // chunk input, updated in place
   size_t bytes = 0;  // capacity of each buffer
-  int64_t* d_off[2] = {nullptr, nullptr};
-  int32_t* d_sz[2] = {nullptr, nullptr};
-  int64_t* h_off[2] = {nullptr, nullptr};  // pinned: rebased offsets of the chunk
-  int32_t* h_sz[2] = {nullptr, nullptr};
+  int64_t* d_off[kHostSlots] = {};
+  int32_t* d_sz[kHostSlots] = {};
+  int64_t* h_off[kHostSlots] = {};  // pinned: rebased offsets of the chunk
+  int32_t* h_sz[kHostSlots] = {};
   int64_t meta_cap = 0;
 };
 
@@ -38,9 +40,8 @@ void host_stage_free(fv_batch* h) {
   if (!st) return;
   if (st->h2d) cudaStreamSynchronize(st->h2d);
   if (st->d2h) cudaStreamSynchronize(st->d2h);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < kHostSlots; ++k) {
     cudaFree(st->d_in[k]);
-    cudaFree(st->d_out[k]);
     cudaFree(st->d_off[k]);
     cudaFree(st->d_sz[k]);
     cudaFreeHost(st->h_off[k]);
@@ -75,7 +76,7 @@ cudaError_t stage_reserve(fv_batch* h, size_t bytes, int64_t npatch) {
     h->host_stage = st;
     e = cudaStreamCreateWithFlags(&st->h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st->d2h, cudaStreamNonBlocking);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int k = 0; k < kHostSlots && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&st->ev_h2d[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->ev_comp[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->ev_free[k], cudaEventDisableTiming);
@@ -83,22 +84,20 @@ cudaError_t stage_reserve(fv_batch* h, size_t bytes, int64_t npatch) {
     if (e != cudaSuccess) return e;
   }
   if (bytes > st->bytes) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kHostSlots; ++k) {
       if (st->used[k]) cudaEventSynchronize(st->ev_free[k]);
       cudaFree(st->d_in[k]);
-      cudaFree(st->d_out[k]);
-      st->d_in[k] = st->d_out[k] = nullptr;
+      st->d_in[k] = nullptr;
     }
     st->bytes = 0;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int k = 0; k < kHostSlots && e == cudaSuccess; ++k) {
       e = cudaMalloc(&st->d_in[k], bytes);
-      if (e == cudaSuccess) e = cudaMalloc(&st->d_out[k], bytes);
     }
     if (e != cudaSuccess) return e;
     st->bytes = bytes;
   }
   if (npatch > st->meta_cap) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kHostSlots; ++k) {
       if (st->used[k]) cudaEventSynchronize(st->ev_free[k]);
       cudaFree(st->d_off[k]);
       cudaFree(st->d_sz[k]);
@@ -110,7 +109,7 @@ cudaError_t stage_reserve(fv_batch* h, size_t bytes, int64_t npatch) {
       st->h_sz[k] = nullptr;
     }
     st->meta_cap = 0;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int k = 0; k < kHostSlots && e == cudaSuccess; ++k) {
       e = cudaMalloc(&st->d_off[k], sizeof(int64_t) * (size_t)npatch);
       if (e == cudaSuccess) e = cudaMalloc(&st->d_sz[k], sizeof(int32_t) * (size_t)npatch);
       if (e == cudaSuccess) e = cudaMallocHost(&st->h_off[k], sizeof(int64_t) * (size_t)npatch);
@@ -154,9 +153,9 @@ fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
       return herr(h, FV_ERR_INVALID_ARG, "patch offsets must ascend without overlap");
   }
   int64_t chunk = chunk_patches;
-  if (chunk <= 0) {  // about 64 MB per chunk
+  if (chunk <= 0) {  // about 128 MB per chunk
     const int64_t per = len(0) * (int64_t)es;
-    chunk = (64ll << 20) / (per > 0 ? per : 1);
+    chunk = (128ll << 20) / (per > 0 ? per : 1);
     if (chunk < 1) chunk = 1;
   }
   if (chunk > n) chunk = n;
@@ -176,7 +175,7 @@ fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
   e = cudaEventRecord(st->ev_comp[0], h->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st->h2d, st->ev_comp[0], 0);
   for (int64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
-    const int k = (int)(c & 1);
+    const int k = (int)(c % kHostSlots);
     const int64_t p0 = c * chunk, p1 = p0 + chunk < n ? p0 + chunk : n;
     const int64_t nc = p1 - p0;
     const int64_t base = off[p0];
@@ -200,14 +199,15 @@ fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
       e = cudaMemcpyAsync(st->d_sz[k], st->h_sz[k], sizeof(int32_t) * nc, cudaMemcpyHostToDevice,
                           st->h2d);
     if (e == cudaSuccess) e = cudaEventRecord(st->ev_h2d[k], st->h2d);
-    // update: the halo cells travel with the chunk; interior cells replaced
+    // update in place: in update mode a CTA reads only its own patch box (the
+    // bulk copy into shared memory, before any write) and writes only that
+    // patch's interior cells, so the chunk buffer can be its own output; the
+    // halo cells travel back unchanged
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, st->ev_h2d[k], 0);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(st->d_out[k], st->d_in[k], bytes, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess) {
       fv::UpdateLaunch l;
       l.in = st->d_in[k];
-      l.out = st->d_out[k];
+      l.out = st->d_in[k];
       l.off = st->d_off[k];
       l.sizes = st->d_sz[k];
       l.n = nc;
@@ -225,7 +225,7 @@ fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
     // device -> host
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st->d2h, st->ev_comp[k], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(static_cast<char*>(host_out) + base * es, st->d_out[k], bytes,
+      e = cudaMemcpyAsync(static_cast<char*>(host_out) + base * es, st->d_in[k], bytes,
                           cudaMemcpyDeviceToHost, st->d2h);
     if (e == cudaSuccess) e = cudaEventRecord(st->ev_free[k], st->d2h);
     st->used[k] = true;

@@ -12,6 +12,15 @@
 #include "fv_device.cuh"
 #include "fv_internal.h"
 
+namespace fv {
+
+std::mutex& smem_attr_mutex() {
+  static std::mutex m;
+  return m;
+}
+
+}  // namespace fv
+
 namespace {
 
 // Instantiated CUDA graphs of fv_run_steps, keyed by every argument that is

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fv.h"
 
 // Threads per CTA of the patch kernels.
@@ -104,6 +106,11 @@ inline int64_t prim_stride_elems(int d, fv_precision prec, int pmax) {
   const int64_t vec = prec == FV_FP64 ? 2 : 4;
   return (c + vec - 1) / vec * vec;
 }
+
+// Serialises the check-and-raise of the kernels' dynamic shared-memory limits
+// (cudaFuncSetAttribute), which handles on several host threads may request
+// at once: without it one thread could lower a limit another just raised.
+std::mutex& smem_attr_mutex();
 
 // Shared memory bytes of the update kernel for patches up to pmax.
 size_t update_smem_bytes(int d, fv_precision prec, int pmax, int nstage);

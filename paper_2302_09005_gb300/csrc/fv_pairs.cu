@@ -586,6 +586,7 @@ __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepPara
 template <int P, bool STEP>
 cudaError_t pairs_smem_attr() {
   static int set_bytes[64] = {0};
+  std::lock_guard<std::mutex> lock(smem_attr_mutex());
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

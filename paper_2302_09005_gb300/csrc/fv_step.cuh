@@ -880,6 +880,7 @@ inline size_t step_smem_bytes(int es, int pmax, int nstage) {
 template <typename T, int D, bool GATHER, bool FUSED, bool PRIMIN, int NT>
 static cudaError_t ensure_smem(size_t smem) {
   static int set_bytes[64] = {0};
+  std::lock_guard<std::mutex> lock(smem_attr_mutex());
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

@@ -166,6 +166,62 @@ def test_two_handles_two_streams(fv):
     b2.close()
 
 
+def test_concurrent_offload_from_host_threads(fv):
+    """Four host threads, each with its own handle and stream, offload at the
+    same time: the host pipeline and device time steps, FP64 and FP32, 2D and
+    3D, patch sizes whose kernels raise their shared-memory limits
+    concurrently.  Every result equals the same calls made alone, bitwise."""
+    import threading
+    torch = fvtest.torch_cuda()
+    cases = [(3, 5, 0, 300, 11), (3, 7, 1, 200, 12), (2, 17, 0, 400, 13), (3, 3, 1, 500, 14)]
+
+    def run(case):
+        d, p, prec, n, seed = case
+        q, off, sz = fvtest.random_batch(n, p, d, seed, np.float32 if prec else np.float64)
+        nbr = inputs.self_periodic_neighbours(n, d)
+        stream = torch.cuda.Stream()
+        b = fv.Batch(d, precision=prec, max_patch_size=p, stream=stream)
+        hin = torch.from_numpy(q).pin_memory()
+        hout = torch.from_numpy(q.copy()).pin_memory()  # the padding between boxes is not written
+        for _ in range(3):
+            fv.fv_patch_update_host(b.h, hin, hout, off, sz, n, 0.01, 1e-4, 64)
+        with torch.cuda.stream(stream):
+            x = hin.to("cuda", non_blocking=True)
+            y = x.clone()
+            toff = torch.from_numpy(off).to("cuda", non_blocking=True)
+            tsz = torch.from_numpy(sz).to("cuda", non_blocking=True)
+            tnbr = torch.from_numpy(nbr).to("cuda", non_blocking=True)
+            b.halo_fill(x, toff, tsz, tnbr)
+            b.max_eigenvalue(x, toff, tsz, 0.4, 0.01)
+            for _ in range(3):
+                b.time_step(x, y, toff, tsz, tnbr, 0.01, 0.4)
+                x, y = y, x
+        stream.synchronize()
+        st = b.status()
+        b.close()
+        return st, hout.numpy().copy(), x.cpu().numpy()
+
+    alone = [run(c) for c in cases]
+    results, errors = [None] * len(cases), []
+
+    def worker(i):
+        try:
+            results[i] = run(cases[i])
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for a_, r in zip(alone, results):
+        assert a_[0] == fv.FV_OK and r[0] == fv.FV_OK
+        assert np.array_equal(a_[1], r[1])
+        assert np.array_equal(a_[2], r[2])
+
+
 def test_fp64_reciprocal_and_sqrt_within_two_ulp(fv):
     """The FP64 kernels' Newton-refined reciprocal and square root stay
     within 2 ulp of the IEEE results over the range of physical states."""

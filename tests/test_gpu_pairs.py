@@ -174,3 +174,31 @@ def test_nonphysical_state_is_reported(fv):
     assert fv.fv_batch_pairs_launches(b.h) == 1
     assert b.status() == fv.FV_ERR_NONPHYSICAL
     b.close()
+
+
+def test_graph_of_steps_on_a_fresh_handle(fv):
+    """fv_run_steps captured into a CUDA graph on a fresh, planned handle (the
+    kernel's first launch happens inside the capture) equals the general
+    kernel's eager steps bitwise."""
+    torch = fvtest.torch_cuda()
+    grid = (6, 5, 4)
+    n = int(np.prod(grid))
+    q, off, sz = fvtest.random_batch(n, P, 3, 77, np.float32)
+    nbr = inputs.grid_neighbours(grid)
+    toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
+    dx, cfl, steps = 1.0 / (grid[0] * P), 0.4, 4
+    b0 = batch(fv, False, tsz, n)
+    ref = time_steps(fv, b0, q, toff, tsz, tnbr, dx, cfl, steps).cpu().numpy()
+    b0.close()
+    stream = torch.cuda.Stream()
+    b = fv.Batch(3, precision=fv.FV_FP32, max_patch_size=P, stream=stream)
+    fv.fv_batch_plan(b.h, tsz, n)
+    q0, q1 = fvtest.to_dev(q), fvtest.to_dev(q)
+    torch.cuda.synchronize()
+    b.run_steps(q0, q1, toff, tsz, tnbr, dx, cfl, steps, use_graph=True)
+    assert b.status() == fv.FV_OK
+    assert fv.fv_batch_pairs_launches(b.h) >= steps
+    mask = fvtest.interior_mask(off, sz, 3, 5, len(q))
+    got = (q0 if steps % 2 == 0 else q1).cpu().numpy()
+    assert np.array_equal(got[mask], ref[mask])
+    b.close()

@@ -295,13 +295,19 @@ __global__ void __launch_bounds__(kCorrNT, 4)
   if (warp >= 4) {
     // ---- producers: stencils of the tiles, one tile ahead of the consumers
     const int row = tid - kTcRows;
+    // this thread's slot = tile * 128 + row and (pid, lf) = divmod(slot,
+    // fmax), advanced by the CTA stride every tile instead of divided anew
+    const int64_t sstep = (int64_t)gridDim.x * kTcRows;
+    const int64_t qstep = sstep / fmax;
+    const int rstep = (int)(sstep - qstep * fmax);
+    int64_t slot = (int64_t)blockIdx.x * kTcRows + row;
+    int64_t pid = slot / fmax;
+    int lf = (int)(slot - pid * fmax);
+    int pcur = 0, rp = 0;  // the patch size rp is for: ceil(2^16 / p), j / p = (j rp) >> 16
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
       if (it >= 2) nbar_sync(kBarEmpty + b, kCorrNT);
-      const int64_t slot = tile * kTcRows + row;
-      const int64_t pid = slot / fmax;
-      const int lf = (int)(slot - pid * fmax);
       bool act = slot < nslots;
       int p = 1, nf1 = 2, k = 0, j = 0, bb = 0, tr = 0;
       if (act) {
@@ -315,17 +321,36 @@ __global__ void __launch_bounds__(kCorrNT, 4)
         }
       }
       if (act) {
-        k = lf / nf1;
+        k = lf >= nf1 ? 1 : 0;
         j = lf - k * nf1;
-        bb = j / p;
+        if (p != pcur) {
+          pcur = p;
+          rp = (65536 + p - 1) / p;  // exact for j < 2^16 / 16 and p <= 16
+        }
+        bb = (j * rp) >> 16;
         tr = j - bb * p;
       }
-      // normalised stencil Q_{b-1..b+2} in the face's normal frame -> A1 row
+      // normalised stencil Q_{b-1..b+2} in the face's normal frame -> A1 row;
+      // faces whose four cells lie inside the patch read them straight from
+      // its block, the others through the neighbour table
       float x[16];
+      const bool inner = act && bb >= 2 && bb + 2 <= p;
+      const T* cin = nullptr;
+      int sal = 0;  // elements between neighbouring cells along the normal
+      if (inner) {
+        const int ne = p + 2;
+        cin = m.q + m.off[pid] +
+              (k == 0 ? ((tr + 1) * ne + (bb - 1)) * 4 : ((bb - 1) * ne + (tr + 1)) * 4);
+        sal = k == 0 ? 4 : ne * 4;
+      }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (act) {
+        if (inner) {
+          const T* src = cin + c * sal;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = narrow(src[u]);
+        } else if (act) {
           const int along = bb - 1 + c;
           int neg;
           const T* src = cell_source(m, pid, p, k == 0 ? along : tr + 1,
@@ -345,6 +370,13 @@ __global__ void __launch_bounds__(kCorrNT, 4)
       s.fkj[b][row] = j | (nf1 << 10) | (k << 20);
       fence_proxy_async_smem();
       nbar_arrive(kBarFull + b, kCorrNT);
+      slot += sstep;
+      pid += qstep;
+      lf += rstep;
+      if (lf >= fmax) {
+        lf -= (int)fmax;
+        ++pid;
+      }
     }
   } else {
     // ---- consumers: the network on the tensor cores, one row per thread

@@ -349,7 +349,9 @@ fv_status fv_batch_set_schedule(fv_batch* h, fv_schedule schedule);
  * Patch-to-thread mapping of the FV_SCHED_CLASSES launches: one CTA advances
  * one patch at a time with `threads` threads (32: a warp per patch, 64, 128
  * or 256: a CTA per patch), set per patch size p (1..max_patch_size).  The
- * default is 128; d = 1 supports 128 only (FV_ERR_UNSUPPORTED otherwise).
+ * default (also of launches without a plan) follows the patch size: 32
+ * threads for up to 64 interior cells, 256 for 3D patches above 200 cells,
+ * else 128; d = 1 supports 128 only (FV_ERR_UNSUPPORTED otherwise).
  * The mapping never changes the results (bitwise).  fv_batch_class_threads
  * reads the current choice.
  */

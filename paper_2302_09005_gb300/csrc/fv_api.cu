@@ -158,8 +158,10 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
   h->d_lam = reinterpret_cast<unsigned long long*>(w + 128);
   h->d_partials = reinterpret_cast<unsigned long long*>(w + 256);
   h->d_sum_partials = reinterpret_cast<double*>(w + 256 + 8ull * FV_MAX_RED_BLOCKS);
+  // CTAs per SM of the untuned launches (their CTA size follows the patch size)
   for (int mode = fv::kModeUpdate; mode <= fv::kModePrim && e == cudaSuccess; ++mode)
-    e = fv::step_occupancy(h, mode, h->max_patch_size, h->nstage, 128, &h->blocks_per_sm[mode]);
+    e = fv::step_occupancy(h, mode, h->max_patch_size, h->nstage,
+                           fv::default_nt(d, h->max_patch_size), &h->blocks_per_sm[mode]);
   if (e != cudaSuccess) {
     cudaFree(h->ws);
     delete h;

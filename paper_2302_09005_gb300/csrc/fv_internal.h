@@ -120,6 +120,19 @@ cudaError_t step_occupancy(const fv_batch* h, int mode, int pmax, int nstage, in
 // Threads per CTA of the step kernel for one launch: 32, 64, 128 or 256.
 inline bool valid_nt(int nt) { return nt == 32 || nt == 64 || nt == 128 || nt == 256; }
 inline int nt_index(int nt) { return nt == 32 ? 0 : nt == 64 ? 1 : nt == 128 ? 2 : 3; }
+// CTA size of launches nobody tuned, by the interior cells p^d of the
+// patches: a warp for up to 64 cells (the small 2D patches and 3^3), eight
+// warps for 3D patches above 200 cells, else four (measured on GB300: 2D
+// 5x5 patches run 1.75x faster on one warp than on four; the size-class
+// autotuner chose the same for 3^3, 5^3 and 7^3).  d = 1 runs 128 threads.
+inline int default_nt(int d, int p) {
+  if (d == 1) return 128;
+  int n = 1;
+  for (int k = 0; k < d; ++k) n *= p;
+  if (n <= 64) return 32;
+  if (d == 3 && n > 200) return 256;
+  return 128;
+}
 // Per-precision, per-CTA-size launch and occupancy (fv_update.cu: double and
 // 128 threads; fv_update_f32.cu: float and 128; fv_update_nt.cu and
 // fv_update_nt_f32.cu: 32, 64 and 256 threads).

@@ -97,7 +97,7 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
       }
       lc.nstage = stages_for(h, lc.pmax);
       const int pi = lc.pmax < 64 ? lc.pmax : 63;
-      lc.nt = h->cls_nt[pi] > 0 ? h->cls_nt[pi] : 128;
+      lc.nt = h->cls_nt[pi] > 0 ? h->cls_nt[pi] : default_nt(h->d, lc.pmax);
       int& bps = h->occ_cache[f][pi][nt_index(lc.nt)];
       if (bps == 0) {
         cudaError_t e = step_occupancy(h, f, lc.pmax, lc.nstage, lc.nt, &bps);
@@ -116,9 +116,10 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
     cudaError_t e = launch_one_size(h, lu, l.n, &done);
     if (e != cudaSuccess || done) return e;
   }
+  l.nt = default_nt(h->d, h->max_patch_size);
   int& bps = h->blocks_per_sm[f];
   if (bps == 0) {
-    cudaError_t e = step_occupancy(h, f, h->max_patch_size, h->nstage, 128, &bps);
+    cudaError_t e = step_occupancy(h, f, h->max_patch_size, h->nstage, l.nt, &bps);
     if (e != cudaSuccess) return e;
   }
   if (h->sched == FV_SCHED_LPT && plan_ok) {
@@ -218,7 +219,7 @@ fv_status fv_batch_set_class_threads(fv_batch* h, int p, int threads) {
   if (!h) return FV_ERR_INVALID_ARG;
   if (p < 1 || p > h->max_patch_size || p >= 64)
     return sched_err(h, FV_ERR_INVALID_ARG, "patch size outside 1..max_patch_size");
-  if (threads == 0) threads = 128;
+  if (threads == 0) threads = fv::default_nt(h->d, p);
   if (!fv::valid_nt(threads)) return sched_err(h, FV_ERR_INVALID_ARG, "threads: 32, 64, 128, 256");
   if (h->d == 1 && threads != 128) return sched_err(h, FV_ERR_UNSUPPORTED, "d = 1: 128 threads");
   h->cls_nt[p] = threads;
@@ -227,7 +228,7 @@ fv_status fv_batch_set_class_threads(fv_batch* h, int p, int threads) {
 
 fv_status fv_batch_class_threads(const fv_batch* h, int p, int* threads) {
   if (!h || !threads || p < 1 || p >= 64) return FV_ERR_INVALID_ARG;
-  *threads = h->cls_nt[p] > 0 ? h->cls_nt[p] : 128;
+  *threads = h->cls_nt[p] > 0 ? h->cls_nt[p] : fv::default_nt(h->d, p);
   return FV_OK;
 }
 

@@ -200,3 +200,14 @@ def test_class_threads_arguments_are_checked(fv):
         fv.fv_batch_set_class_threads(b1.h, 4, 32)
     assert e.value.status == fv.FV_ERR_UNSUPPORTED
     b1.close()
+
+
+def test_default_cta_size_follows_the_patch_size(fv):
+    """Untuned launches and classes: a warp for up to 64 interior cells, eight
+    warps for 3D patches above 200 cells, else four; d = 1 stays at 128."""
+    for d, pmax, expect in ((2, 8, {5: 32, 8: 32}), (2, 17, {9: 128, 17: 128}),
+                            (3, 7, {3: 32, 4: 32, 5: 128, 6: 256, 7: 256}), (1, 8, {8: 128})):
+        b = fv.Batch(d, max_patch_size=pmax)
+        for p, nt in expect.items():
+            assert fv.fv_batch_class_threads(b.h, p) == nt, (d, p)
+        b.close()

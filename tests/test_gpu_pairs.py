@@ -202,3 +202,26 @@ def test_graph_of_steps_on_a_fresh_handle(fv):
     got = (q0 if steps % 2 == 0 else q1).cpu().numpy()
     assert np.array_equal(got[mask], ref[mask])
     b.close()
+
+
+def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv):
+    """A patch whose box runs past the declared buffer length (n_elems): both
+    kernels report FV_ERR_BAD_PATCH, leave it untouched and update the rest
+    identically."""
+    torch = fvtest.torch_cuda()
+    n = 40
+    q, off, sz = fvtest.random_batch(n, P, 3, 78, np.float32)
+    toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
+    n_elems = int(off[-1]) + 10  # the last patch does not fit
+    res = []
+    for planned in (False, True):
+        b = batch(fv, planned, tsz, n)
+        x = fvtest.to_dev(q)
+        y = x.clone()
+        b.update(x, y, toff, tsz, 0.01, 0.001, n_elems=n_elems)
+        res.append((b.status(), y.cpu().numpy(), fv.fv_batch_pairs_launches(b.h)))
+        b.close()
+    assert res[0][0] == fv.FV_ERR_BAD_PATCH and res[1][0] == fv.FV_ERR_BAD_PATCH
+    assert res[0][2] == 0 and res[1][2] == 1
+    assert np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[1][1][off[-1]:], q[off[-1]:])  # the last patch untouched

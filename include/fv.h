@@ -333,8 +333,9 @@ fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* patch_off
 typedef enum { FV_SCHED_STRIDE = 0, FV_SCHED_LPT = 1, FV_SCHED_CLASSES = 2 } fv_schedule;
 
 /*
- * fv_batch_plan -- sorts the patches of a batch by size on the device
- * (counting sort; patch_sizes: device int32[n_patches]) for the LPT and
+ * fv_batch_plan -- sorts the patches of a batch by size (a stable counting
+ * sort: within a size the patches keep their index order; patch_sizes:
+ * device int32[n_patches], read back to the host once) for the LPT and
  * CLASSES schedules, and keeps the plan in the handle.  Synchronises the
  * handle's stream (call it outside stream capture).  A later update or time
  * step uses the plan when it is given the same patch_sizes pointer and

@@ -9,36 +9,17 @@
 //                     fill the tail);
 //   FV_SCHED_CLASSES  one launch per patch size, each with the shared memory,
 //                     pipeline depth and occupancy of its own size.
-// fv_batch_plan sorts the patches on the device (counting sort by size);
+// fv_batch_plan sorts the patches by size (a stable counting sort);
 // fv_batch_autotune times the three on the caller's batch and keeps the
 // fastest.
 #include <stdio.h>
+
+#include <vector>
 
 #include "fv_device.cuh"
 #include "fv_internal.h"
 
 namespace fv {
-
-// bucket of a patch size: 1..pmax, or pmax+1 for sizes the kernels reject
-__device__ __forceinline__ int size_bucket(int p, int pmax) {
-  return (p >= 1 && p <= pmax) ? p : pmax + 1;
-}
-
-__global__ void plan_hist_kernel(const int32_t* __restrict__ sizes, int64_t n, int pmax,
-                                 unsigned long long* counts) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&counts[size_bucket(sizes[i], pmax)], 1ull);
-}
-
-__global__ void plan_scatter_kernel(const int32_t* __restrict__ sizes, int64_t n, int pmax,
-                                    unsigned long long* cursor, int32_t* order) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long pos = atomicAdd(&cursor[size_bucket(sizes[i], pmax)], 1ull);
-    order[pos] = (int32_t)i;
-  }
-}
 
 void plan_free(fv_batch* h) {
   if (h->d_order) cudaFree(h->d_order);
@@ -146,6 +127,8 @@ fv_status fv_batch_plan(fv_batch* h, const int32_t* sizes, int64_t n) {
   h->last_error[0] = 0;
   if (n < 0 || (n > 0 && !sizes)) return sched_err(h, FV_ERR_INVALID_ARG, "bad sizes / n");
   if (n > 0x7FFFFFFFll) return sched_err(h, FV_ERR_UNSUPPORTED, "more than 2^31-1 patches");
+  const int pmax = h->max_patch_size;
+  if (pmax + 2 > 80) return sched_err(h, FV_ERR_UNSUPPORTED, "max_patch_size too large to plan");
   cudaError_t e = cudaSuccess;
   if (n > h->plan_cap) {
     if (h->d_order) cudaFree(h->d_order);
@@ -155,52 +138,46 @@ fv_status fv_batch_plan(fv_batch* h, const int32_t* sizes, int64_t n) {
     if (e != cudaSuccess) return sched_err(h, FV_ERR_CUDA, "plan: out of device memory");
     h->plan_cap = n;
   }
-  const int pmax = h->max_patch_size;
-  const int nb = pmax + 2;  // buckets 0..pmax+1 (0 unused)
-  unsigned long long* counts = h->d_partials;  // workspace slots, stream ordered
-  unsigned long long host[80] = {0};
-  if (nb > 80) return sched_err(h, FV_ERR_UNSUPPORTED, "max_patch_size too large to plan");
-  e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * nb, h->stream);
-  const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
-  if (e == cudaSuccess && n > 0) {
-    fv::plan_hist_kernel<<<grid, 256, 0, h->stream>>>(sizes, n, pmax, counts);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(host, counts, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost,
+  // the sizes to the host, a stable counting sort there (patches of a class
+  // keep their index order, so a class launch walks its patches in memory
+  // order, with the neighbours' halo cells close in L2), the order back
+  std::vector<int32_t> hs((size_t)n), order((size_t)n);
+  if (n > 0)
+    e = cudaMemcpyAsync(hs.data(), sizes, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost,
                         h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
+  // bucket of a patch size: 1..pmax, or pmax+1 for sizes the kernels reject
+  auto bucket = [&](int32_t p) { return (p >= 1 && p <= pmax) ? p : pmax + 1; };
+  int64_t count[80] = {0}, start[80] = {0};
+  for (int64_t i = 0; i < n; ++i) ++count[bucket(hs[(size_t)i])];
   // positions: largest size first, rejected sizes last
-  unsigned long long start[80] = {0};
-  unsigned long long pos = 0;
+  int64_t pos = 0;
   h->ncls = 0;
   for (int p = pmax; p >= 1; --p) {
     start[p] = pos;
-    if (host[p] > 0) {
+    if (count[p] > 0) {
       h->cls_p[h->ncls] = p;
       h->cls_real[h->ncls] = 1;
-      h->cls_begin[h->ncls] = (int64_t)pos;
-      h->cls_end[h->ncls] = (int64_t)(pos + host[p]);
+      h->cls_begin[h->ncls] = pos;
+      h->cls_end[h->ncls] = pos + count[p];
       ++h->ncls;
     }
-    pos += host[p];
+    pos += count[p];
   }
   start[pmax + 1] = pos;
-  if (host[pmax + 1] > 0) {  // rejected sizes: the kernels flag and skip them
+  if (count[pmax + 1] > 0) {  // rejected sizes: the kernels flag and skip them
     h->cls_p[h->ncls] = pmax;
     h->cls_real[h->ncls] = 0;
-    h->cls_begin[h->ncls] = (int64_t)pos;
-    h->cls_end[h->ncls] = (int64_t)(pos + host[pmax + 1]);
+    h->cls_begin[h->ncls] = pos;
+    h->cls_end[h->ncls] = pos + count[pmax + 1];
     ++h->ncls;
   }
-  e = cudaMemcpyAsync(counts, start, sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice,
-                      h->stream);
-  if (e == cudaSuccess && n > 0) {
-    fv::plan_scatter_kernel<<<grid, 256, 0, h->stream>>>(sizes, n, pmax, counts, h->d_order);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // `start` lives on this stack
+  for (int64_t i = 0; i < n; ++i) order[(size_t)start[bucket(hs[(size_t)i])]++] = (int32_t)i;
+  if (n > 0)
+    e = cudaMemcpyAsync(h->d_order, order.data(), sizeof(int32_t) * (size_t)n,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // `order` lives on this stack
   if (e != cudaSuccess) return sched_err(h, FV_ERR_CUDA, cudaGetErrorString(e));
   h->plan_n = n;
   h->plan_sizes = sizes;

@@ -75,7 +75,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str |
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static" if False else "-cudart=static"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart=static"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, lib)
     return lib

@@ -57,7 +57,13 @@ struct PairGeom {
   static constexpr int HP = (P + 1) / 2;            // x pairs of interior cells per row
   static constexpr int DP = 2 * HP;                 // flux-difference slots per row
   static constexpr int NROW = P * P;                // interior x rows
-  static constexpr int NDG = 2 * S * NROW * DP;     // y, z flux differences [k-1][v][row][slot]
+  // y and z flux differences of the interior cells, [v][z][y][slot] per
+  // direction.  The z planes of the y block lie B1 floats apart, B1 = DP
+  // (mod 32) with B1 >= P DP: the lanes storing the P lines of a y half-line
+  // step then hit distinct banks (the z block's lines are DP apart already).
+  static constexpr int B1 = P * DP + (DP - (P * DP) % 32 + 32) % 32;
+  static constexpr int DGV1 = P * B1, DG2 = S * DGV1, DGV2 = NROW * DP;
+  static constexpr int NDG = DG2 + S * DGV2;
   static constexpr int BOX = NE * NE * NE * S;      // cells of the staged box
   static constexpr int BOXP = (BOX + 3) / 4 * 4;
   // conversion items: x pairs of the interior rows (with their x halos),
@@ -207,7 +213,7 @@ template <int P, bool STEP>
 __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepParams<float> a) {
   using G = PairGeom<P>;
   constexpr int S = G::S, NE = G::NE, RP = G::RP, PZ = G::PZ, NSL = G::NSL, HP = G::HP,
-                DP = G::DP, NROW = G::NROW;
+                DP = G::DP;
   constexpr unsigned FULL = 0xFFFFFFFFu;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // one per box buffer
@@ -416,8 +422,6 @@ __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepPara
       const int t = rem / HP, j = rem - (rem / HP) * HP;
       const int s0 = 2 * j + (k == 1 ? PZ * (1 + t) : RP * (1 + t));
       const int st = k == 1 ? RP : PZ;                // SoA step along the line
-      const int r0 = k == 1 ? P * t : t;              // interior row of cell b = 1
-      const int rs = k == 1 ? 1 : P;                  // row step along the line
       const unsigned hmask = 2 + 2 * j <= P ? kMagMask : 0u;  // second line real
       const int vn = 1 + k, vt2 = k == 1 ? 3 : 2;     // normal / 2nd transverse momentum
       auto load = [&](int b) {
@@ -428,13 +432,17 @@ __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepPara
                      e4, ld2(sp + (G::AUY + k - 1) * NSL),
                      pr, ld2(sp + G::ACS * NSL), add2(e4, pr)};
       };
+      // cell b of the line: k = 1: y = b, z = 1 + t; k = 2: y = 1 + t, z = b
+      const int dgb = k == 1 ? t * G::B1 + 2 * j : G::DG2 + t * DP + 2 * j;
+      const int dgs = k == 1 ? DP : P * DP;        // dG step along the line
+      const int dgv = k == 1 ? G::DGV1 : G::DGV2;  // dG step per unknown
       auto store_dg = [&](int b, const f2 (&gpl)[5], const f2 (&gmi)[5]) {
-        float* d = dg + ((k - 1) * S * NROW + r0 + (b - 1) * rs) * DP + 2 * j;
+        float* d = dg + dgb + (b - 1) * dgs;
         st2(d, sub2(gpl[0], gmi[0]));
-        st2(d + 1 * NROW * DP, sub2(gpl[1], gmi[1]));
-        st2(d + vn * NROW * DP, sub2(gpl[2], gmi[2]));
-        st2(d + vt2 * NROW * DP, sub2(gpl[3], gmi[3]));
-        st2(d + 4 * NROW * DP, sub2(gpl[4], gmi[4]));
+        st2(d + 1 * dgv, sub2(gpl[1], gmi[1]));
+        st2(d + vn * dgv, sub2(gpl[2], gmi[2]));
+        st2(d + vt2 * dgv, sub2(gpl[3], gmi[3]));
+        st2(d + 4 * dgv, sub2(gpl[4], gmi[4]));
       };
       f2 gfirst[5], glast[5];
 #pragma unroll
@@ -508,11 +516,11 @@ __global__ void __launch_bounds__(128, FV_PAIRS_MINBLOCKS) pairs_kernel(StepPara
 #pragma unroll
       for (int v = 0; v < S; ++v) acc[v] = dgx[v];
 #pragma unroll
-      for (int k = 1; k < 3; ++k) {
+      for (int v = 0; v < S; ++v)
+        acc[v] = add2(acc[v], ld2(dg + v * G::DGV1 + (y - 1) * DP + (z - 1) * G::B1 + 2 * j));
 #pragma unroll
-        for (int v = 0; v < S; ++v)
-          acc[v] = add2(acc[v], ld2(dg + (((k - 1) * S + v) * NROW + r) * DP + 2 * j));
-      }
+      for (int v = 0; v < S; ++v)
+        acc[v] = add2(acc[v], ld2(dg + G::DG2 + v * G::DGV2 + (y - 1) * DP + (z - 1) * P * DP + 2 * j));
       const int slot = 2 * j + RP * y + PZ * z;
       f2 qn[5];
 #pragma unroll

@@ -419,13 +419,16 @@ __host__ __device__ constexpr bool kPencilFaces() {
 // keeps at least as many lanes busy (to 2 %).
 template <int D, int P, int NT>
 __host__ __device__ constexpr bool kWarpSlots() {
-  if (P <= 0 || D == 1) return false;
-  const int nface = (P + 1) * (D == 2 ? P : P * P);
-  const int slot_lanes = D * ((nface + 31) / 32) * 32;
-  const int total = D * nface;
-  const int flat_full = total / NT, flat_rest = total - flat_full * NT;
-  const int flat_lanes = flat_full * NT + (flat_rest + 31) / 32 * 32;
-  return 100 * total / slot_lanes + 2 >= 100 * total / flat_lanes;
+  if constexpr (P <= 0 || D == 1) {
+    return false;
+  } else {
+    const int nface = (P + 1) * (D == 2 ? P : P * P);
+    const int slot_lanes = D * ((nface + 31) / 32) * 32;
+    const int total = D * nface;
+    const int flat_full = total / NT, flat_rest = total - flat_full * NT;
+    const int flat_lanes = flat_full * NT + (flat_rest + 31) / 32 * 32;
+    return 100 * total / slot_lanes + 2 >= 100 * total / flat_lanes;
+  }
 }
 
 template <typename T, int D, int P, bool GATHER, bool FUSED, bool PRIMIN, int NT>

@@ -107,6 +107,7 @@ def test_run_steps_graph_equals_eager(fv, prec, n_steps):
         torch.cuda.synchronize()
         b.run_steps(q0, q1, toff, tsz, tnbr, dx, cfl, n_steps, use_graph)
         if use_graph:  # replay the cached graph from the same start
+            stream.synchronize()  # the first run is done with q0 before it is reset
             q0.copy_(fvtest.to_dev(q))
             torch.cuda.synchronize()
             b.run_steps(q0, q1, toff, tsz, tnbr, dx, cfl, n_steps, use_graph)

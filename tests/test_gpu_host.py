@@ -1,7 +1,9 @@
 """The batched update on patches in host memory (fv_patch_update_host): the
 chunked copy-in / update / copy-out pipeline gives bitwise the device
 update's result for any chunk size, mixed patch sizes and both precisions;
-halo cells come back as they went in; bad layouts are refused."""
+halo cells come back as they went in; in place (host_in == host_out, where
+equally spaced patches of one size copy back only their interior spans) the
+whole buffer ends as out of place; bad layouts are refused."""
 import numpy as np
 import pytest
 
@@ -48,6 +50,50 @@ def test_host_pipeline_equals_device_update_bitwise(fv, prec, chunk):
     # a second call reuses the staging
     fv.fv_patch_update_host(b.h, hin, hout, off, sz, n, dx, dt, chunk)
     assert np.array_equal(hout.numpy()[mask], ref[mask])
+    b.close()
+
+
+def spaced_batch(q, off, sz, d, gap_every):
+    """The boxes of a batch moved apart by 8 extra elements after every
+    gap_every-th patch (equal sizes, unequal spacing)."""
+    box = (int(sz[0]) + 2) ** d * (d + 2)
+    off2 = off + 8 * (np.arange(len(off)) // gap_every)
+    q2 = np.zeros(int(off2[-1]) + box + 8, dtype=q.dtype)
+    for o, o2 in zip(off, off2):
+        q2[int(o2):int(o2) + box] = q[int(o):int(o) + box]
+    return q2, off2
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case,chunk", [("uniform3d", 0), ("uniform3d", 7), ("uniform2d", 0),
+                                        ("uneven", 5), ("spaced", 4), ("one", 0)])
+def test_in_place_equals_out_of_place_bitwise(fv, prec, case, chunk):
+    torch = fvtest.torch_cuda()
+    dtype = np.float32 if prec else np.float64
+    d, p = (2, 8) if case == "uniform2d" else (3, 5)
+    n = 1 if case == "one" else 157
+    if case == "uneven":
+        sizes = inputs.uneven_sizes(n, seed=83, mix=((3, 0.5), (5, 0.5)))
+        q, off, sz = inputs.random_batch(n, sizes, d, seed=83, dtype=dtype)
+    else:
+        q, off, sz = fvtest.random_batch(n, p, d, 83, dtype)
+        if case == "spaced":
+            q, off = spaced_batch(q, off, sz, d, 3)
+    dx, dt = 0.01, 0.001
+    b = fv.Batch(d, precision=prec, max_patch_size=p)
+    hin = torch.from_numpy(q).pin_memory()
+    hout = torch.from_numpy(q.copy()).pin_memory()  # halos and gaps as the input's
+    fv.fv_patch_update_host(b.h, hin, hout, off, sz, n, dx, dt, chunk)
+    hbuf = torch.from_numpy(q.copy()).pin_memory()
+    fv.fv_patch_update_host(b.h, hbuf, hbuf, off, sz, n, dx, dt, chunk)
+    assert b.status() == fv.FV_OK
+    assert np.array_equal(hbuf.numpy(), hout.numpy())
+    x = fvtest.to_dev(q)
+    y = x.clone()
+    b.update(x, y, fvtest.to_dev(off), fvtest.to_dev(sz), dx, dt)
+    mask = fvtest.interior_mask(off, sz, d, d + 2, len(q))
+    assert np.array_equal(hbuf.numpy()[mask], y.cpu().numpy()[mask])
+    assert not np.array_equal(hbuf.numpy()[mask], q[mask])
     b.close()
 
 

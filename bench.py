@@ -684,6 +684,8 @@ def precision_variant(args, N: int = 4095, p: int = 5, steps: int = 100):
         stream = torch.cuda.Stream()
         b = fv.Batch(2, precision=fv.FV_FP64 if prec == "f64" else fv.FV_FP32,
                      max_patch_size=p, stream=stream)
+        if prec == "f32":  # one patch size: the FP32 kernel built for it
+            fv.fv_batch_plan(b.h, tsz, n)
         q = q64 if prec == "f64" else q64.astype(np.float32)
         x0 = torch.from_numpy(q).cuda()
         x, y = x0.clone(), x0.clone()
@@ -716,6 +718,24 @@ def precision_variant(args, N: int = 4095, p: int = 5, steps: int = 100):
                      "conserved_totals_start": a0.tolist(),
                      "conserved_drift_rel_to_l1": (np.abs(a1 - a0) / l1_scale.cpu().numpy()
                                                    ).tolist()}
+        if prec == "f32":
+            out[prec]["pairs_kernel_used"] = fv.fv_batch_pairs_launches(b.h) > 0
+            # the same steps on the general kernel (no plan)
+            bg = fv.Batch(2, precision=fv.FV_FP32, max_patch_size=p, stream=stream)
+            x.copy_(x0)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                bg.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps, use_graph=True)
+            stream.synchronize()
+            x.copy_(x0)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                bg.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps, use_graph=True)
+                e1.record(stream)
+            stream.synchronize()
+            out[prec]["general_kernel_ms_per_step"] = e0.elapsed_time(e1) / steps
+            bg.close()
         b.close()
         del x0, x, y
     d64, d32 = finals["f64"], finals["f32"]

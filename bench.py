@@ -54,6 +54,9 @@ WORKLOADS = {
     # small cases of the same kernels (profiling captures, quick checks)
     "euler3d_fp64_32768x5": (3, 5, 32768, (32, 32, 32), "f64"),
     "euler3d_fp32_32768x5": (3, 5, 32768, (32, 32, 32), "f32"),
+    # the precision workload's size (4095^2 cells in 5 x 5 patches), random
+    # states: the one-warp FP32 kernel for 2D (profiling captures)
+    "euler2d_fp32_670761x5": (2, 5, 670761, (819, 819), "f32"),
 }
 
 
@@ -414,8 +417,9 @@ def run_ours(args, ws, rank, local):
            "unit": "GB/s", "frac": alg_bytes / (kern_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
            "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src}
     if roof is None:
-        kname = ("pairs_kernel<5,step>" if fv.fv_batch_pairs_launches(b.h) > 0
-                 else "step_kernel<float,3,gather,fused>")
+        kname = ((f"pairs{'2d' if d == 2 else ''}_kernel<5,step>"
+                  if fv.fv_batch_pairs_launches(b.h) > 0 else
+                  f"step_kernel<float,{d},gather,fused>"))
         roof = {"bound": "hbm", "kernel": kname, **hbm,
                 "traffic": _traffic(args.workload)}
     b.close()

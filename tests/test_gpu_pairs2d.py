@@ -47,7 +47,7 @@ def time_steps(fv, b, q, toff, tsz, tnbr, dx, cfl, steps, lam=None):
 @pytest.mark.parametrize("sched", [0, 1, 2])
 @pytest.mark.parametrize("grid,periodic,bnd", [
     ((12, 10), True, -1), ((3, 3), False, -1), ((4, 7), False, -2), ((1, 1), True, -1),
-    ((80, 60), True, -1)])
+    ((80, 60), True, -1), ((200, 100), False, -2)])
 def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd):
     torch = fvtest.torch_cuda()
     n = int(np.prod(grid))
@@ -100,10 +100,10 @@ def test_primitives_of_the_new_state_bitwise(fv):
     assert np.array_equal(res[0][1], res[1][1])
 
 
-@pytest.mark.parametrize("device_dt", [False, True])
-def test_update_mode_bitwise_equal_general_kernel(fv, device_dt):
+@pytest.mark.parametrize("device_dt,n", [(False, 9000), (True, 9000), (False, 40000)])
+def test_update_mode_bitwise_equal_general_kernel(fv, device_dt, n):
     torch = fvtest.torch_cuda()
-    n = 9000  # more patches than resident warps: several per CTA
+    # more patches than resident warps: several per CTA (40,000: about 11)
     q, off, sz = fvtest.random_batch(n, P, D, 93, np.float32)
     toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
     dx = 0.01
@@ -222,3 +222,36 @@ def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv):
     assert res[0][2] == 0 and res[1][2] == 1
     assert np.array_equal(res[0][1], res[1][1])
     assert np.array_equal(res[1][1][off[-1]:], q[off[-1]:])
+
+
+@pytest.mark.parametrize("step", [False, True])
+def test_invalid_patches_inside_the_sequence(fv, step):
+    """Patches with a misaligned offset scattered through a long sequence (many
+    patches per CTA): both kernels report FV_ERR_BAD_PATCH, skip them (and,
+    in a time step, treat them as absent neighbours the same way) and agree
+    bitwise on everything else."""
+    torch = fvtest.torch_cuda()
+    grid = (200, 100)
+    n = int(np.prod(grid))
+    q, off, sz = fvtest.random_batch(n, P, D, 99, np.float32)
+    bad = np.arange(17, n, 1511)
+    off = off.copy()
+    off[bad] += 1  # not a multiple of 16 bytes
+    nbr = inputs.grid_neighbours(grid)
+    toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
+    dx = 1.0 / (grid[0] * P)
+    res = []
+    for planned in (False, True):
+        b = batch(fv, planned, tsz, n, 2)
+        x = fvtest.to_dev(q)
+        y = x.clone()
+        if step:
+            b.max_eigenvalue(x, toff, tsz, 0.4, dx)
+            b.time_step(x, y, toff, tsz, tnbr, dx, 0.4)
+        else:
+            b.update(x, y, toff, tsz, dx, 0.001)
+        res.append((b.status(), y.cpu().numpy(), fv.fv_batch_pairs_launches(b.h)))
+        b.close()
+    assert res[0][0] == fv.FV_ERR_BAD_PATCH and res[1][0] == fv.FV_ERR_BAD_PATCH
+    assert res[0][2] == 0 and res[1][2] == 1
+    assert np.array_equal(res[0][1], res[1][1])

@@ -506,6 +506,21 @@ fv_status fv_conserved_totals(fv_batch* h, const void* q_with_halo, const int64_
                               const int32_t* patch_sizes, int64_t n_patches, double* totals);
 
 /*
+ * fv_patch_sums -- the per-patch stage of fv_conserved_totals written out:
+ * the FP64 sum of every unknown over each patch's interior cells (the
+ * conservation epilogue of Algorithm 1's update, per patch), in the same
+ * fixed order, so the totals are the fixed-order sum of these.
+ *   per_patch  device double[n_patches][s], 8-byte aligned
+ *              (FV_ERR_ALIGNMENT); row i holds patch i's sums; rows of
+ *              invalid patches (bad size or offset: the status word's
+ *              bad-patch bit) are left as they are.
+ *   totals     device double[s] or NULL: as fv_conserved_totals.
+ */
+fv_status fv_patch_sums(fv_batch* h, const void* q_with_halo, const int64_t* patch_offsets,
+                        const int32_t* patch_sizes, int64_t n_patches, double* per_patch,
+                        double* totals);
+
+/*
  * fv_conserved_totals_noalloc -- the sums of fv_conserved_totals for callers
  * that cannot allocate device memory (no counterpart in the paper).  Some
  * callers own the whole GPU through their own memory pool and forbid any

@@ -332,11 +332,8 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q, const int64_t* of
   return FV_OK;
 }
 
-fv_status fv_conserved_totals(fv_batch* h, const void* q, const int64_t* off,
-                              const int32_t* sizes, int64_t n, double* totals) {
-  if (!h) return FV_ERR_INVALID_ARG;
-  h->last_error[0] = 0;
-  if (!totals) return set_err(h, FV_ERR_INVALID_ARG, "null totals");
+static fv_status sums_impl(fv_batch* h, const void* q, const int64_t* off, const int32_t* sizes,
+                           int64_t n, double* totals, double* per_patch) {
   fv_status st = check_meta(h, q, off, sizes, n);
   if (st != FV_OK) return st;
   const int64_t nchunks = (n + FV_SUM_CHUNK - 1) / FV_SUM_CHUNK;
@@ -352,12 +349,33 @@ fv_status fv_conserved_totals(fv_batch* h, const void* q, const int64_t* off,
     l.halo = h->halo;
     l.partials = h->d_sum_partials;
     l.status = h->d_status;
+    l.per_patch = per_patch;
     e = fv::launch_sums(h, l, (int)nchunks);
     if (e != cudaSuccess) return cuda_err(h, e, "sums kernel");
   }
-  e = fv::launch_sums_finish(h, h->d_sum_partials, (int)nchunks, totals);
-  if (e != cudaSuccess) return cuda_err(h, e, "sums finish kernel");
+  if (totals) {
+    e = fv::launch_sums_finish(h, h->d_sum_partials, (int)nchunks, totals);
+    if (e != cudaSuccess) return cuda_err(h, e, "sums finish kernel");
+  }
   return FV_OK;
+}
+
+fv_status fv_conserved_totals(fv_batch* h, const void* q, const int64_t* off,
+                              const int32_t* sizes, int64_t n, double* totals) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  h->last_error[0] = 0;
+  if (!totals) return set_err(h, FV_ERR_INVALID_ARG, "null totals");
+  return sums_impl(h, q, off, sizes, n, totals, nullptr);
+}
+
+fv_status fv_patch_sums(fv_batch* h, const void* q, const int64_t* off, const int32_t* sizes,
+                        int64_t n, double* per_patch, double* totals) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  h->last_error[0] = 0;
+  if (!per_patch) return set_err(h, FV_ERR_INVALID_ARG, "null per_patch");
+  if (reinterpret_cast<uintptr_t>(per_patch) % 8 != 0)
+    return set_err(h, FV_ERR_ALIGNMENT, "per_patch not 8-byte aligned");
+  return sums_impl(h, q, off, sizes, n, totals, per_patch);
 }
 
 static fv_status time_step_impl(fv_batch* h, const void* in, void* out, const int64_t* off,

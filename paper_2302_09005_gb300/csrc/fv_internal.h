@@ -194,6 +194,7 @@ struct SumLaunch {
   int halo;
   double* partials;  // [nchunks][s]
   unsigned int* status;
+  double* per_patch = nullptr;  // [n][s] or null: each valid patch's sums
 };
 // Patches per chunk of the fixed-order conservation sum.
 #define FV_SUM_CHUNK 1024

@@ -197,6 +197,7 @@ struct SumParams {
   int pmax;
   double* partials;
   unsigned int* status;
+  double* per_patch;
 };
 
 template <int S>
@@ -255,6 +256,10 @@ __global__ void __launch_bounds__(FV_NT) sums_kernel(SumParams<T> a) {
       for (int k = 0; k < S; ++k) acc[k] = acc[k] + (double)__ldg(qc + k);
     }
     block_sum_fixed<S>(acc, sh);
+    if (a.per_patch != nullptr && threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < S; ++k) a.per_patch[i * S + k] = acc[k];
+    }
 #pragma unroll
     for (int k = 0; k < S; ++k) chunk[k] = chunk[k] + acc[k];
   }
@@ -293,6 +298,7 @@ static cudaError_t launch_sums_t(const fv_batch* h, const SumLaunch& l, int nchu
   a.pmax = h->max_patch_size;
   a.partials = l.partials;
   a.status = l.status;
+  a.per_patch = l.per_patch;
   sums_kernel<T, D><<<nchunks, FV_NT, 0, h->stream>>>(a);
   return cudaGetLastError();
 }

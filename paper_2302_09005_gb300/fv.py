@@ -83,6 +83,7 @@ def _lib() -> ctypes.CDLL:
         L.fv_amr_plan_destroy.restype = c_int
         L.fv_max_eigenvalue_reduce.argtypes = [vp, vp, vp, vp, i64, vp, vp, dbl, dbl, vp]
         L.fv_conserved_totals.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.fv_patch_sums.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         L.fv_get_dt_ptr.argtypes = [vp, ctypes.POINTER(vp)]
         L.fv_get_status.argtypes = [vp]
         L.fv_selftest_math.argtypes = [vp, vp, i64, c_int]
@@ -311,6 +312,13 @@ def fv_conserved_totals(h, q_with_halo, patch_offsets, patch_sizes, n_patches: i
     st = _lib().fv_conserved_totals(h, _ptr(q_with_halo), _ptr(patch_offsets),
                                     _ptr(patch_sizes), n_patches, _ptr(totals))
     _check(h, st, "fv_conserved_totals")
+
+
+def fv_patch_sums(h, q_with_halo, patch_offsets, patch_sizes, n_patches: int, per_patch,
+                  totals=None):
+    st = _lib().fv_patch_sums(h, _ptr(q_with_halo), _ptr(patch_offsets), _ptr(patch_sizes),
+                              n_patches, _ptr(per_patch), _ptr(totals))
+    _check(h, st, "fv_patch_sums")
 
 
 def fv_conserved_totals_noalloc(d: int, s: int, precision: int, q_with_halo, patch_offsets,

@@ -194,6 +194,47 @@ def test_conserved_totals_deterministic(fv, prec):
     b.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_patch_sums_match_oracle_and_make_up_the_totals(fv, prec):
+    """fv_patch_sums: every valid patch's FP64 sums within 1e-14 of the
+    oracle's (relative to the sum of magnitudes), the totals it writes
+    bitwise those of fv_conserved_totals, the row of an invalid patch left
+    alone and reported."""
+    torch = fvtest.torch_cuda()
+    d, p, n = 2, 8, 2100  # three sum chunks, the last ragged
+    s = d + 2
+    q, off, sz = fvtest.random_batch(n, p, d, 19, np.float32 if prec else np.float64)
+    tq = fvtest.to_dev(q)
+    toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
+    b = fv.Batch(d, precision=prec, max_patch_size=p)
+    per = torch.full((n, s), float("nan"), dtype=torch.float64, device="cuda")
+    t1 = torch.zeros(s, dtype=torch.float64, device="cuda")
+    t2 = torch.zeros(s, dtype=torch.float64, device="cuda")
+    fv.fv_patch_sums(b.h, tq, toff, tsz, n, per, t1)
+    b.totals(tq, toff, tsz, t2)
+    assert b.status() == fv.FV_OK
+    assert torch.equal(t1, t2)
+    q64 = q.astype(np.float64)
+    ps = oracle.patch_sums(q64, off, sz, d, s)
+    pa = oracle.patch_sums(np.abs(q64), off, sz, d, s)
+    got = per.cpu().numpy()
+    assert np.all(np.abs(got - ps) <= 2e-14 * pa)  # both sums of <= 64 terms
+    for v in range(s):
+        assert abs(t1[v].item() - math.fsum(got[:, v])) <= 1e-14 * math.fsum(pa[:, v])
+    # an invalid patch: reported, its row untouched; totals may be omitted
+    bad = sz.copy()
+    bad[7] = 0
+    per2 = torch.full((n, s), float("nan"), dtype=torch.float64, device="cuda")
+    fv.fv_patch_sums(b.h, tq, toff, fvtest.to_dev(bad), n, per2)
+    assert b.status() == fv.FV_ERR_BAD_PATCH
+    got2 = per2.cpu().numpy()
+    assert np.all(np.isnan(got2[7])) and np.array_equal(np.delete(got2, 7, 0), np.delete(got, 7, 0))
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_patch_sums(b.h, tq, toff, tsz, n, None)
+    assert e.value.status == fv.FV_ERR_INVALID_ARG
+    b.close()
+
+
 def test_multistep_periodic_matches_oracle_and_conserves(fv):
     """Ten steps of halo fill -> CFL reduce -> update with the device dt on a
     periodic 2D patch mesh: parity with the oracle's own steps, and the

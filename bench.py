@@ -19,8 +19,10 @@ needed between steps.
 
 Arms:
   default            the CUDA library (value: device-resident timing; e2e: the
-                     same step with the state copied host->device before and
-                     device->host after it, from/to pinned host memory)
+                     update through fv_patch_update_host on the pinned host
+                     batch, advanced in place: chunked host->device copies of
+                     the boxes, the update, device->host copies of each
+                     patch's interior span, overlapped; wall clock)
   --impl reference   the FP64 CPU oracle on the host cores (a bounded sample
                      of the same workload per step)
 

@@ -1,0 +1,35 @@
+"""Host-side accounting of bench.py (no GPU): the interior span the in-place
+host pipeline copies back, against the cells of a patch box counted one by
+one, and the algorithmic bytes per patch of the roofline."""
+import importlib.util
+import itertools
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("d,p", [(1, 4), (2, 5), (2, 17), (3, 3), (3, 5), (3, 7)])
+def test_interior_span_is_first_to_last_interior_cell(bench, d, p):
+    s = d + 2
+    ne = p + 2
+    idx = [sum(c[m] * ne ** m for m in range(d))
+           for c in itertools.product(range(ne), repeat=d) if all(1 <= x <= p for x in c)]
+    assert bench._interior_span(d, p, s) == (max(idx) - min(idx) + 1) * s
+
+
+@pytest.mark.parametrize("d,p", [(2, 5), (3, 5), (3, 7)])
+def test_algorithmic_bytes_count_interior_and_face_halo(bench, d, p):
+    s, item = d + 2, 4
+    interior = p ** d
+    face_halo = 2 * d * p ** (d - 1)
+    assert bench.alg_bytes_per_patch(d, p, item) == ((interior + face_halo) * s + interior * s) * item

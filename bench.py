@@ -21,8 +21,8 @@ Arms:
   default            the CUDA library (value: device-resident timing; e2e: the
                      update through fv_patch_update_host on the pinned host
                      batch, advanced in place: chunked host->device copies of
-                     the boxes, the update, device->host copies of each
-                     patch's interior span, overlapped; wall clock)
+                     each patch's face-halo span, the update, device->host
+                     copies of its interior span, overlapped; wall clock)
   --impl reference   the FP64 CPU oracle on the host cores (a bounded sample
                      of the same workload per step)
 
@@ -349,8 +349,9 @@ def run_ours(args, ws, rank, local):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ems = float(tt.item())
     e2e_value = ws * cells_per_step * e2e_steps / (ems / 1e3)
-    h2d = h_q.numel() * itemsize + h_off.numel() * 8 + h_sz.numel() * 4
-    d2h = n * _interior_span(d, p, s) * itemsize  # one size, equal spacing: the span copy
+    # one size, equal spacing: the span copies
+    h2d = n * _face_halo_span(d, p, s) * itemsize + h_off.numel() * 8 + h_sz.numel() * 4
+    d2h = n * _interior_span(d, p, s) * itemsize
     if not args.no_variants:
         # the same pipeline out of place (host_out != host_in): whole boxes back
         fv.fv_patch_update_host(b.h, h_q, h_out, off_np, sz_np, n, dx, dt_e2e)
@@ -361,7 +362,8 @@ def run_ours(args, ws, rank, local):
         oms = (time.perf_counter() - t_oop) * 1e3
         variants["e2e_out_of_place"] = {
             "value": cells_per_step * e2e_steps / (oms / 1e3), "unit": UNIT,
-            "ms_per_step": oms / e2e_steps, "h2d_bytes_per_step": h2d,
+            "ms_per_step": oms / e2e_steps,
+            "h2d_bytes_per_step": h_q.numel() * itemsize + h_off.numel() * 8 + h_sz.numel() * 4,
             "d2h_bytes_per_step": h_out.numel() * itemsize,
             "what": "fv_patch_update_host from the pinned host batch into a second one: whole "
                     "boxes (halos included) copied back"}
@@ -449,9 +451,10 @@ def run_ours(args, ws, rank, local):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                     "what": "fv_patch_update_host in place on the pinned host batch (patches "
-                            "with their halos): chunked host->device copies of the boxes, "
-                            "update, device->host copies of each patch's interior span, "
-                            "overlapped; wall clock"},
+                            "with their halos): chunked host->device copies of each patch's "
+                            "span from its first to its last face-halo cell, update, "
+                            "device->host copies of each patch's interior span, overlapped; "
+                            "wall clock"},
             "gpu_launches": args.steps,
             "step_kernel_ms": kern_ms,
             "roofline": roof,
@@ -934,6 +937,17 @@ def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, s
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
                          "peak_source": peak_src}}
+
+
+def _face_halo_span(d, p, s):
+    """Elements of a patch box from its first to past its last face-halo cell
+    (what the in-place host update copies in)."""
+    tot, top = 0, 1
+    for m in range(d):
+        tot += top
+        if m + 1 < d:
+            top *= p + 2
+    return s * (p * (tot - top) + (p + 1) * top + 1) - s * (tot - top)
 
 
 def _interior_span(d, p, s):

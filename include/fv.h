@@ -187,9 +187,11 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
  *                      interior cells of host_out receive Q^{n+1}, its halo
  *                      cells a copy of host_in's.  host_out == host_in
  *                      updates in place: then a chunk of equally spaced
- *                      patches of one size is copied back only from each
- *                      patch's first to its last interior cell (a third less
- *                      for 5^3 boxes), the halo cells staying as they are.
+ *                      patches of one size is copied in only from each
+ *                      patch's first to its last face-halo cell (what the
+ *                      update reads) and back only from its first to its
+ *                      last interior cell (a third less for 5^3 boxes), the
+ *                      halo cells staying as they are.
  *   patch_offsets, patch_sizes  HOST arrays; offsets must ascend without
  *                      overlap (FV_ERR_INVALID_ARG), 16-byte multiples
  *                      (FV_ERR_ALIGNMENT); sizes in 1..max_patch_size

@@ -9,9 +9,10 @@
 // reused in turn, so the upload of a chunk need not wait for the download of
 // the chunk before it (full-duplex link); events order the reuse.  Updated in
 // place on the host (host_in == host_out), a chunk of equally spaced patches
-// of one size travels back as each patch's span from its first to its last
-// interior cell (one 2D copy; 229 of the 343 cells of a 5^3 box): the halo
-// cells are on the host already.
+// of one size travels as spans, one 2D copy each way: in, each patch from
+// its first to its last face-halo cell (what the update reads: 327 of the 343
+// cells of a 5^3 box); back, from its first to its last interior cell (229):
+// the halo cells are on the host already.
 #include <stdio.h>
 #include <string.h>
 
@@ -191,9 +192,34 @@ fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
       st->h_off[k][i] = off[p0 + i] - base;
       st->h_sz[k][i] = sizes[p0 + i];
     }
+    // in place, a chunk of equally spaced patches of one size moves spans
+    bool span = inplace;
+    const int64_t pitch = nc > 1 ? off[p0 + 1] - off[p0] : len(p0);
+    for (int64_t i = p0 + 1; i < p1 && span; ++i)
+      span = sizes[i] == sizes[p0] && off[i] - off[i - 1] == pitch;
+    // elements of a patch: in, first face-halo cell (1, .., 1, 0) to past the
+    // last (p, .., p, p + 1); back, first interior cell to past the last
+    int64_t lo_in = 0, hi_in = 0, lo = 0, hi = 0;
+    if (span) {
+      const int64_t p = sizes[p0], ne = p + 2;
+      int64_t sum = 0, top = 1;  // sum_m ne^m (the cell (1, .., 1)); ne^(d-1)
+      for (int m = 0; m < d; ++m) {
+        sum += top;
+        if (m + 1 < d) top *= ne;
+      }
+      lo_in = s * (sum - top);
+      hi_in = s * (p * (sum - top) + (p + 1) * top + 1);
+      lo = s * sum;
+      hi = s * (p * sum + 1);
+    }
     // host -> device, once the slot's previous output has left
     if (st->used[k]) e = cudaStreamWaitEvent(st->h2d, st->ev_free[k], 0);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && span)
+      e = cudaMemcpy2DAsync(static_cast<char*>(st->d_in[k]) + lo_in * es, (size_t)pitch * es,
+                            static_cast<const char*>(host_in) + (base + lo_in) * es,
+                            (size_t)pitch * es, (size_t)(hi_in - lo_in) * es, (size_t)nc,
+                            cudaMemcpyHostToDevice, st->h2d);
+    else if (e == cudaSuccess)
       e = cudaMemcpyAsync(st->d_in[k], static_cast<const char*>(host_in) + base * es, bytes,
                           cudaMemcpyHostToDevice, st->h2d);
     if (e == cudaSuccess)
@@ -226,22 +252,7 @@ fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
       e = fv::launch_scheduled(h, l);
     }
     if (e == cudaSuccess) e = cudaEventRecord(st->ev_comp[k], h->stream);
-    // device -> host: the whole chunk, or in place the interior spans of a
-    // chunk of equally spaced patches of one size
-    bool span = inplace;
-    const int64_t pitch = nc > 1 ? off[p0 + 1] - off[p0] : len(p0);
-    for (int64_t i = p0 + 1; i < p1 && span; ++i)
-      span = sizes[i] == sizes[p0] && off[i] - off[i - 1] == pitch;
-    int64_t lo = 0, hi = 0;  // elements of a patch: first interior cell, past the last
-    if (span) {
-      int64_t sum = 0, pw = 1;  // index of cell (1, .., 1) = sum_m NE^m
-      for (int m = 0; m < d; ++m) {
-        sum += pw;
-        pw *= sizes[p0] + 2;
-      }
-      lo = s * sum;
-      hi = s * (sizes[p0] * sum + 1);
-    }
+    // device -> host: the whole chunk, or the interior spans
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st->d2h, st->ev_comp[k], 0);
     if (e == cudaSuccess && span)
       e = cudaMemcpy2DAsync(static_cast<char*>(host_out) + (base + lo) * es, (size_t)pitch * es,

@@ -1,5 +1,5 @@
-"""Host-side accounting of bench.py (no GPU): the interior span the in-place
-host pipeline copies back, against the cells of a patch box counted one by
+"""Host-side accounting of bench.py (no GPU): the spans the in-place host
+pipeline copies in and back, against the cells of a patch box counted one by
 one, and the algorithmic bytes per patch of the roofline."""
 import importlib.util
 import itertools
@@ -25,6 +25,16 @@ def test_interior_span_is_first_to_last_interior_cell(bench, d, p):
     idx = [sum(c[m] * ne ** m for m in range(d))
            for c in itertools.product(range(ne), repeat=d) if all(1 <= x <= p for x in c)]
     assert bench._interior_span(d, p, s) == (max(idx) - min(idx) + 1) * s
+
+
+@pytest.mark.parametrize("d,p", [(1, 4), (2, 5), (2, 17), (3, 3), (3, 5), (3, 7)])
+def test_face_halo_span_covers_what_the_update_reads(bench, d, p):
+    s = d + 2
+    ne = p + 2
+    idx = [sum(c[m] * ne ** m for m in range(d))
+           for c in itertools.product(range(ne), repeat=d)
+           if sum(1 for x in c if x in (0, p + 1)) <= 1]  # interior and face-halo cells
+    assert bench._face_halo_span(d, p, s) == (max(idx) - min(idx) + 1) * s
 
 
 @pytest.mark.parametrize("d,p", [(2, 5), (3, 5), (3, 7)])

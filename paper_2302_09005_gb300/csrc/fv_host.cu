@@ -232,7 +232,9 @@ fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
     // update in place: in update mode a CTA reads only its own patch box (the
     // bulk copy into shared memory, before any write) and writes only that
     // patch's interior cells, so the chunk buffer can be its own output; the
-    // halo cells travel back unchanged
+    // halo cells travel back unchanged.  After a span upload the edge and
+    // corner cells outside the span hold stale values: the update uses only
+    // interior and face-halo cells, and those cells are not copied back.
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, st->ev_h2d[k], 0);
     if (e == cudaSuccess) {
       fv::UpdateLaunch l;

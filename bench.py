@@ -328,7 +328,8 @@ def run_ours(args, ws, rank, local):
     # goes through fv_patch_update_host, which overlaps chunked host->device
     # copies, the update and device->host copies.  The batch is advanced in
     # place, step after step, as an engine updates its patch storage: the
-    # copy back then takes each patch's interior span only.  dt: the CFL step
+    # copies then take spans (in: first to last face-halo cell of each
+    # patch; back: first to last interior cell).  dt: the CFL step
     # the device slot holds.  Wall-clock time of the synchronous calls.
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     off_np, sz_np = h_off.numpy(), h_sz.numpy()
@@ -366,7 +367,7 @@ def run_ours(args, ws, rank, local):
             "h2d_bytes_per_step": h_q.numel() * itemsize + h_off.numel() * 8 + h_sz.numel() * 4,
             "d2h_bytes_per_step": h_out.numel() * itemsize,
             "what": "fv_patch_update_host from the pinned host batch into a second one: whole "
-                    "boxes (halos included) copied back"}
+                    "boxes (halos included) copied both ways"}
     if not args.no_variants:
         # the device time step with serial copies around it (state and
         # metadata in, halo gather + CFL + update, state out)

@@ -349,6 +349,23 @@ typedef enum { FV_SCHED_STRIDE = 0, FV_SCHED_LPT = 1, FV_SCHED_CLASSES = 2 } fv_
  */
 fv_status fv_batch_plan(fv_batch* h, const int32_t* patch_sizes, int64_t n_patches);
 
+/*
+ * fv_batch_set_wait_limit -- how many clock cycles a CTA of the step kernel
+ * (the general update / time-step kernel; not the FP32 one-size kernels)
+ * waits for the bulk copy of a patch before it gives up, sets the timeout bit
+ * of the status word (fv_get_status then returns FV_ERR_TIMEOUT) and leaves
+ * its remaining patches unwritten.  Every wait of the device code is bounded
+ * this way; the default, about one second at 2 GHz (2e9 cycles), only runs
+ * out if a copy never completes.  cycles <= 0 restores the default; larger
+ * values are refused (FV_ERR_INVALID_ARG).  A smaller limit makes the timeout
+ * path testable on healthy hardware: the waits for copies already in flight
+ * after a wait gave up keep the full default limit, so no CTA exits with a
+ * copy pending and the context stays usable.  Applies to launches made after
+ * the call (a graph cached by fv_run_steps keeps the limit it was captured
+ * with).  Not in the paper: the failure handling of the library.
+ */
+fv_status fv_batch_set_wait_limit(fv_batch* h, long long cycles);
+
 /* Selects the schedule of later updates and time steps. */
 fv_status fv_batch_set_schedule(fv_batch* h, fv_schedule schedule);
 
@@ -540,8 +557,10 @@ fv_status fv_patch_sums(fv_batch* h, const void* q_with_halo, const int64_t* pat
  *                    (4096 chunks of 1024 patches); larger batches return
  *                    FV_ERR_UNSUPPORTED and enqueue nothing.
  *   totals           device double[s], written.
- *   status_word      device unsigned int or NULL; bad-patch (1) and
- *                    non-physical (2) bits are OR-ed into it.
+ *   status_word      device unsigned int, required (NULL returns
+ *                    FV_ERR_INVALID_ARG: the library keeps no status word
+ *                    that such a caller could read); bad-patch (1) and
+ *                    non-physical (2) bits are OR-ed into it, never cleared.
  *   cuda_stream      cudaStream_t to enqueue on (NULL: legacy default stream).
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress) and caches it; make that first call

@@ -11,7 +11,7 @@
  * What it computes, and where the paper defines it:
  *   - Euler flux f^j(q) of the compressible Euler equations, Eq. 2 (Sec. 2),
  *     with the energy flux read as (E_t + p) j_j / rho (the printed formula
- *     drops the j; see the readings list in the design doc).
+ *     lacks the factor j_j, without which it would not be a flux along j).
  *   - Maximum wave speed |u_j| + c, c = sqrt(gamma p / rho): the largest
  *     |eigenvalue| of the Euler flux Jacobian in direction j, Eq. 5.
  *     "Between Q_{i-1} and Q_i" is read as the maximum over the two states.

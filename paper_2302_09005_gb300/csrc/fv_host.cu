@@ -36,6 +36,7 @@ struct fv_host_stage {
   int64_t* h_off[kHostSlots] = {};  // pinned: rebased offsets of the chunk
   int32_t* h_sz[kHostSlots] = {};
   int64_t meta_cap = 0;
+  size_t max_pitch = 0;  // largest pitch of a 2D copy (cudaDevAttrMaxPitch)
 };
 
 namespace fv {
@@ -79,7 +80,10 @@ cudaError_t stage_reserve(fv_batch* h, size_t bytes, int64_t npatch) {
     st = new (std::nothrow) fv_host_stage();
     if (!st) return cudaErrorMemoryAllocation;
     h->host_stage = st;
-    e = cudaStreamCreateWithFlags(&st->h2d, cudaStreamNonBlocking);
+    int mp = 0;
+    e = cudaDeviceGetAttribute(&mp, cudaDevAttrMaxPitch, h->device);
+    st->max_pitch = mp > 0 ? (size_t)mp : 0;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st->h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st->d2h, cudaStreamNonBlocking);
     for (int k = 0; k < kHostSlots && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&st->ev_h2d[k], cudaEventDisableTiming);
@@ -197,6 +201,9 @@ fv_status fv_patch_update_host(fv_batch* h, const void* host_in, void* host_out,
     const int64_t pitch = nc > 1 ? off[p0 + 1] - off[p0] : len(p0);
     for (int64_t i = p0 + 1; i < p1 && span; ++i)
       span = sizes[i] == sizes[p0] && off[i] - off[i - 1] == pitch;
+    // a 2D copy takes pitches up to the device's limit; patches spaced wider
+    // apart go as one 1D copy of the chunk
+    if (span && (size_t)pitch * es > st->max_pitch) span = false;
     // elements of a patch: in, first face-halo cell (1, .., 1, 0) to past the
     // last (p, .., p, p + 1); back, first interior cell to past the last
     int64_t lo_in = 0, hi_in = 0, lo = 0, hi = 0;

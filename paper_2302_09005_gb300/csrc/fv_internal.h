@@ -12,6 +12,9 @@
 #define FV_NT 128
 // Maximum number of CTAs of a grid-stride reduction kernel (partials slots).
 #define FV_MAX_RED_BLOCKS 4096
+// Clock cycles a CTA waits for a copy before it reports FV_ERR_TIMEOUT
+// (about one second at 2 GHz).
+#define FV_WAIT_LIMIT 2000000000ll
 
 struct fv_batch {
   int d = 0, s = 0, halo = 1;
@@ -51,6 +54,7 @@ struct fv_batch {
   int64_t pairs_launches = 0;                // launches that used the FP32 pairs kernel
   void* host_stage = nullptr;                // fv_patch_update_host: streams, staging buffers
   int smem_optin = 0;                        // opt-in shared memory per CTA
+  long long wait_limit = FV_WAIT_LIMIT;      // step kernel: cycles of a copy wait
   char last_error[512] = {0};
 };
 

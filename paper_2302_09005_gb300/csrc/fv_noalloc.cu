@@ -21,18 +21,15 @@ namespace {
 // library until the process exits.
 constexpr int kNoallocChunks = 4096;
 static __device__ __align__(256) double g_noalloc_partials[kNoallocChunks * 8];
-// Status bits of calls that pass no status word of their own.
-static __device__ __align__(256) unsigned int g_noalloc_status[64];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double* g_partials_addr[kMaxDevices] = {nullptr};
-unsigned int* g_status_addr[kMaxDevices] = {nullptr};
 
-// Device addresses of the static arrays on the current device.  Looked up
-// once per device (with that device current) and cached; host code cannot
-// use the arrays' names as device addresses.
-cudaError_t noalloc_addresses(double** partials, unsigned int** status) {
+// Device address of the static array on the current device.  Looked up once
+// per device (with that device current) and cached; host code cannot use the
+// array's name as a device address.
+cudaError_t noalloc_partials(double** partials) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -40,16 +37,11 @@ cudaError_t noalloc_addresses(double** partials, unsigned int** status) {
   std::lock_guard<std::mutex> lock(g_mutex);
   if (g_partials_addr[dev] == nullptr) {
     void* p = nullptr;
-    void* s = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
-    e = cudaGetSymbolAddress(&s, g_noalloc_status);
-    if (e != cudaSuccess) return e;
     g_partials_addr[dev] = static_cast<double*>(p);
-    g_status_addr[dev] = static_cast<unsigned int*>(s);
   }
   *partials = g_partials_addr[dev];
-  *status = g_status_addr[dev];
   return cudaSuccess;
 }
 
@@ -63,7 +55,9 @@ extern "C" fv_status fv_conserved_totals_noalloc(int d, int s, fv_precision prec
                                                  void* cuda_stream) {
   if (d < 1 || d > 3 || s != d + 2) return FV_ERR_INVALID_ARG;
   if (precision != FV_FP64 && precision != FV_FP32) return FV_ERR_INVALID_ARG;
-  if (n_patches < 0 || !totals) return FV_ERR_INVALID_ARG;
+  // the status word is required: the library keeps no word of its own that
+  // a caller could read, so without one bad patches would go unreported
+  if (n_patches < 0 || !totals || !status_word) return FV_ERR_INVALID_ARG;
   if (n_patches > (int64_t)kNoallocChunks * FV_SUM_CHUNK) return FV_ERR_UNSUPPORTED;
   if (n_patches > 0) {
     if (!q_with_halo || !patch_offsets || !patch_sizes) return FV_ERR_INVALID_ARG;
@@ -71,9 +65,9 @@ extern "C" fv_status fv_conserved_totals_noalloc(int d, int s, fv_precision prec
         ((uintptr_t)patch_sizes & 3u))
       return FV_ERR_ALIGNMENT;
   }
+  if ((uintptr_t)status_word & 3u) return FV_ERR_ALIGNMENT;
   double* partials = nullptr;
-  unsigned int* own_status = nullptr;
-  if (noalloc_addresses(&partials, &own_status) != cudaSuccess) return FV_ERR_CUDA;
+  if (noalloc_partials(&partials) != cudaSuccess) return FV_ERR_CUDA;
 
   // A handle-shaped description on the stack: no workspace, no allocation.
   fv_batch desc;
@@ -94,7 +88,7 @@ extern "C" fv_status fv_conserved_totals_noalloc(int d, int s, fv_precision prec
     l.n = n_patches;
     l.halo = 1;
     l.partials = partials;  // every slot the finish reads is written first
-    l.status = status_word ? status_word : own_status;
+    l.status = status_word;
     e = fv::launch_sums(&desc, l, nchunks);
   }
   if (e == cudaSuccess) e = fv::launch_sums_finish(&desc, partials, nchunks, totals);

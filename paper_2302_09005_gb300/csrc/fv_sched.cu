@@ -195,6 +195,14 @@ fv_status fv_batch_set_schedule(fv_batch* h, fv_schedule s) {
   return FV_OK;
 }
 
+fv_status fv_batch_set_wait_limit(fv_batch* h, long long cycles) {
+  if (!h) return FV_ERR_INVALID_ARG;
+  if (cycles > FV_WAIT_LIMIT)
+    return sched_err(h, FV_ERR_INVALID_ARG, "wait limit above the default (2e9 cycles)");
+  h->wait_limit = cycles > 0 ? cycles : FV_WAIT_LIMIT;
+  return FV_OK;
+}
+
 fv_status fv_batch_set_class_threads(fv_batch* h, int p, int threads) {
   if (!h) return FV_ERR_INVALID_ARG;
   if (p < 1 || p > h->max_patch_size || p >= 64)

@@ -78,6 +78,7 @@ struct StepParams {
   const T* __restrict__ prim_in;  // carried primitives of `in` (primitive-carry mode)
   T* __restrict__ prim_out;       // primitives of `out` (time-step modes), or null
   int64_t prim_stride;            // elements per patch of prim_in / prim_out
+  long long wait_limit = FV_WAIT_LIMIT;  // cycles of a wait for a patch's copy
 };
 
 template <int D>
@@ -165,8 +166,12 @@ struct Stage {
 };
 
 // Clock cycles a CTA waits for a copy before it reports FV_ERR_TIMEOUT
-// (about one second at 2 GHz).
-constexpr long long kWaitLimit = 2000000000ll;
+// (about one second at 2 GHz).  The step kernel's waits for the copies of the
+// patches it is about to process take the launch's limit (StepParams::
+// wait_limit, normally this value); once a wait has given up, the waits for
+// the copies still in flight take this full limit, so no CTA leaves with a
+// bulk copy pending.
+constexpr long long kWaitLimit = FV_WAIT_LIMIT;
 
 // ---------------------------------------------------------------------------
 // Copies into a stage
@@ -389,7 +394,7 @@ template <typename T, int D, bool GATHER, bool PRIMIN, int NT>
 __device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
                                          const NextPatch<T>& nx) {
   if (nx.j >= a.i_end) return;
-  const bool ok = mbar_wait_bounded(&pp.bar[nx.slot], (pp.parity >> nx.slot) & 1u, kWaitLimit);
+  const bool ok = mbar_wait_bounded(&pp.bar[nx.slot], (pp.parity >> nx.slot) & 1u, a.wait_limit);
   if (ok) {
     pp.parity ^= 1u << nx.slot;
     pp.pending &= ~(1u << nx.slot);
@@ -803,7 +808,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<T, NT>()))
     if (tid == 0) issue_stage<T, D, PRIMIN>(a, pidc, pc, oc, stage_at(0), &bar[0]);
     pp.pending = 1u;
     __syncthreads();  // face sources visible
-    const bool ok = mbar_wait_bounded(&bar[0], 0u, kWaitLimit);
+    const bool ok = mbar_wait_bounded(&bar[0], 0u, a.wait_limit);
     if (ok) {
       pp.parity ^= 1u;
       pp.pending = 0u;
@@ -931,6 +936,7 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.prim_in = static_cast<const T*>(l.prim_in);
   a.prim_out = static_cast<T*>(l.prim_out);
   a.prim_stride = l.prim_stride;
+  a.wait_limit = h->wait_limit;
   const size_t smem = step_smem_bytes<D>((int)sizeof(T), l.pmax, a.nstage);
   cudaError_t e = ensure_smem<T, D, GATHER, FUSED, PRIMIN, NT>(smem);
   if (e != cudaSuccess) return e;

@@ -105,6 +105,8 @@ def _lib() -> ctypes.CDLL:
         L.fv_batch_plan.restype = c_int
         L.fv_batch_set_schedule.argtypes = [vp, c_int]
         L.fv_batch_set_schedule.restype = c_int
+        L.fv_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+        L.fv_batch_set_wait_limit.restype = c_int
         L.fv_batch_set_class_threads.argtypes = [vp, c_int, c_int]
         L.fv_batch_set_class_threads.restype = c_int
         L.fv_batch_class_threads.argtypes = [vp, c_int, ctypes.POINTER(c_int)]
@@ -353,6 +355,10 @@ def fv_batch_plan(h, patch_sizes, n_patches: int):
 
 def fv_batch_set_schedule(h, schedule: int):
     _check(h, _lib().fv_batch_set_schedule(h, schedule), "fv_batch_set_schedule")
+
+
+def fv_batch_set_wait_limit(h, cycles: int):
+    _check(h, _lib().fv_batch_set_wait_limit(h, cycles), "fv_batch_set_wait_limit")
 
 
 def fv_batch_set_class_threads(h, p: int, threads: int):

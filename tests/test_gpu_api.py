@@ -162,6 +162,12 @@ def test_two_handles_two_streams(fv):
         b2.update(qb, ob, toff, tsz, 0.02, -1.0)
     assert b1.status() == fv.FV_OK and b2.status() == fv.FV_OK
     assert torch.equal(oa, ob)
+    # and both equal the oracle's step (CFL dt from the batch maximum, Eq. 3-5)
+    _, lam = oracle.max_eigenvalue(q, off, sz, d)
+    ref = oracle.patch_update(q, off, sz, d, 0.02, oracle.cfl_dt(lam, 0.4, 0.02, d))
+    mask = fvtest.interior_mask(off, sz, d, d + 2, len(q))
+    for o in (oa, ob):
+        assert np.all(fvtest.per_unknown_rel_err(o.cpu().numpy(), ref, mask, d + 2) <= 1e-12)
     b1.close()
     b2.close()
 
@@ -170,7 +176,9 @@ def test_concurrent_offload_from_host_threads(fv):
     """Four host threads, each with its own handle and stream, offload at the
     same time: the host pipeline and device time steps, FP64 and FP32, 2D and
     3D, patch sizes whose kernels raise their shared-memory limits
-    concurrently.  Every result equals the same calls made alone, bitwise."""
+    concurrently.  Every result equals the same calls made alone, bitwise,
+    and the oracle (one update; three full time steps) within 1e-12 (FP64)
+    or 1e-5 (FP32, against the oracle on the FP32-rounded input)."""
     import threading
     torch = fvtest.torch_cuda()
     cases = [(3, 5, 0, 300, 11), (3, 7, 1, 200, 12), (2, 17, 0, 400, 13), (3, 3, 1, 500, 14)]
@@ -220,6 +228,72 @@ def test_concurrent_offload_from_host_threads(fv):
         assert a_[0] == fv.FV_OK and r[0] == fv.FV_OK
         assert np.array_equal(a_[1], r[1])
         assert np.array_equal(a_[2], r[2])
+    for case, r in zip(cases, results):
+        d, p, prec, n, seed = case
+        q, off, sz = fvtest.random_batch(n, p, d, seed, np.float32 if prec else np.float64)
+        q = q.astype(np.float64)
+        nbr = inputs.self_periodic_neighbours(n, d)
+        tol = 1e-5 if prec else 1e-12
+        mask = fvtest.interior_mask(off, sz, d, d + 2, len(q))
+        ref_host = oracle.patch_update(q, off, sz, d, 0.01, 1e-4)
+        assert np.all(fvtest.per_unknown_rel_err(r[1], ref_host, mask, d + 2) <= tol), case
+        ref = q
+        for _ in range(3):
+            ref, _ = oracle.step(ref, off, sz, nbr, d, 0.01, 0.4)
+        assert np.all(fvtest.per_unknown_rel_err(r[2], ref, mask, d + 2) <= tol), case
+
+
+@pytest.mark.parametrize("mode", ["update", "time_step"])
+def test_copy_wait_that_runs_out_reports_timeout(fv, mode):
+    """Every device wait is bounded.  With the step kernel's copy-wait limit
+    set to one clock cycle, CTAs give up on the bulk copies of their patches:
+    the status word reports FV_ERR_TIMEOUT (no trap, no hang), and after the
+    default limit is restored the same handle computes the step again,
+    bitwise equal to a handle that never timed out and to the oracle."""
+    torch = fvtest.torch_cuda()
+    d, p = 3, 5
+    grid = (32, 32, 32)
+    n = int(np.prod(grid))
+    q, off, sz = fvtest.random_batch(n, p, d, 21)
+    nbr = inputs.grid_neighbours(grid)
+    toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
+    dx, dt = 1.0 / 160, 2e-4
+
+    def run(b):
+        x = fvtest.to_dev(q)
+        y = torch.zeros_like(x)
+        if mode == "update":
+            b.update(x, y, toff, tsz, dx, dt)
+        else:
+            b.halo_fill(x, toff, tsz, tnbr)
+            b.max_eigenvalue(x, toff, tsz, 0.4, dx)
+            b.time_step(x, y, toff, tsz, tnbr, dx, 0.4)
+        return y
+
+    b = fv.Batch(d, max_patch_size=p)
+    fv.fv_batch_set_wait_limit(b.h, 1)
+    run(b)
+    assert b.status() == fv.FV_ERR_TIMEOUT
+    fv.fv_batch_set_wait_limit(b.h, 0)  # back to the default
+    y = run(b)
+    assert b.status() == fv.FV_OK
+    ref_b = fv.Batch(d, max_patch_size=p)
+    y_ref = run(ref_b)
+    assert ref_b.status() == fv.FV_OK
+    assert torch.equal(y, y_ref)
+    with pytest.raises(fv.FvError):
+        fv.fv_batch_set_wait_limit(b.h, 10 ** 12)
+    b.close()
+    ref_b.close()
+    # the first 64 patches against the oracle
+    k = 64
+    got = y.cpu().numpy()
+    if mode == "update":
+        ref = oracle.patch_update(q, off, sz, d, dx, dt)
+    else:
+        ref, _ = oracle.step(q, off, sz, nbr, d, dx, 0.4)
+    mask = fvtest.interior_mask(off[:k], sz[:k], d, d + 2, len(q))
+    assert np.all(fvtest.per_unknown_rel_err(got, ref, mask, d + 2) <= 1e-12)
 
 
 def test_fp64_reciprocal_and_sqrt_within_two_ulp(fv):

@@ -3,10 +3,14 @@ chunked copy-in / update / copy-out pipeline gives bitwise the device
 update's result for any chunk size, mixed patch sizes and both precisions;
 halo cells come back as they went in; in place (host_in == host_out, where
 equally spaced patches of one size copy back only their interior spans) the
-whole buffer ends as out of place; bad layouts are refused."""
+whole buffer ends as out of place, also when the device staging still holds
+another batch's values; the results match the oracle's update (1e-12 in
+FP64; 1e-5 in FP32 against the oracle on the FP32-rounded input); bad
+layouts are refused."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2302_09005_gb300 import inputs
 from tests import fvtest
 
@@ -42,6 +46,9 @@ def test_host_pipeline_equals_device_update_bitwise(fv, prec, chunk):
     got = hout.numpy()
     mask = fvtest.interior_mask(off, sz, 3, 5, len(q))
     assert np.array_equal(got[mask], ref[mask])
+    oref = oracle.patch_update(q.astype(np.float64), off, sz, 3, dx, dt)
+    tol = 1e-5 if prec else 1e-12
+    assert np.all(fvtest.per_unknown_rel_err(got, oref, mask, 5) <= tol)
     covered = np.zeros(len(q), dtype=bool)
     for o, p in zip(off, sz):
         covered[int(o):int(o) + (int(p) + 2) ** 3 * 5] = True
@@ -94,6 +101,45 @@ def test_in_place_equals_out_of_place_bitwise(fv, prec, case, chunk):
     mask = fvtest.interior_mask(off, sz, d, d + 2, len(q))
     assert np.array_equal(hbuf.numpy()[mask], y.cpu().numpy()[mask])
     assert not np.array_equal(hbuf.numpy()[mask], q[mask])
+    oref = oracle.patch_update(q.astype(np.float64), off, sz, d, dx, dt)
+    tol = 1e-5 if prec else 1e-12
+    assert np.all(fvtest.per_unknown_rel_err(hbuf.numpy(), oref, mask, d + 2) <= tol)
+    b.close()
+
+
+@pytest.mark.parametrize("prec,d,p", [(0, 3, 5), (1, 3, 5), (1, 2, 5), (0, 2, 8)])
+def test_in_place_after_poisoned_staging(fv, prec, d, p):
+    """In place, the span upload leaves the cells of a box outside the span
+    (leading and trailing edge / corner cells) as the staging slot last held
+    them.  Fill every slot with NaN boxes first (an out-of-place call on a
+    NaN batch of the same layout, whose non-physical status is read and
+    cleared), then run the in-place call: no NaN may reach the update (status
+    FV_OK), the interiors match the oracle, and every halo and gap element of
+    the host buffer stays as it was."""
+    torch = fvtest.torch_cuda()
+    dtype = np.float32 if prec else np.float64
+    n, chunk = 157, 16
+    q, off, sz = fvtest.random_batch(n, p, d, 85 + d, dtype)
+    dx, dt = 0.01, 0.001
+    b = fv.Batch(d, precision=prec, max_patch_size=p)
+    poison = torch.full((len(q),), float("nan"), dtype=torch.from_numpy(q).dtype).pin_memory()
+    sink = torch.zeros_like(poison).pin_memory()
+    fv.fv_patch_update_host(b.h, poison, sink, off, sz, n, dx, dt, chunk)
+    assert b.status() == fv.FV_ERR_NONPHYSICAL  # the slots now hold NaN boxes
+    hbuf = torch.from_numpy(q.copy()).pin_memory()
+    fv.fv_patch_update_host(b.h, hbuf, hbuf, off, sz, n, dx, dt, chunk)
+    assert b.status() == fv.FV_OK
+    got = hbuf.numpy()
+    mask = fvtest.interior_mask(off, sz, d, d + 2, len(q))
+    assert not np.isnan(got).any()
+    assert np.array_equal(got[~mask], q[~mask])
+    oref = oracle.patch_update(q.astype(np.float64), off, sz, d, dx, dt)
+    tol = 1e-5 if prec else 1e-12
+    assert np.all(fvtest.per_unknown_rel_err(got, oref, mask, d + 2) <= tol)
+    x = fvtest.to_dev(q)
+    y = x.clone()
+    b.update(x, y, fvtest.to_dev(off), fvtest.to_dev(sz), dx, dt)
+    assert np.array_equal(got[mask], y.cpu().numpy()[mask])
     b.close()
 
 

@@ -1,6 +1,7 @@
 """CUDA path vs the FP64 CPU oracle, through the C ABI (libfv.so).
 
-Tolerances (written here, derived in the design doc):
+Tolerances (from the rounding of each precision over the few tens of
+operations per cell of one step):
   * FP64 update: per unknown, max|Q_gpu - Q_ref| / max|Q_ref| <= 1e-12.
   * FP32 update: the same measure <= 1e-5 against the oracle run on the
     FP32-rounded input.

@@ -37,6 +37,18 @@ MUTATIONS = [
      "if (nb == -2 && 1 + k < s) qd[1 + k] = -qs[1 + k];", ""),
     ("eigenvalue faces miss the low halo layer", "c[k2] = (k2 == k ? h - 1 : h) + rem % len;",
      "c[k2] = h + rem % len;"),
+    ("conservation sums over the whole box, halo included",
+     "for (int k = 0; k < d; ++k) ncell *= p;\n    for (int t = 0; t < ncell; ++t) {\n"
+     "      int c[3] = {0, 0, 0};\n      int rem = t;\n      for (int k = 0; k < d; ++k) {\n"
+     "        c[k] = h + rem % p;\n        rem /= p;",
+     "for (int k = 0; k < d; ++k) ncell *= ne;\n    for (int t = 0; t < ncell; ++t) {\n"
+     "      int c[3] = {0, 0, 0};\n      int rem = t;\n      for (int k = 0; k < d; ++k) {\n"
+     "        c[k] = rem % ne;\n        rem /= ne;"),
+    ("conservation sums read the interior at the wrong row stride",
+     "const double *qc = Q + cell_index(c, d, ne) * s;\n"
+     "      for (int v = 0; v < s; ++v) acc[v] = acc[v] + qc[v];",
+     "const double *qc = Q + cell_index(c, d, p) * s;\n"
+     "      for (int v = 0; v < s; ++v) acc[v] = acc[v] + qc[v];"),
 ]
 
 

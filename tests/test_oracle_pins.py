@@ -130,6 +130,55 @@ def test_periodic_conservation(d, p, grid):
     assert np.abs(out - q).max() > 1e-3
 
 
+@pytest.mark.parametrize("d,halo", [(1, 1), (2, 1), (3, 1), (2, 2)])
+def test_patch_sums_are_interior_sums(d, halo):
+    """The per-patch conservation sums (the FP64 epilogue of Eq. 3) cover the
+    p^d interior cells of each patch and nothing else.  Expected values come
+    from numpy slicing of each patch's box, not from the oracle: every cell
+    holds a small integer state, so every sum is exact in FP64 and any order
+    gives the same bits.  The halo cells hold values far from the interior's
+    (1000 + ...), so a sum over the whole box, or an interior read at the
+    wrong stride, is off by hundreds."""
+    s = d + 2
+    rng = np.random.default_rng(40 + d)
+    sizes = rng.integers(1, 7, 9).astype(np.int32)
+    off, total = inputs.layout(sizes, d, s, halo, 8, 16)
+    q = np.zeros(total)
+    expected = np.zeros((len(sizes), s))
+    for i, p in enumerate(sizes):
+        ne = int(p) + 2 * halo
+        box = 1000.0 + rng.integers(0, 50, (ne,) * d + (s,)).astype(np.float64)
+        inner = (slice(halo, halo + int(p)),) * d
+        box[inner] = rng.integers(-20, 20, (int(p),) * d + (s,))
+        q[off[i]:off[i] + ne ** d * s] = box.reshape(-1)
+        expected[i] = box[inner].reshape(-1, s).sum(axis=0)
+    got = oracle.patch_sums(q, off, sizes, d, s, halo=halo)
+    assert np.array_equal(got, expected)
+
+
+@pytest.mark.parametrize("d,p,grid", [(1, 5, (4,)), (2, 3, (4, 3)), (3, 2, (2, 3, 2))])
+def test_patch_sums_add_up_to_the_domain_totals(d, p, grid):
+    """On a patch mesh cut from a domain (halos then filled from the
+    neighbours, so they differ from the interior), the per-patch sums of
+    each patch equal the sum of that patch's block of the domain, and
+    together the domain total (integer states: exact)."""
+    s = d + 2
+    rng = np.random.default_rng(50 + d)
+    N = [g * p for g in grid]
+    U = rng.integers(-30, 30, tuple(N[::-1]) + (s,)).astype(np.float64)
+    q, off, sz, g = inputs.domain_to_patches(U, p)
+    oracle.halo_fill(q, off, sz, inputs.grid_neighbours(grid), d, s)
+    got = oracle.patch_sums(q, off, sz, d, s)
+    D = inputs.patches_to_domain(q, off, p, grid, s)
+    assert np.array_equal(D, U)
+    idx = 0
+    for blk in np.ndindex(*grid[::-1]):  # slowest axis first; patch index x fastest
+        sl = tuple(slice(b * p, (b + 1) * p) for b in blk)
+        assert np.array_equal(got[idx], U[sl].reshape(-1, s).sum(axis=0)), idx
+        idx += 1
+    assert np.array_equal(got.sum(axis=0), U.reshape(-1, s).sum(axis=0))
+
+
 @pytest.mark.parametrize("d,p,grid", [(2, 4, (3, 3)), (3, 3, (2, 2, 2))])
 def test_patch_decomposition_invariance_bitwise(d, p, grid):
     """Cutting a periodic domain into patches does not change the result:

@@ -430,9 +430,24 @@ fv_status fv_batch_autotune(fv_batch* h, const void* in_with_halo, void* scratch
 
 typedef struct fv_mlp_trainer fv_mlp_trainer; /* opaque */
 
-/* Workspace for batches of up to max_batch samples, on cuda_stream. */
+/*
+ * The trainer: batches of up to max_batch samples, on cuda_stream (on the
+ * current device).  The network kernel walks tiles of 128 samples, two CTAs
+ * per SM, each CTA running forward, loss gradient, backward and the weight
+ * gradients of its tiles on the tensor cores (tcgen05) and leaving one
+ * partial gradient; a second kernel sums the partials in a fixed order and
+ * applies Adam, so results are deterministic.  The trainer owns the partial
+ * gradients (2 x SMs x FV_MLP_NPARAM floats), the Adam moments (zero at
+ * creation) and a status word.  x and target (below) must be 16-byte
+ * aligned (FV_ERR_ALIGNMENT otherwise).
+ */
 fv_status fv_mlp_trainer_create(fv_mlp_trainer** t, int64_t max_batch, void* cuda_stream);
 fv_status fv_mlp_trainer_destroy(fv_mlp_trainer* t);
+
+/* Synchronises the trainer's stream, reads and clears its status word:
+ * FV_ERR_TIMEOUT if a kernel gave up waiting for its products (bounded
+ * waits, about one second), else FV_OK. */
+fv_status fv_mlp_trainer_status(fv_mlp_trainer* t);
 
 /* y (device float[batch*4]) = network(x) for normalised inputs x
  * (device float[batch*16]). */
@@ -449,6 +464,19 @@ fv_status fv_mlp_grad(fv_mlp_trainer* t, const float* params, const float* x,
  * trainer) on params in place; *loss receives the batch loss before it. */
 fv_status fv_mlp_train_step(fv_mlp_trainer* t, float* params, const float* x, const float* target,
                             int64_t batch, float lr, int step, float* loss);
+
+/*
+ * n_steps Adam steps (steps first_step .. first_step + n_steps - 1, each
+ * counted as in fv_mlp_train_step) on consecutive minibatches of a sample set
+ * already on the device: step k uses the batch rows starting at
+ * ((k - 1) mod (n_samples / batch)) * batch of x (float[n_samples*16]) and
+ * target (float[n_samples*4]).  losses (device float[n_steps], nullable)
+ * receives each step's batch loss.  Two kernel launches per step, enqueued
+ * without synchronisation.
+ */
+fv_status fv_mlp_train_steps(fv_mlp_trainer* t, float* params, const float* x,
+                             const float* target, int64_t n_samples, int64_t batch,
+                             int first_step, int n_steps, float lr, float* losses);
 
 /*
  * Learned correction on 2D patch meshes (handles with d == 2 and patches of

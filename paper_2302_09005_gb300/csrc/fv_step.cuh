@@ -173,6 +173,14 @@ struct Stage {
 // bulk copy pending.
 constexpr long long kWaitLimit = FV_WAIT_LIMIT;
 
+// Wait for a patch's copy with the launch's limit: the default limit with
+// try_wait; a shortened one (a test of the timeout path) by polling.
+__device__ __forceinline__ bool wait_patch_copy(uint64_t* bar, uint32_t parity,
+                                                long long limit) {
+  return limit >= kWaitLimit ? mbar_wait_bounded(bar, parity, limit)
+                             : mbar_wait_polled(bar, parity, limit);
+}
+
 // ---------------------------------------------------------------------------
 // Copies into a stage
 // ---------------------------------------------------------------------------
@@ -394,7 +402,7 @@ template <typename T, int D, bool GATHER, bool PRIMIN, int NT>
 __device__ __forceinline__ void mid_hook(const StepParams<T>& a, Pipe& pp,
                                          const NextPatch<T>& nx) {
   if (nx.j >= a.i_end) return;
-  const bool ok = mbar_wait_bounded(&pp.bar[nx.slot], (pp.parity >> nx.slot) & 1u, a.wait_limit);
+  const bool ok = wait_patch_copy(&pp.bar[nx.slot], (pp.parity >> nx.slot) & 1u, a.wait_limit);
   if (ok) {
     pp.parity ^= 1u << nx.slot;
     pp.pending &= ~(1u << nx.slot);
@@ -808,7 +816,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<T, NT>()))
     if (tid == 0) issue_stage<T, D, PRIMIN>(a, pidc, pc, oc, stage_at(0), &bar[0]);
     pp.pending = 1u;
     __syncthreads();  // face sources visible
-    const bool ok = mbar_wait_bounded(&bar[0], 0u, a.wait_limit);
+    const bool ok = wait_patch_copy(&bar[0], 0u, a.wait_limit);
     if (ok) {
       pp.parity ^= 1u;
       pp.pending = 0u;

@@ -121,8 +121,12 @@ def _lib() -> ctypes.CDLL:
         L.fv_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
         L.fv_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         L.fv_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, c_int, vp]
+        L.fv_mlp_train_steps.argtypes = [vp, vp, vp, vp, i64, i64, c_int, c_int, ctypes.c_float,
+                                         vp]
+        L.fv_mlp_trainer_status.argtypes = [vp]
         for name in ("fv_mlp_trainer_create", "fv_mlp_trainer_destroy", "fv_mlp_forward",
-                     "fv_mlp_grad", "fv_mlp_train_step"):
+                     "fv_mlp_grad", "fv_mlp_train_step", "fv_mlp_train_steps",
+                     "fv_mlp_trainer_status"):
             getattr(L, name).restype = c_int
         L.fv_corr_stride.argtypes = [vp]
         L.fv_corr_stride.restype = i64
@@ -431,6 +435,16 @@ class MlpTrainer:
         _check(None, _lib().fv_mlp_train_step(self.h, _ptr(params), _ptr(x), _ptr(target),
                                               x.shape[0], lr, step, _ptr(loss)),
                "fv_mlp_train_step")
+
+    def train_steps(self, params, x, target, batch: int, first_step: int, n_steps: int,
+                    lr: float, losses=None):
+        """n_steps Adam steps on consecutive minibatches of (x, target)."""
+        _check(None, _lib().fv_mlp_train_steps(self.h, _ptr(params), _ptr(x), _ptr(target),
+                                               x.shape[0], batch, first_step, n_steps, lr,
+                                               _ptr(losses)), "fv_mlp_train_steps")
+
+    def status(self) -> int:
+        return _lib().fv_mlp_trainer_status(self.h)
 
 
 def _sp(stream):

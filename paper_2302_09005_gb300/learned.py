@@ -162,18 +162,22 @@ def train(X, T, norm, *, steps: int, batch: int, lr: float, seed: int, stream):
     Xs, Ts = X[perm].contiguous(), T[perm].contiguous()
     params = torch.from_numpy(init_params(seed)).cuda()
     trainer = fv.MlpTrainer(batch, stream)
-    loss = torch.empty(1, dtype=torch.float32, device="cuda")
-    losses = []
-    nb = Xs.shape[0] // batch
+    step_loss = torch.zeros(steps, dtype=torch.float32, device="cuda")
+    n1 = int(0.9 * steps)  # steps 1..n1 at lr, the rest at lr / 10
     with torch.cuda.stream(stream):
-        for it in range(1, steps + 1):
-            i0 = ((it - 1) % nb) * batch
-            rate = lr if it <= 0.9 * steps else lr * 0.1
-            trainer.train_step(params, Xs[i0:i0 + batch], Ts[i0:i0 + batch], rate, it, loss)
-            if it == 1 or it % max(1, steps // 20) == 0 or it == steps:
-                losses.append((it, float(loss.item())))
+        if n1 > 0:
+            trainer.train_steps(params, Xs, Ts, batch, 1, n1, lr, step_loss[:n1])
+        if steps > n1:
+            trainer.train_steps(params, Xs, Ts, batch, n1 + 1, steps - n1, lr * 0.1,
+                                step_loss[n1:])
     stream.synchronize()
+    st = trainer.status()
     trainer.close()
+    if st != fv.FV_OK:
+        raise RuntimeError(f"training status {st}")
+    sl = step_loss.cpu().numpy()
+    losses = [(it, float(sl[it - 1])) for it in range(1, steps + 1)
+              if it == 1 or it % max(1, steps // 20) == 0 or it == steps]
     return params, losses
 
 

@@ -1,4 +1,5 @@
-"""BF16 tensor-core network kernels against the FP64 oracle (oracle/mlp.py).
+"""BF16 tensor-core network kernels (tcgen05) against the FP64 oracle
+(oracle/mlp.py).
 
 The GPU rounds weights, inputs and hidden activations to BF16 before every
 product and accumulates in FP32; the oracle is run in FP64 on the same
@@ -58,8 +59,10 @@ def test_forward_matches_oracle(fv, B):
     tr.close()
 
 
-@pytest.mark.parametrize("B", [64, 5000])
+@pytest.mark.parametrize("B", [64, 5000, 50000])
 def test_gradient_matches_oracle(fv, B):
+    """B = 50000 is 391 tiles of 128 samples: more than the kernel's CTAs, so
+    the weight gradients accumulate over several tiles in tensor memory."""
     torch = fvtest.torch_cuda()
     theta, X, T = data(B, 2)
     tr = fv.MlpTrainer(B)
@@ -105,4 +108,36 @@ def test_adam_training_reduces_the_loss(fv):
         if step in (1, 400):
             losses.append(loss.item())
     assert losses[-1] < 0.1 * losses[0], losses
+    assert tr.status() == fv.FV_OK
     tr.close()
+
+
+def test_train_steps_equal_single_steps_bitwise(fv):
+    """fv_mlp_train_steps (many steps per call, losses on the device) gives
+    bitwise the parameters and losses of the same steps taken one call at a
+    time; the minibatches cycle through the sample set, the last partial
+    batch unused."""
+    torch = fvtest.torch_cuda()
+    rng = np.random.default_rng(4)
+    n, B, steps = 5000, 1024, 11
+    X = fvtest.to_dev(rng.standard_normal((n, 16)), torch.float32)
+    T = fvtest.to_dev(0.3 * rng.standard_normal((n, 4)), torch.float32)
+    th0 = fvtest.to_dev(mlp.init_params(4), torch.float32)
+    ta, tb = fv.MlpTrainer(B), fv.MlpTrainer(B)
+    pa, pb = th0.clone(), th0.clone()
+    la = torch.zeros(steps, dtype=torch.float32, device="cuda")
+    ta.train_steps(pa, X, T, B, 1, 6, 2e-3, la[:6])
+    ta.train_steps(pa, X, T, B, 7, steps - 6, 2e-4, la[6:])
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    lb = []
+    nb = n // B
+    for it in range(1, steps + 1):
+        i0 = ((it - 1) % nb) * B
+        tb.train_step(pb, X[i0:i0 + B], T[i0:i0 + B], 2e-3 if it <= 6 else 2e-4, it, loss)
+        lb.append(loss.clone())
+    torch.cuda.synchronize()
+    assert torch.equal(pa, pb)
+    assert torch.equal(la, torch.cat(lb))
+    assert ta.status() == fv.FV_OK and tb.status() == fv.FV_OK
+    ta.close()
+    tb.close()

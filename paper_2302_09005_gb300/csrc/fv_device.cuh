@@ -123,6 +123,24 @@ struct Arith<double> {
   __device__ __forceinline__ double sub(double a, double b) const { return fma(b, mone, a); }
   __device__ __forceinline__ double mul(double a, double b) const { return fma(a, b, mzero); }
 };
+// A float as a double, exactly, with integer operations (sign; exponent
+// rebased from 127 to 1023; the 23 fraction bits on top of the 52): the
+// conversion instruction would run on the FP64 pipe, the scarce unit of this
+// GPU.  Zero and subnormal floats give a signed zero (subnormals, below
+// 1.2e-38, are flushed); infinities and NaNs keep their class.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu, sign = u & 0x80000000u, m = u & 0x7FFFFFu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned lo = u << 29;
+  hi = e == 0u ? sign : hi;
+  lo = e == 0u ? 0u : lo;
+  hi = e == 255u ? (sign | 0x7FF00000u | (m >> 3)) : hi;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double to_t(float f, double*) { return widen_f32(f); }
+__device__ __forceinline__ float to_t(float f, float*) { return f; }
+
 // The same operations with literal constants (the compiler may use plain
 // adds and multiplies; the results are the same bits).
 template <typename T>

@@ -7,10 +7,11 @@
 //               -> 4 GELU network, evaluated 128 faces at a time on the
 //               5th-generation tensor cores (tcgen05.mma, BF16 operands in
 //               shared memory, FP32 accumulators in tensor memory; one thread
-//               per face for the stencil, bias, GELU and output).  The update
+//               per face for the stencil, GELU and output).  The update
 //               adds C to the face flux once per face, so both cells see the
-//               same flux and the totals are conserved.  A face shared by two
-//               patches gets the same C in both (same stencil, same arithmetic).
+//               same flux and the totals are conserved.  Every face is
+//               evaluated once, and a face shared by two patches has its C
+//               written into both patches' slots.
 //   targets     the data the network is trained on: the fine solution at r
 //               times the resolution, restricted by block averages, evolves
 //               exactly by the time-and-face averages of the fine fluxes
@@ -130,53 +131,84 @@ __device__ __forceinline__ int phys_comp(int k, int vn) {
 // ---------------------------------------------------------------------------
 // Correction kernel: the network on the 5th-generation tensor cores
 // ---------------------------------------------------------------------------
-// A CTA of 256 threads takes tiles of 128 face slots (slot = patch * fmax +
-// face, fmax the faces of a patch of the handle's largest size; slots past a
-// smaller patch's faces are idle rows), in two warp groups:
+// Every face of the mesh is evaluated once.  A patch evaluates its low faces
+// (b in [0, p) along each direction); the result of its face b = 0 is also
+// the high face b = p of its low neighbour, and is written there too when
+// the two patches name each other as neighbours along that direction (as on
+// any regular mesh).  A patch evaluates its own high faces only where no
+// neighbour does (walls, outflow, or a neighbour table that is not
+// symmetric).  The faces are enumerated as slots in two ranges:
+//   A: patch * 2 pmax^2 + lf, lf = k p^2 + p b + tr (b < p);
+//   B: (after A) patch * 2 pmax + k p + tr, the high faces b = p, idle
+//      unless the patch itself must evaluate them.
+// A CTA of 256 threads takes tiles of 128 slots (idle slots are idle rows),
+// in two warp groups:
 //   producers (warps 4-7)  thread 128 + t gathers the stencil of row t of the
 //                          next tile, normalises it into row t of that tile's
 //                          A1 buffer (BF16, K-major, two buffers) and records
-//                          the row's face;
+//                          where the row's result goes; whether the tile has
+//                          any active row is reduced over the producers, and
+//                          the consumers skip tiles that have none;
 //   consumers (warps 0-3)  thread 0 issues the MMAs (tcgen05, FP32
 //                          accumulators in tensor memory, D row t = TMEM lane
 //                          t, which warp t / 32 may read); thread t reads its
-//                          row back, adds the bias, applies GELU and writes
-//                          row t of the next layer's A operand:
-//   D1 = A1[128x16] W1^T (N = 64), D2 = A2[128x64] W2^T (N = 64),
-//   D3 = A3[128x64] W3^T (N = 16, rows 4..15 of W3 zero).
+//                          row back, applies GELU and writes row t of the next
+//                          layer's A operand:
+//   D1 = A1[128x16] W1^T (N = 64), D2 = A2[128x80] W2'^T (N = 64),
+//   D3 = A2[128x80] W3'^T (N = 16, rows 4..15 of W3' zero).
+// The biases of layers 2 and 3 ride in the products: columns 64, 65 of A2
+// are ones, and the matching columns of the weight tiles hold the bias split
+// into two BF16 parts (b = hi + lo to about 2^-17 of b); layer 1 adds its
+// bias in FP32.  The GELU layers
+// write 2 gelu(z) = z (1 + tanh(u)) (one FMA after the tanh) and W2', W3'
+// hold W2 / 2, W3 / 2: the same products, exactly, as gelu(z) with W.
 // The stencil loads of one tile (through the neighbour table) overlap the
 // MMA / GELU chain of the previous one.  Named barriers hand the A1 buffers
 // over: FULL[b] (producers arrive, consumers wait) and EMPTY[b] (consumers
 // arrive once the MMA that read the buffer has completed, producers wait).
-// D1, D2 and D3 share 64 TMEM columns; A3 reuses A2's buffer (each MMA has
+// D1, D2 and D3 share 64 TMEM columns; A2 serves layers 2 and 3 (each MMA has
 // completed before its operands are overwritten).
 constexpr int kTcRows = 128;  // faces per tile: the MMA's M
 constexpr int kTcCols = 64;   // TMEM columns of a CTA
 constexpr int kCorrNT = 256;  // consumers + producers
+constexpr int kK1 = 16;       // layer-1 K: the 16 inputs
+constexpr int kK2 = 80;       // layers 2, 3 K: 64 hidden, two ones columns, zeros
 
 struct TcSmem {
-  alignas(128) unsigned char a1[2][kTcRows * 16 * 2];
-  alignas(128) unsigned char a2[kTcRows * 64 * 2];
-  alignas(128) unsigned char w1[64 * 16 * 2];
-  alignas(128) unsigned char w2[64 * 64 * 2];
-  alignas(128) unsigned char w3[16 * 64 * 2];
+  alignas(128) unsigned char a1[2][kTcRows * kK1 * 2];
+  alignas(128) unsigned char a2[kTcRows * kK2 * 2];
+  alignas(128) unsigned char w1[64 * kK1 * 2];
+  alignas(128) unsigned char w2[64 * kK2 * 2];
+  alignas(128) unsigned char w3[16 * kK2 * 2];
   alignas(16) float b1[64];
-  alignas(16) float b2[64];
-  float b3[4];
   float mu[16], rsd[16], sdy[4];
-  int64_t fpid[2][kTcRows];  // face of each row: patch, or -1 (idle row)
-  int fkj[2][kTcRows];       // j | nf1 << 10 | k << 20
+  int fpid[2][kTcRows];  // patch of each row's face, or -1 (idle row)
+  int fext[2][kTcRows];  // low neighbour that shares the face (b = 0), or -1
+  int fkj[2][kTcRows];   // j | nf1 << 10 | k << 20
+  int fany[2];           // whether the tile has an active row
   alignas(8) uint64_t bar;
   uint32_t tmem;
 };
 
-// Named barriers (0 is __syncthreads): FULL[b], EMPTY[b], the consumers'.
-constexpr int kBarFull = 1, kBarEmpty = 3, kBarCons = 5;
+// Named barriers (0 is __syncthreads): FULL[b], EMPTY[b], the consumers',
+// the producers' reduction.
+constexpr int kBarFull = 1, kBarEmpty = 3, kBarCons = 5, kBarProd = 7;
 __device__ __forceinline__ void nbar_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 __device__ __forceinline__ void nbar_arrive(int id, int n) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// Barrier over n threads that also returns whether any of them passed true.
+__device__ __forceinline__ bool nbar_or(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+      "barrier.cta.red.or.pred p, %1, %3, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(id), "r"((uint32_t)v), "r"(n)
+      : "memory");
+  return r != 0;
 }
 
 // A stencil value as float.  FP64 states are narrowed by repacking the bits
@@ -206,36 +238,37 @@ __device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v)
   *reinterpret_cast<uint4*>(dst) = u;
 }
 
-// gelu_f (fv_mma.cuh) on two values with the packed FP32 instructions: the
-// same operations, each half rounded as the scalar one (the same bits), at
-// half the instruction issue; the tanh stays one special-function
-// instruction per value.
-__device__ __forceinline__ f2 gelu2(f2 z) {
+// 2 gelu(z) on two values with the packed FP32 instructions, in the tanh form
+// of gelu_f (fv_mma.cuh): u = z (c1 + c3 z^2), 2 gelu(z) = z + z tanh(u).
+// Each half is rounded as the scalar operation would be; the tanh is one
+// special-function instruction per value.
+__device__ __forceinline__ f2 gelu2x2(f2 z) {
   const f2 c3 = f2_pack(0.0356774081f, 0.0356774081f), c1 = f2_pack(0.7978845608f, 0.7978845608f);
-  const f2 half = f2_pack(0.5f, 0.5f);
   const f2 u = mul2(z, fma2(c3, mul2(z, z), c1));
-  const f2 h = mul2(half, z);
   float ul, uh;
   f2_unpack(u, ul, uh);
-  return fma2(h, f2_pack(tanh_hw(ul), tanh_hw(uh)), h);
+  return fma2(z, f2_pack(tanh_hw(ul), tanh_hw(uh)), z);
 }
 
-// Row `row` of a 64-wide hidden layer: TMEM accumulators + bias -> GELU ->
-// BF16 into the K-major A tile of the next layer.
-__device__ __forceinline__ void hidden_row(uint32_t trow, const float* bias, unsigned char* a,
-                                           int row) {
+// Row `row` of a 64-wide hidden layer: TMEM accumulators (+ bias, where the
+// product does not carry it) -> 2 gelu -> BF16 into columns 0..63 of the
+// K-major A2 tile.
+template <bool BIAS>
+__device__ __forceinline__ void hidden_row(uint32_t trow, unsigned char* a, int row,
+                                           const float* bias) {
 #pragma unroll
   for (int c = 0; c < 64; c += 16) {
     float v[16];
     tc_ld16(trow + c, v);
 #pragma unroll
     for (int i = 0; i < 16; i += 2) {
-      const f2 g = gelu2(add2(f2_pack(v[i], v[i + 1]),
-                              *reinterpret_cast<const f2*>(bias + c + i)));
+      f2 z = f2_pack(v[i], v[i + 1]);
+      if (BIAS) z = add2(z, *reinterpret_cast<const f2*>(bias + c + i));
+      const f2 g = gelu2x2(z);
       f2_unpack(g, v[i], v[i + 1]);
     }
-    store_bf16x8(a + tc_kmajor_offset(row, c, 64), v);
-    store_bf16x8(a + tc_kmajor_offset(row, c + 8, 64), v + 8);
+    store_bf16x8(a + tc_kmajor_offset(row, c, kK2), v);
+    store_bf16x8(a + tc_kmajor_offset(row, c + 8, kK2), v + 8);
   }
 }
 
@@ -248,30 +281,120 @@ __device__ __forceinline__ void tc_handoff_cons() {
   tc_fence_after_sync();
 }
 
+// BF16 parts of a bias: b ~ hi + lo.
+__device__ __forceinline__ void bias_parts(float b, uint16_t& hi, uint16_t& lo) {
+  hi = f32_to_bf16(b);
+  lo = f32_to_bf16(b - bf16_to_f32(hi));
+}
+
+// Slot decoding of one range: (pid, lf) = divmod(slot, per) advanced by the
+// CTA stride each tile instead of divided anew.
+struct SlotWalk {
+  int64_t pid;
+  int lf;
+  int64_t qstep;
+  int rstep;
+  int per;
+  __device__ __forceinline__ void init(int64_t slot, int per_, int64_t sstep) {
+    per = per_;
+    pid = slot / per;
+    lf = (int)(slot - pid * per);
+    qstep = sstep / per;
+    rstep = (int)(sstep - qstep * per);
+  }
+  __device__ __forceinline__ void advance() {
+    pid += qstep;
+    lf += rstep;
+    if (lf >= per) {
+      lf -= per;
+      ++pid;
+    }
+  }
+};
+
+// Stage of patch pid for the correction kernel's producers (thread `t` of
+// `nt`): its interior and the two cell layers beyond each face, narrowed to
+// float, one float4 per cell at (X, Y) = (x + 1, y + 1), X, Y in [0, p + 4).
+template <typename T>
+__device__ __forceinline__ void stage_patch(const MeshView<T>& m, int64_t pid, int p,
+                                            float4* stage, int t, int nt) {
+  const int ns = p + 4;
+  const int total = p * p + 8 * p;  // interior, then 4 sides x 2 layers x p
+  for (; t < total; t += nt) {
+    int x, y;
+    if (t < p * p) {
+      y = t / p;
+      x = 1 + t - y * p;
+      ++y;
+    } else {
+      const int u = t - p * p;
+      const int side4 = u / (2 * p);  // 0: -x, 1: +x, 2: -y, 3: +y
+      const int r = u - side4 * 2 * p;
+      const int layer = r / p;  // 0: next to the face, 1: beyond
+      const int tr = 1 + r - layer * p;
+      const int c = (side4 & 1) ? p + 1 + layer : -layer;
+      if (side4 < 2) { x = c; y = tr; } else { x = tr; y = c; }
+    }
+    int neg;
+    const T* src = cell_source(m, pid, p, x, y, neg);
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (u == neg) ? -narrow(src[u]) : narrow(src[u]);
+    stage[(y + 1) * ns + (x + 1)] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// Whether patch q is a valid neighbour of size p that names `back` as its
+// neighbour on side `side` of direction k.
+template <typename T>
+__device__ __forceinline__ bool links_back(const MeshView<T>& m, int64_t q, int p, int k,
+                                           int side, int64_t back) {
+  return q >= 0 && q < m.n && m.sizes[q] == p && m.nbr[q * 4 + 2 * k + side] == back;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kCorrNT, 4)
     corr_kernel(MeshView<T> m, int pmax, const float* params, const float* norm, float* corr,
                 int64_t stride) {
-  __shared__ TcSmem s;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
+  float4* stage = reinterpret_cast<float4*>(smem_raw + sizeof(TcSmem));  // (pmax + 4)^2 cells
   const int tid = threadIdx.x, warp = tid >> 5;
-  // weights (BF16, K-major tiles), biases, normalisation
-  for (int i = tid; i < 64 * 16; i += kCorrNT)
-    *reinterpret_cast<uint16_t*>(s.w1 + tc_kmajor_offset(i >> 4, i & 15, 16)) =
+  // weights (BF16, K-major tiles) with the biases in the columns that meet
+  // the ones of the A operands; W2, W3 halved for the 2 gelu of the layers
+  // before them
+  for (int i = tid; i < 64 * kK1; i += kCorrNT)
+    *reinterpret_cast<uint16_t*>(s.w1 + tc_kmajor_offset(i >> 4, i & 15, kK1)) =
         f32_to_bf16(params[kOffW1 + i]);
-  for (int i = tid; i < 64 * 64; i += kCorrNT)
-    *reinterpret_cast<uint16_t*>(s.w2 + tc_kmajor_offset(i >> 6, i & 63, 64)) =
-        f32_to_bf16(params[kOffW2 + i]);
-  for (int i = tid; i < 16 * 64; i += kCorrNT)
-    *reinterpret_cast<uint16_t*>(s.w3 + tc_kmajor_offset(i >> 6, i & 63, 64)) =
-        i < 4 * 64 ? f32_to_bf16(params[kOffW3 + i]) : (uint16_t)0;
-  if (tid < 64) {
-    s.b1[tid] = params[kOffB1 + tid];
-    s.b2[tid] = params[kOffB2 + tid];
+  if (tid < 64) s.b1[tid] = params[kOffB1 + tid];
+  for (int i = tid; i < 64 * kK2; i += kCorrNT) {
+    const int r = i / kK2, c = i - r * kK2;
+    uint16_t v = 0, hi, lo;
+    if (c < 64) v = f32_to_bf16(0.5f * bf16_to_f32(f32_to_bf16(params[kOffW2 + r * 64 + c])));
+    if (c == 64 || c == 65) {
+      bias_parts(params[kOffB2 + r], hi, lo);
+      v = c == 64 ? hi : lo;
+    }
+    *reinterpret_cast<uint16_t*>(s.w2 + tc_kmajor_offset(r, c, kK2)) = v;
   }
-  if (tid < 4) {
-    s.b3[tid] = params[kOffB3 + tid];
-    s.sdy[tid] = norm[32 + tid];
+  for (int i = tid; i < 16 * kK2; i += kCorrNT) {
+    const int r = i / kK2, c = i - r * kK2;
+    uint16_t v = 0, hi, lo;
+    if (r < 4 && c < 64)
+      v = f32_to_bf16(0.5f * bf16_to_f32(f32_to_bf16(params[kOffW3 + r * 64 + c])));
+    if (r < 4 && (c == 64 || c == 65)) {
+      bias_parts(params[kOffB3 + r], hi, lo);
+      v = c == 64 ? hi : lo;
+    }
+    *reinterpret_cast<uint16_t*>(s.w3 + tc_kmajor_offset(r, c, kK2)) = v;
   }
+  // the constant columns of A2: ones at 64, 65, zeros after them
+  for (int r = tid; r < kTcRows; r += kCorrNT) {
+    *reinterpret_cast<uint4*>(s.a2 + tc_kmajor_offset(r, 64, kK2)) =
+        make_uint4(0x3F803F80u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(s.a2 + tc_kmajor_offset(r, 72, kK2)) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid < 4) s.sdy[tid] = norm[32 + tid];
   if (tid < 16) {
     s.mu[tid] = norm[tid];
     s.rsd[tid] = 1.0f / norm[16 + tid];
@@ -286,54 +409,95 @@ __global__ void __launch_bounds__(kCorrNT, 4)
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tm = s.tmem;
-  const int64_t fmax = 2ll * (pmax + 1) * pmax;
-  const int64_t nslots = m.n * fmax;
-  const int64_t ntiles = (nslots + kTcRows - 1) / kTcRows;
+  const int perA = 2 * pmax * pmax, perB = 2 * pmax;
+  const int64_t nA = m.n * perA, nB = m.n * perB;
+  const int64_t tilesA = (nA + kTcRows - 1) / kTcRows;
+  const int64_t ntiles = tilesA + (nB + kTcRows - 1) / kTcRows;
+  // every tile of range A lies within the slots of one patch
+  const bool staged = perA % kTcRows == 0;
   constexpr uint32_t kId64 = tc_idesc_bf16(kTcRows, 64), kId16 = tc_idesc_bf16(kTcRows, 16);
   bool failed = false;
 
   if (warp >= 4) {
     // ---- producers: stencils of the tiles, one tile ahead of the consumers
     const int row = tid - kTcRows;
-    // this thread's slot = tile * 128 + row and (pid, lf) = divmod(slot,
-    // fmax), advanced by the CTA stride every tile instead of divided anew
     const int64_t sstep = (int64_t)gridDim.x * kTcRows;
-    const int64_t qstep = sstep / fmax;
-    const int rstep = (int)(sstep - qstep * fmax);
-    int64_t slot = (int64_t)blockIdx.x * kTcRows + row;
-    int64_t pid = slot / fmax;
-    int lf = (int)(slot - pid * fmax);
-    int pcur = 0, rp = 0;  // the patch size rp is for: ceil(2^16 / p), j / p = (j rp) >> 16
+    SlotWalk wa, wb;
+    wa.init((int64_t)blockIdx.x * kTcRows + row, perA, sstep);
+    wb.init(0, perB, sstep);
+    bool in_b = false;
+    int pcur = 0, rp = 0;  // the patch size rp is for: ceil(2^16 / p), x / p = (x rp) >> 16
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
       if (it >= 2) nbar_sync(kBarEmpty + b, kCorrNT);
-      bool act = slot < nslots;
+      if (tile >= tilesA && !in_b) {
+        in_b = true;
+        wb.init((tile - tilesA) * kTcRows + row, perB, sstep);
+      }
+      const int64_t slot = in_b ? (tile - tilesA) * kTcRows + row : tile * kTcRows + row;
+      const int64_t pid = in_b ? wb.pid : wa.pid;
+      const int lf = in_b ? wb.lf : wa.lf;
+      bool act = slot < (in_b ? nB : nA);
       int p = 1, nf1 = 2, k = 0, j = 0, bb = 0, tr = 0;
+      int ext = -1;
       if (act) {
         p = m.sizes[pid];
         if (p < 1 || p > pmax) {
           if (lf == 0) atomicOr(m.status, ST_BAD_PATCH);
           act = false;
-        } else {
+        } else if (!in_b) {  // a low face, b < p
+          act = lf < 2 * p * p;
+          if (act) {
+            k = lf >= p * p ? 1 : 0;
+            const int jj = lf - k * p * p;
+            if (p != pcur) {
+              pcur = p;
+              rp = (65536 + p - 1) / p;  // exact for jj < 2^16 / 16 and p <= 16
+            }
+            bb = (jj * rp) >> 16;
+            tr = jj - bb * p;
+          }
+        } else {  // a high face, b = p: only where no neighbour evaluates it
+          act = lf < 2 * p;
+          if (act) {
+            k = lf >= p ? 1 : 0;
+            tr = lf - k * p;
+            bb = p;
+            act = !links_back(m, (int64_t)m.nbr[pid * 4 + 2 * k + 1], p, k, 0, pid);
+          }
+        }
+        if (act) {
           nf1 = (p + 1) * p;
-          act = lf < 2 * nf1;
+          j = tr + p * bb;
+          if (bb == 0) {  // also the high face of the low neighbour
+            const int64_t nl = m.nbr[pid * 4 + 2 * k];
+            if (links_back(m, nl, p, k, 1, pid)) ext = (int)nl;
+          }
         }
       }
-      if (act) {
-        k = lf >= nf1 ? 1 : 0;
-        j = lf - k * nf1;
-        if (p != pcur) {
-          pcur = p;
-          rp = (65536 + p - 1) / p;  // exact for j < 2^16 / 16 and p <= 16
+      // normalised stencil Q_{b-1..b+2} in the face's normal frame -> A1 row
+      float x[16];
+      if (staged && !in_b) {
+        // the tile's rows are the low faces of one patch: its cells and
+        // halo layers are staged once, every stencil read from there
+        if (p >= 1 && p <= pmax && slot < nA) stage_patch(m, pid, p, stage, row, kTcRows);
+        nbar_sync(kBarProd, kTcRows);
+        const int ns = p + 4;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (act) q4 = stage[k == 0 ? (tr + 2) * ns + (bb + c) : (bb + c) * ns + (tr + 2)];
+          const float vn4[4] = {q4.x, k ? q4.z : q4.y, k ? q4.y : q4.z, q4.w};
+#pragma unroll
+          for (int vn = 0; vn < 4; ++vn) {
+            const int phi = 4 * c + vn;
+            x[phi] = act ? (vn4[vn] - s.mu[phi]) * s.rsd[phi] : 0.f;
+          }
         }
-        bb = (j * rp) >> 16;
-        tr = j - bb * p;
-      }
-      // normalised stencil Q_{b-1..b+2} in the face's normal frame -> A1 row;
+      } else {
       // faces whose four cells lie inside the patch read them straight from
       // its block, the others through the neighbour table
-      float x[16];
       const bool inner = act && bb >= 2 && bb + 2 <= p;
       const T* cin = nullptr;
       int sal = 0;  // elements between neighbouring cells along the normal
@@ -358,25 +522,26 @@ __global__ void __launch_bounds__(kCorrNT, 4)
 #pragma unroll
           for (int u = 0; u < 4; ++u) v[u] = (u == neg) ? -narrow(src[u]) : narrow(src[u]);
         }
+        // normal frame: the momenta swap places for y faces (selects, not
+        // a runtime index, which would put v in local memory)
+        const float vn4[4] = {v[0], k ? v[2] : v[1], k ? v[1] : v[2], v[3]};
 #pragma unroll
         for (int vn = 0; vn < 4; ++vn) {
           const int phi = 4 * c + vn;
-          x[phi] = act ? (v[phys_comp(k, vn)] - s.mu[phi]) * s.rsd[phi] : 0.f;
+          x[phi] = act ? (vn4[vn] - s.mu[phi]) * s.rsd[phi] : 0.f;
         }
       }
-      store_bf16x8(s.a1[b] + tc_kmajor_offset(row, 0, 16), x);
-      store_bf16x8(s.a1[b] + tc_kmajor_offset(row, 8, 16), x + 8);
-      s.fpid[b][row] = act ? pid : -1;
-      s.fkj[b][row] = j | (nf1 << 10) | (k << 20);
-      fence_proxy_async_smem();
-      nbar_arrive(kBarFull + b, kCorrNT);
-      slot += sstep;
-      pid += qstep;
-      lf += rstep;
-      if (lf >= fmax) {
-        lf -= (int)fmax;
-        ++pid;
       }
+      store_bf16x8(s.a1[b] + tc_kmajor_offset(row, 0, kK1), x);
+      store_bf16x8(s.a1[b] + tc_kmajor_offset(row, 8, kK1), x + 8);
+      s.fpid[b][row] = act ? (int)pid : -1;
+      s.fext[b][row] = ext;
+      s.fkj[b][row] = j | (nf1 << 10) | (k << 20) | (p << 21);
+      fence_proxy_async_smem();
+      const bool any = nbar_or(kBarProd, kTcRows, act);
+      if (row == 0) s.fany[b] = any ? 1 : 0;
+      nbar_arrive(kBarFull + b, kCorrNT);
+      if (in_b) wb.advance(); else wa.advance();
     }
   } else {
     // ---- consumers: the network on the tensor cores, one row per thread
@@ -384,7 +549,7 @@ __global__ void __launch_bounds__(kCorrNT, 4)
     uint32_t parity = 0;
     int it = 0;
     auto mma_wait = [&]() {
-      failed |= !mbar_wait_bounded(&s.bar, parity, kTcWaitLimit);
+      failed |= !mbar_wait_sleep(&s.bar, parity, kTcWaitLimit);
       parity ^= 1u;
       tc_fence_after_sync();
     };
@@ -393,46 +558,56 @@ __global__ void __launch_bounds__(kCorrNT, 4)
       tc_fence_before_sync();
       nbar_sync(kBarFull + b, kCorrNT);  // A1[b] written (and the last tile's D3 read)
       tc_fence_after_sync();
+      const bool refill = tile + 2 * gridDim.x < ntiles;
+      // this row's destination, read before buffer b is handed back
+      const int pid = s.fpid[b][tid], ext = s.fext[b][tid], fkj = s.fkj[b][tid];
+      if (s.fany[b] == 0) {  // no face of this tile is evaluated here
+        if (refill) nbar_arrive(kBarEmpty + b, kCorrNT);
+        continue;
+      }
       const bool run = !failed;  // a wait that gave up stops the tensor work
-      // ---- layer 1: 16 -> 64
+      // ---- layer 1: 16 -> 64 (+ bias)
       if (tid == 0 && run) {
-        tc_mma_bf16(tm, tc_smem_desc(s.a1[b], 128, 256), tc_smem_desc(s.w1, 128, 256), kId64, 0);
+        tc_mma_bf16(tm, tc_smem_desc(s.a1[b], 128, kK1 * 16), tc_smem_desc(s.w1, 128, kK1 * 16),
+                    kId64, 0);
         tc_commit(&s.bar);
       }
       if (run) mma_wait();
       // A1[b] has been read: the producers may refill it (if they will)
-      if (tile + 2 * gridDim.x < ntiles) nbar_arrive(kBarEmpty + b, kCorrNT);
-      if (run) hidden_row(trow, s.b1, s.a2, tid);
+      if (refill) nbar_arrive(kBarEmpty + b, kCorrNT);
+      if (run) hidden_row<true>(trow, s.a2, tid, s.b1);
       tc_handoff_cons();
-      // ---- layer 2: 64 -> 64
+      // ---- layer 2: 64 (+ bias) -> 64
       if (tid == 0 && run && !failed) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, 1024),
-                      tc_smem_desc(s.w2 + kk * 256, 128, 1024), kId64, kk > 0);
+        for (int kk = 0; kk < kK2 / 16; ++kk)
+          tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, kK2 * 16),
+                      tc_smem_desc(s.w2 + kk * 256, 128, kK2 * 16), kId64, kk > 0);
         tc_commit(&s.bar);
       }
       if (run) mma_wait();
-      if (run) hidden_row(trow, s.b2, s.a2, tid);
+      if (run) hidden_row<false>(trow, s.a2, tid, nullptr);
       tc_handoff_cons();
-      // ---- layer 3: 64 -> 4 (N = 16)
+      // ---- layer 3: 64 (+ bias) -> 4 (N = 16)
       if (tid == 0 && run && !failed) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, 1024),
-                      tc_smem_desc(s.w3 + kk * 256, 128, 1024), kId16, kk > 0);
+        for (int kk = 0; kk < kK2 / 16; ++kk)
+          tc_mma_bf16(tm, tc_smem_desc(s.a2 + kk * 256, 128, kK2 * 16),
+                      tc_smem_desc(s.w3 + kk * 256, 128, kK2 * 16), kId16, kk > 0);
         tc_commit(&s.bar);
       }
       if (run) mma_wait();
       float y[4] = {0.f, 0.f, 0.f, 0.f};
       if (run) tc_ld4(trow, y);
-      const int64_t pid = s.fpid[b][tid];
       if (run && pid >= 0) {
-        const int fkj = s.fkj[b][tid];
-        const int j = fkj & 1023, nf1 = (fkj >> 10) & 1023, k = fkj >> 20;
+        const int j = fkj & 1023, nf1 = (fkj >> 10) & 1023, k = (fkj >> 20) & 1, p = fkj >> 21;
 #pragma unroll
-        for (int vn = 0; vn < 4; ++vn)
-          corr[pid * stride + (k * 4 + phys_comp(k, vn)) * nf1 + j] = (y[vn] + s.b3[vn]) * s.sdy[vn];
+        for (int vn = 0; vn < 4; ++vn) {
+          const float c = y[vn] * s.sdy[vn];
+          const int64_t col = (int64_t)(k * 4 + phys_comp(k, vn)) * nf1;
+          corr[(int64_t)pid * stride + col + j] = c;
+          if (ext >= 0) corr[(int64_t)ext * stride + col + j + p * p] = c;
+        }
       }
     }
   }
@@ -442,6 +617,31 @@ __global__ void __launch_bounds__(kCorrNT, 4)
   __syncthreads();
   tc_fence_after_sync();
   if (warp == 0) tc_dealloc(tm, kTcCols);
+}
+
+// Dynamic shared memory of corr_kernel for patches up to pmax: the fixed part
+// and the patch stage.
+inline size_t corr_smem_bytes(int pmax) {
+  return sizeof(TcSmem) + (size_t)(pmax + 4) * (pmax + 4) * 16;
+}
+
+// Dynamic shared memory of corr_kernel<T> raised once per device.
+template <typename T>
+cudaError_t corr_smem_attr() {
+  static int set[64] = {0};
+  std::lock_guard<std::mutex> lock(smem_attr_mutex());
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && set[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(corr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)corr_smem_bytes(kLPmax));
+  // four CTAs per SM need the largest shared-memory carveout
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(corr_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) set[dev] = 1;
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -653,22 +853,33 @@ fv_status fv_flux_correction(fv_batch* h, const void* q, const int64_t* off, con
   if (n == 0) return FV_OK;
   if (!q || !off || !sizes || !nbr || !params || !norm || !corr)
     return lerr(h, FV_ERR_INVALID_ARG, "null pointer");
+  if (n > 0x7FFFFFFFll) return lerr(h, FV_ERR_UNSUPPORTED, "more than 2^31 - 1 patches");
   const int64_t stride = fv::corr_stride_for(h->max_patch_size);
-  // tiles of 128 face slots; up to four CTAs of 256 threads per SM (registers
-  // and shared memory; 4 x 64 TMEM columns of 512)
-  const int64_t ntiles = (n * (stride / 4) + fv::kTcRows - 1) / fv::kTcRows;
+  // tiles of 128 face slots (the low faces, then the high faces); up to four
+  // CTAs of 256 threads per SM (registers and shared memory; 4 x 64 TMEM
+  // columns of 512)
+  const int64_t pm = h->max_patch_size;
+  const int64_t ntiles = (n * 2 * pm * pm + fv::kTcRows - 1) / fv::kTcRows +
+                         (n * 2 * pm + fv::kTcRows - 1) / fv::kTcRows;
   const int64_t gmax = (int64_t)h->num_sms * 4;
   const int grid = (int)(ntiles < gmax ? ntiles : gmax);
+  const size_t smem = fv::corr_smem_bytes(h->max_patch_size);
+  cudaError_t e;
   if (h->prec == FV_FP64) {
+    e = fv::corr_smem_attr<double>();
     fv::MeshView<double> m{static_cast<const double*>(q), off, sizes, nbr, n, h->d_status};
-    fv::corr_kernel<double><<<grid, fv::kCorrNT, 0, h->stream>>>(m, h->max_patch_size, params,
-                                                                 norm, corr, stride);
+    if (e == cudaSuccess)
+      fv::corr_kernel<double><<<grid, fv::kCorrNT, smem, h->stream>>>(m, h->max_patch_size,
+                                                                      params, norm, corr, stride);
   } else {
+    e = fv::corr_smem_attr<float>();
     fv::MeshView<float> m{static_cast<const float*>(q), off, sizes, nbr, n, h->d_status};
-    fv::corr_kernel<float><<<grid, fv::kCorrNT, 0, h->stream>>>(m, h->max_patch_size, params,
-                                                                norm, corr, stride);
+    if (e == cudaSuccess)
+      fv::corr_kernel<float><<<grid, fv::kCorrNT, smem, h->stream>>>(m, h->max_patch_size,
+                                                                     params, norm, corr, stride);
   }
-  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return lerr(h, FV_ERR_CUDA, cudaGetErrorString(e));
+  e = cudaGetLastError();
   return e == cudaSuccess ? FV_OK : lerr(h, FV_ERR_CUDA, cudaGetErrorString(e));
 }
 

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kRows, 2) mlp_kernel(MlpArgs a) {
   auto commit_wait = [&]() {
     if (failed) return;
     if (tid == 0) tc_commit(&bar);
-    if (!mbar_wait_bounded(&bar, parity, kMlpWait)) {
+    if (!mbar_wait_sleep(&bar, parity, kMlpWait)) {
       failed = true;
       outstanding = 1;
     } else {

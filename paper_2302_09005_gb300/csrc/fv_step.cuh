@@ -566,9 +566,11 @@ __device__ __forceinline__ void patch_compute(const StepParams<T>& a, int p_rt, 
 #pragma unroll
     for (int v = 0; v < S; ++v) {
       T gv = gs[v];
-      // learned correction C of this face (G = 2F, so G + 2C = 2(F + C))
+      // learned correction C of this face (G = 2F, so G + 2C = 2(F + C)); 2C
+      // is exact in FP32, and its widening to FP64 runs on the integer pipe
       if (a.corr != nullptr)
-        gv = ar.add(gv, T(2) * (T)a.corr[i * a.corr_stride + (k * S + v) * nface + j]);
+        gv = ar.add(gv, to_t(2.f * a.corr[i * a.corr_stride + (k * S + v) * nface + j],
+                             (T*)nullptr));
       Gk[v * nface + j] = gv;
     }
   };

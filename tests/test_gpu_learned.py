@@ -102,6 +102,69 @@ def test_correction_kernel_matches_oracle(fv, prec):
     m.close()
 
 
+def bf16_net(X, theta, norm):
+    """The network on normalised-frame stencils X (..., 16) with the GPU's
+    BF16 rounding points; outputs in the normal frame times sd_y."""
+    mu, sd, sdy = norm
+    r = omlp.bf16_round
+    Xn = ((X - mu) / sd).astype(np.float32).astype(np.float64)
+    p = omlp.unpack(theta)
+    h1 = r(omlp.gelu(r(Xn.reshape(-1, 16)) @ r(p["W1"]).T + p["b1"]))
+    h2 = r(omlp.gelu(h1 @ r(p["W2"]).T + p["b2"]))
+    return ((h2 @ r(p["W3"]).T + p["b3"]) * sdy).reshape(X.shape[:-1] + (4,))
+
+
+def test_correction_faces_once_with_walls(fv):
+    """Walls on the x boundaries (mirror cells, x momentum negated), periodic
+    in y.  Each face is evaluated once: a shared face has bitwise the same
+    correction in both patches' slots, and the faces on the walls (the low
+    wall by the first patch's face b = 0, the high wall by the last patch's
+    own face b = p) match the network on stencils with mirrored ghost cells."""
+    torch = fvtest.torch_cuda()
+    N, p = 32, 8
+    g = N // p
+    rng = np.random.default_rng(5)
+    U = inputs.random_cells(rng, N * N, 2).reshape(N, N, 4)
+    m = mesh(fv, N, p, 0, U)
+    nbr = inputs.grid_neighbours((g, g))
+    for pid in range(g * g):
+        a = pid % g
+        if a == 0:
+            nbr[pid, 0] = -2
+        if a == g - 1:
+            nbr[pid, 1] = -2
+    m.nbr = fvtest.to_dev(nbr)
+    theta, norm = random_net(6)
+    pv, nv = net_to_dev(theta, norm)
+    stride = fv.fv_corr_stride(m.b.h)
+    corr = torch.full((m.n * stride,), float("nan"), dtype=torch.float32, device="cuda")
+    fv.fv_flux_correction(m.b.h, m.x, m.off, m.sizes, m.nbr, m.n, pv, nv, corr)
+    assert m.b.status() == fv.FV_OK
+    c = corr.cpu().numpy().reshape(m.n, 2, 4, (p + 1) * p)
+    assert not np.isnan(c).any()
+    nf = p * p  # offset of the high faces b = p in a direction's block
+    for pid in range(g * g):
+        for k in range(2):
+            hi = nbr[pid, 2 * k + 1]
+            if hi >= 0:  # the high face is the high neighbour's low face, bitwise
+                assert np.array_equal(c[pid, k, :, nf:], c[hi, k, :, :p]), (pid, k)
+    # x faces i = 0..N against the network on mirrored stencils
+    mir = np.array([1.0, -1.0, 1.0, 1.0])
+    Ue = np.concatenate([U[:, 1:2] * mir, U[:, 0:1] * mir, U, U[:, N - 1:N] * mir,
+                         U[:, N - 2:N - 1] * mir], axis=1)  # columns -2 .. N + 1
+    X = np.concatenate([olearned.to_normal(Ue[:, s:s + N + 1], 1) for s in range(4)], axis=-1)
+    Cx = olearned.to_normal(bf16_net(X, theta, norm), 1)  # (N, N + 1, 4), physical frame
+    Gx = np.full((N, N + 1, 4), np.nan)
+    for pid in range(g * g):
+        a, b = pid % g, pid // g
+        for j in range((p + 1) * p):
+            bb, tr = j // p, j % p
+            Gx[b * p + tr, a * p + bb] = c[pid, 0, :, j]
+    scale = np.abs(Cx).max()
+    assert np.max(np.abs(Gx - Cx)) <= 2e-2 * scale
+    m.close()
+
+
 def test_corrected_update_matches_oracle_and_conserves(fv):
     """Given the corrections, the GPU update is the oracle's update with
     F + C to FP64 roundoff, and the totals are conserved."""

@@ -34,6 +34,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -75,6 +76,10 @@ def _peaks():
 # clock) on GB300, 152 SMs.  The peak uses the maximum SM clock.
 FP64_LANES_PER_SM = 2
 NUM_SMS = 152
+# Special-function unit: 16 tanh.approx.f32 results per SM per clock (4 per
+# SM sub-partition), the rate that bounds the correction kernel's 128 GELUs
+# per face.
+SFU_TANH_PEAK = 16 * NUM_SMS * 2.07e9
 
 
 def fp64_ops_per_patch(d: int, p: int, mode: str = "carry") -> int:
@@ -784,6 +789,7 @@ def learned_variant(args, Nc: int = 1024, pc: int = 8, pf: int = 8, r: int = 4, 
     e1.record(st)
     st.synchronize()
     train_ms = e0.elapsed_time(e1)
+    steps_ms = learned.train.last_ms
     del X, T
     Uf = inputs.shear_layer(Nc * r, seed=eval_seed)
     _, _, dts, refs = learned.generate(Uf, Nc, pc, pf, r, steps, 0.4, st)
@@ -810,6 +816,50 @@ def learned_variant(args, Nc: int = 1024, pc: int = 8, pf: int = 8, r: int = 4, 
         D, ref = mc.domain(), refs[n + 1]
         l1_2x.append((np.abs(D - ref).sum(axis=(0, 1)) / np.abs(ref).sum(axis=(0, 1))).tolist())
     m2.close()
+    mean = lambda rows: float(np.mean(rows[-1]))  # noqa: E731
+    # equal cost: the plain method's cost per coarse step at N = 1024, 1448,
+    # 2048 (N / Nc substeps of its own step), its error where measured (Nc,
+    # 2 Nc), both interpolated log-log to the learned step's cost
+    cost_n = {}
+    for Nr in (Nc, int(round(Nc * 2 ** 0.5 / pc)) * pc, 2 * Nc):
+        mr = learned.Mesh2D(Nr, pc, fv.FV_FP64, st, U=inputs.shear_layer(Nr, seed=eval_seed))
+        with torch.cuda.stream(st):
+            for _ in range(3):
+                mr.step(dts[0] * Nc / Nr)
+            a, b = _events(1)[0]
+            a.record(st)
+            for _ in range(10):
+                mr.step(dts[0] * Nc / Nr)
+            b.record(st)
+        st.synchronize()
+        cost_n[Nr] = a.elapsed_time(b) / 10 * (Nr / Nc)
+        mr.close()
+    # the learned step timed as the plain ones: correction + halo fill +
+    # corrected update, ten back to back
+    ml = learned.Mesh2D(Nc, pc, fv.FV_FP64, st, U=refs[0])
+    cl = torch.zeros(ml.n * fv.fv_corr_stride(ml.b.h), dtype=torch.float32, device="cuda")
+
+    def learned_step():
+        fv.fv_flux_correction(ml.b.h, ml.x, ml.off, ml.sizes, ml.nbr, ml.n, params, norm, cl)
+        ml.step(dts[0], cl)
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            learned_step()
+        a, b = _events(1)[0]
+        a.record(st)
+        for _ in range(10):
+            learned_step()
+        b.record(st)
+    st.synchronize()
+    learned_ms = a.elapsed_time(b) / 10
+    ml.close()
+    eq = _equal_cost(cost_n, {Nc: mean(l1_plain), 2 * Nc: mean(l1_2x)}, learned_ms)
+    eq["learned_ms"] = learned_ms
+    eq["learned_mean_rel_l1"] = mean(l1_learned)
+    eq["learned_beats_plain_at_equal_cost"] = bool(mean(l1_learned) < eq["plain_mean_rel_l1"])
+    # the same network, FP32 state arithmetic
+    l1_plain32, l1_learned32, ms32 = learned.evaluate(refs[0], refs, dts, pc, params, norm, st,
+                                                      precision=fv.FV_FP32)
     # correction kernel alone: faces/s and BF16 TFLOP/s (10,752 flop per face)
     m = learned.Mesh2D(Nc, pc, fv.FV_FP32, st, U=refs[0])
     corr = torch.zeros(m.n * fv.fv_corr_stride(m.b.h), dtype=torch.float32, device="cuda")
@@ -823,18 +873,21 @@ def learned_variant(args, Nc: int = 1024, pc: int = 8, pf: int = 8, r: int = 4, 
         b.record(st)
     st.synchronize()
     kms = a.elapsed_time(b) / 10
-    faces = m.n * 2 * (pc + 1) * pc
+    faces = m.n * 2 * pc * pc  # each face of the mesh once
     flops = faces * 2 * (16 * 64 + 64 * 64 + 64 * 4)
     m.close()
     mc.close()
     peaks, src = _peaks()
     tf = flops / (kms / 1e3) / 1e12
-    mean = lambda rows: float(np.mean(rows[-1]))  # noqa: E731
+    tanh_rate = faces * 128 / (kms / 1e3)  # one hardware tanh per hidden unit
     return {
         "domain": f"{Nc}x{Nc} periodic shear layer, {pc}x{pc} patches; fine {Nc * r}^2 FP64",
         "train": {"samples": nsamples, "seeds": list(train_seeds), "steps": train_steps,
-                  "batch": batch, "ms": train_ms, "loss_first_last": [losses[0][1],
-                                                                      losses[-1][1]]},
+                  "batch": batch, "ms": train_ms, "adam_steps_ms": steps_ms,
+                  "note": "ms: normalisation, one shuffle of the sample set and the Adam "
+                          "steps; adam_steps_ms: the steps alone (tcgen05 network kernel "
+                          "and the fixed-order reduction + Adam kernel, two launches a step)",
+                  "loss_first_last": [losses[0][1], losses[-1][1]]},
         "eval_seed": eval_seed, "coarse_steps": steps,
         "rel_l1_after_steps": {"plain_Nc": l1_plain[-1], "learned_Nc": l1_learned[-1],
                                "plain_2Nc": l1_2x[-1]},
@@ -842,12 +895,50 @@ def learned_variant(args, Nc: int = 1024, pc: int = 8, pf: int = 8, r: int = 4, 
                         "plain_2Nc": mean(l1_2x)},
         "ms_per_coarse_step": {"plain_Nc": ms[False], "learned_Nc": ms[True],
                                "plain_2Nc": ms_2x / len(dts)},
+        "equal_cost": eq,
+        "fp32_state": {"mean_rel_l1": {"plain_Nc": mean(l1_plain32),
+                                       "learned_Nc": mean(l1_learned32)},
+                       "ms_per_coarse_step": {"plain_Nc": ms32[False], "learned_Nc": ms32[True]}},
         "correction_kernel": {"ms": kms, "faces": faces, "gflop": flops / 1e9,
                               "roofline": {"bound": "tensor", "achieved": tf,
                                            "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                                            "frac": tf / peaks["bf16_tflops"],
-                                           "peak_source": src + " (BF16 dense, burst)"}},
+                                           "peak_source": src + " (BF16 dense, burst)"},
+                              "roofline_sfu": {"bound": "sfu", "achieved": tanh_rate / 1e12,
+                                               "peak": SFU_TANH_PEAK / 1e12,
+                                               "unit": "T tanh/s",
+                                               "frac": tanh_rate / SFU_TANH_PEAK,
+                                               "peak_source": "derived: 16 tanh per SM per "
+                                                              "cycle x 152 SMs x 2.07 GHz"}},
     }
+
+
+def _equal_cost(cost_n, err_n, target_ms):
+    """The resolution N* at which the plain method costs target_ms per coarse
+    step and its error there: cost(N) and err(N) interpolated piecewise
+    linearly in log-log (extrapolated from the end segments outside the
+    measured range)."""
+    def interp(pts, x):
+        pts = sorted(pts)
+        lx = [math.log(a) for a, _ in pts]
+        ly = [math.log(b) for _, b in pts]
+        i = 0
+        while i < len(lx) - 2 and x > lx[i + 1]:
+            i += 1
+        t = (x - lx[i]) / (lx[i + 1] - lx[i])
+        return ly[i] + t * (ly[i + 1] - ly[i])
+    # invert cost(N): N as a function of cost
+    lnN = interp([(c, n) for n, c in cost_n.items()], math.log(target_ms))
+    n_star = math.exp(lnN)
+    err = math.exp(interp(list(err_n.items()), lnN))
+    lo, hi = min(cost_n), max(cost_n)
+    return {"cost_ms_by_N": {str(k): v for k, v in sorted(cost_n.items())},
+            "N_at_learned_cost": n_star, "plain_mean_rel_l1": err,
+            "plain_mean_rel_l1_by_N": {str(k): v for k, v in sorted(err_n.items())},
+            "interpolated": bool(lo <= n_star <= hi),
+            "how": "plain Rusanov cost per coarse step (N / Nc substeps) timed at each N; "
+                   "error measured at Nc and 2 Nc against the restricted fine run; both "
+                   "interpolated log-log to the learned step's cost"}
 
 
 def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, stream):

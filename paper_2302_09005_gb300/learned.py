@@ -152,7 +152,8 @@ def init_params(seed: int = 0) -> np.ndarray:
 def train(X, T, norm, *, steps: int, batch: int, lr: float, seed: int, stream):
     """Normalise the samples in place, shuffle once, and run `steps` Adam
     steps on contiguous minibatches (the BF16 tensor-core trainer; the last
-    tenth of the steps at lr / 10).  Returns (params, losses)."""
+    tenth of the steps at lr / 10).  Returns (params, losses); train.last_ms
+    holds the device time of the Adam steps alone (CUDA events on `stream`)."""
     import torch
     fv.fv_normalize_columns(X, norm[0:16], norm[16:32], stream)
     fv.fv_normalize_columns(T, None, norm[32:36], stream)
@@ -164,13 +165,18 @@ def train(X, T, norm, *, steps: int, batch: int, lr: float, seed: int, stream):
     trainer = fv.MlpTrainer(batch, stream)
     step_loss = torch.zeros(steps, dtype=torch.float32, device="cuda")
     n1 = int(0.9 * steps)  # steps 1..n1 at lr, the rest at lr / 10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
+        e0.record(stream)
         if n1 > 0:
             trainer.train_steps(params, Xs, Ts, batch, 1, n1, lr, step_loss[:n1])
         if steps > n1:
             trainer.train_steps(params, Xs, Ts, batch, n1 + 1, steps - n1, lr * 0.1,
                                 step_loss[n1:])
+        e1.record(stream)
     stream.synchronize()
+    train.last_ms = e0.elapsed_time(e1)
     st = trainer.status()
     trainer.close()
     if st != fv.FV_OK:

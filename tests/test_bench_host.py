@@ -43,3 +43,19 @@ def test_algorithmic_bytes_count_interior_and_face_halo(bench, d, p):
     interior = p ** d
     face_halo = 2 * d * p ** (d - 1)
     assert bench.alg_bytes_per_patch(d, p, item) == ((interior + face_halo) * s + interior * s) * item
+
+
+def test_equal_cost_interpolation(bench):
+    """Plain cost growing as N^3 and error as N^-1.5: the resolution whose cost
+    is twice the N = 1000 cost is 1000 * 2^(1/3), and the error there follows
+    the same power law (both exact in log-log)."""
+    cost = {n: 0.5 * (n / 1000.0) ** 3 for n in (1000, 1400, 2000)}
+    err = {n: 3e-3 * (n / 1000.0) ** -1.5 for n in (1000, 2000)}
+    r = bench._equal_cost(cost, err, 1.0)
+    assert r["N_at_learned_cost"] == pytest.approx(1000 * 2 ** (1 / 3), rel=1e-12)
+    assert r["plain_mean_rel_l1"] == pytest.approx(3e-3 * 2 ** -0.5, rel=1e-12)
+    assert r["interpolated"]
+    # outside the timed range: extrapolated from the end segment, and said so
+    r = bench._equal_cost(cost, err, 0.25)
+    assert r["N_at_learned_cost"] == pytest.approx(1000 * 0.5 ** (1 / 3), rel=1e-12)
+    assert not r["interpolated"]

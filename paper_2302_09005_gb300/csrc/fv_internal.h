@@ -150,12 +150,14 @@ bool pairs_class(const fv_batch* h, int p);
 bool pairs_eligible(const fv_batch* h, const UpdateLaunch& l);
 cudaError_t launch_pairs(const fv_batch* h, const UpdateLaunch& l, int grid);
 cudaError_t pairs_occupancy(int mode, int* blocks_per_sm);
-// The same for launches of one 2D patch size, p = 5 (fv_pairs2d.cu: one
-// warp per patch).
-bool pairs2d_class(const fv_batch* h, int p);
-bool pairs2d_eligible(const fv_batch* h, const UpdateLaunch& l);
-cudaError_t launch_pairs2d(const fv_batch* h, const UpdateLaunch& l, int grid);
-cudaError_t pairs2d_occupancy(int mode, int* blocks_per_sm);
+// The same for launches of one 2D patch size, p = 5 (fv_rows2d.cu: a lane
+// per row of cells, four patches per warp, rows2d_patches_per_cta() patches
+// per CTA and iteration).
+bool rows2d_class(const fv_batch* h, int p);
+bool rows2d_eligible(const fv_batch* h, const UpdateLaunch& l);
+int rows2d_patches_per_cta();
+cudaError_t launch_rows2d(const fv_batch* h, const UpdateLaunch& l, int grid);
+cudaError_t rows2d_occupancy(int mode, int* blocks_per_sm);
 // Launches the update / time-step kernel(s) under the handle's schedule.
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l);
 // Frees the schedule plan of a handle.

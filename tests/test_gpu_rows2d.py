@@ -1,5 +1,5 @@
-"""The FP32 kernel for launches of one 2D patch size (csrc/fv_pairs2d.cu, 5x5
-patches, one warp a patch): it runs (launch counter) for planned batches
+"""The FP32 kernel for launches of one 2D patch size (csrc/fv_rows2d.cu, 5x5
+patches, a lane per row of cells, four patches a warp): it runs (launch counter) for planned batches
 under every schedule and for the 5x5 class of uneven batches, and its results
 are bitwise those of the general kernel -- time steps on periodic, outflow
 and wall meshes (with per-patch wave speeds, the time step and the

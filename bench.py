@@ -541,6 +541,27 @@ def batching_variant(args, prec: str, n: int = 200000, steps_per_graph: int = 20
         e3.record(stream)
     stream.synchronize()
     ems = e2.elapsed_time(e3)
+
+    # eager steps (fv_run_steps without a graph) under one schedule
+    def eager_ms(sched, steps=steps_per_graph):
+        fv.fv_batch_set_schedule(b.h, sched)
+        with torch.cuda.stream(stream):
+            b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, 2)
+            a_, b_ = _events(1)[0]
+            a_.record(stream)
+            b.run_steps(x, y, toff, tsz, tnbr, dx, cfl, steps)
+            b_.record(stream)
+        stream.synchronize()
+        return a_.elapsed_time(b_) / steps
+    queue_ms = eager_ms(fv.FV_SCHED_QUEUE)
+    classes_ms = eager_ms(fv.FV_SCHED_CLASSES)
+    # why one launch loses: the persistent kernel has one CTA size for every
+    # patch (the largest patch's); the per-size launches at that same size
+    pers_nt = fv.fv_batch_class_threads(b.h, 7)
+    for p_ in (3, 5):
+        fv.fv_batch_set_class_threads(b.h, p_, pers_nt)
+    classes_one_nt_ms = eager_ms(fv.FV_SCHED_CLASSES)
+    ok = ok and b.status() == fv.FV_OK
     b.close()
     del x0
     names = ["stride (persistent, index order)", "lpt (persistent, largest first)",
@@ -551,6 +572,13 @@ def batching_variant(args, prec: str, n: int = 200000, steps_per_graph: int = 20
             "schedule_chosen": names[chosen],
             "ms_per_step_by_schedule": dict(zip(names, ms_sched)),
             "class_threads_chosen": class_threads,
+            "work_queue": {"ms_per_step": queue_ms, "classes_ms_per_step": classes_ms,
+                           "classes_at_one_cta_size_ms_per_step": classes_one_nt_ms,
+                           "one_cta_size": pers_nt,
+                           "what": "eager steps: FV_SCHED_QUEUE (one persistent launch, CTAs "
+                                   "pop patches largest first from a device counter) against "
+                                   "one launch per size with the tuned CTA sizes, and with "
+                                   "every size at the persistent launch's one CTA size"},
             "e2e": {"value": steps_per_graph * cells / (ems / 1e3), "unit": UNIT,
                     "h2d_bytes": q.nbytes, "d2h_bytes": q.nbytes}}
 

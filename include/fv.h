@@ -334,9 +334,20 @@ fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* patch_off
  *                     largest first (longest-processing-time-first order).
  *   FV_SCHED_CLASSES  one launch per patch size, each with the shared memory,
  *                     pipeline depth and occupancy of its own size.
- * All three give bitwise identical results.
+ *   FV_SCHED_QUEUE    one persistent launch whose CTAs pop the patches, sorted
+ *                     by size, largest first, from a work queue (a device
+ *                     counter in the handle's workspace, zeroed by a memset
+ *                     enqueued before the launch): a CTA that finishes early
+ *                     takes the next patch.
+ * All four give bitwise identical results.  fv_batch_autotune chooses among
+ * the first three.
  */
-typedef enum { FV_SCHED_STRIDE = 0, FV_SCHED_LPT = 1, FV_SCHED_CLASSES = 2 } fv_schedule;
+typedef enum {
+  FV_SCHED_STRIDE = 0,
+  FV_SCHED_LPT = 1,
+  FV_SCHED_CLASSES = 2,
+  FV_SCHED_QUEUE = 3
+} fv_schedule;
 
 /*
  * fv_batch_plan -- sorts the patches of a batch by size (a stable counting

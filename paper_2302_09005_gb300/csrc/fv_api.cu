@@ -142,7 +142,8 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
     delete h;
     return FV_ERR_UNSUPPORTED;  // max_patch_size too large for shared memory
   }
-  // workspace: status | dt | lam | partials (u64) | sum partials (double, 8 per slot)
+  // workspace: status | dt | lam | queue | partials (u64) | sum partials (double, 8
+  // per slot)
   const size_t bytes = 256 + 8ull * FV_MAX_RED_BLOCKS + 64ull * FV_MAX_RED_BLOCKS;
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ws, 0, bytes, h->stream);
@@ -156,6 +157,7 @@ fv_status fv_batch_create(fv_batch** out, int d, int s, const fv_options* o, voi
   h->d_status = reinterpret_cast<unsigned int*>(w);
   h->d_dt = reinterpret_cast<double*>(w + 64);
   h->d_lam = reinterpret_cast<unsigned long long*>(w + 128);
+  h->d_queue = reinterpret_cast<unsigned long long*>(w + 192);
   h->d_partials = reinterpret_cast<unsigned long long*>(w + 256);
   h->d_sum_partials = reinterpret_cast<double*>(w + 256 + 8ull * FV_MAX_RED_BLOCKS);
   // CTAs per SM of the untuned launches (their CTA size follows the patch size)

@@ -33,6 +33,7 @@ struct fv_batch {
   int lam_cur = 0;                           // slot holding lambda of the current state
   unsigned long long* d_partials = nullptr;  // FV_MAX_RED_BLOCKS slots
   double* d_sum_partials = nullptr;          // FV_MAX_RED_BLOCKS * 8 slots
+  unsigned long long* d_queue = nullptr;     // FV_SCHED_QUEUE: positions handed out
   int blocks_per_sm[3] = {0, 0, 0};          // occupancy by kernel mode (kModeUpdate..)
   // primitive carry of fv_run_steps: two buffers of prim_cap elements
   void* d_prim[2] = {nullptr, nullptr};
@@ -91,6 +92,7 @@ struct UpdateLaunch {
   void* prim_out = nullptr;       // time step: primitives of `out`, or null
   int64_t prim_stride = 0;        // elements per patch of the primitive buffers
   int uniform_p = 0;              // every patch of the launch has this size (0: unknown)
+  unsigned long long* queue = nullptr;  // zeroed counter: CTAs pop positions (null: stride)
 };
 
 // Kernel modes: update (halos filled by the caller), time step (halo gather,

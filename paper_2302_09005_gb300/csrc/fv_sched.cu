@@ -8,7 +8,12 @@
 //                     scheduling: the big patches start early, the small ones
 //                     fill the tail);
 //   FV_SCHED_CLASSES  one launch per patch size, each with the shared memory,
-//                     pipeline depth and occupancy of its own size.
+//                     pipeline depth and occupancy of its own size;
+//   FV_SCHED_QUEUE    one persistent launch whose CTAs pop the patches of the
+//                     size-sorted order (largest first) from a work queue, a
+//                     device counter zeroed by a memset before the launch (a
+//                     memset node in a captured graph): dynamic list
+//                     scheduling, a CTA that finishes early takes the next one.
 // fv_batch_plan sorts the patches by size (a stable counting sort);
 // fv_batch_autotune times the three on the caller's batch and keeps the
 // fastest.
@@ -109,10 +114,15 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
     cudaError_t e = step_occupancy(h, f, h->max_patch_size, h->nstage, l.nt, &bps);
     if (e != cudaSuccess) return e;
   }
-  if (h->sched == FV_SCHED_LPT && plan_ok) {
+  if ((h->sched == FV_SCHED_LPT || h->sched == FV_SCHED_QUEUE) && plan_ok) {
     l.order = h->d_order;
     l.i_begin = 0;
     l.i_end = l.n;
+    if (h->sched == FV_SCHED_QUEUE) {
+      l.queue = h->d_queue;
+      cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned long long), h->stream);
+      if (e != cudaSuccess) return e;
+    }
   }
   return launch_update(h, l, grid_for(h, l.n, bps));
 }
@@ -192,7 +202,7 @@ fv_status fv_batch_plan(fv_batch* h, const int32_t* sizes, int64_t n) {
 
 fv_status fv_batch_set_schedule(fv_batch* h, fv_schedule s) {
   if (!h) return FV_ERR_INVALID_ARG;
-  if (s != FV_SCHED_STRIDE && s != FV_SCHED_LPT && s != FV_SCHED_CLASSES)
+  if (s != FV_SCHED_STRIDE && s != FV_SCHED_LPT && s != FV_SCHED_CLASSES && s != FV_SCHED_QUEUE)
     return FV_ERR_INVALID_ARG;
   h->sched = (int)s;
   return FV_OK;

@@ -19,7 +19,8 @@
 //              a quarter of the FP64 work of a 3D step.  Bitwise equal to the
 //              time step without the carry.
 //
-// Each CTA is persistent and walks its patches i = blockIdx.x + k*gridDim.x.
+// Each CTA is persistent and walks its patches i = blockIdx.x + k*gridDim.x,
+// or pops them one at a time from a work queue (a zeroed device counter).
 // While it computes patch i, the TMA engine copies patch i+1 (and, carrying
 // primitives, their interior block) into the other of two shared-memory
 // stages (cp.async.bulk, completion on an mbarrier), and the halo cells of
@@ -79,6 +80,7 @@ struct StepParams {
   T* __restrict__ prim_out;       // primitives of `out` (time-step modes), or null
   int64_t prim_stride;            // elements per patch of prim_in / prim_out
   long long wait_limit = FV_WAIT_LIMIT;  // cycles of a wait for a patch's copy
+  unsigned long long* queue = nullptr;    // zeroed counter of positions handed out, or null
 };
 
 template <int D>
@@ -802,16 +804,28 @@ __global__ void __launch_bounds__(NT, (min_blocks<T, NT>()))
   unsigned long long lam_next = 0ull;
 
   // Processing sequence: positions [i_begin, i_end), patch order[pos] (or
-  // pos itself), CTA b takes positions i_begin + b, + gridDim.x, ...
+  // pos itself).  CTA b takes positions i_begin + b, + gridDim.x, ...; or,
+  // with a queue, the next position not yet handed out (one atomic per
+  // patch, by thread 0, broadcast through shared memory), so CTAs that
+  // finish early take more patches.
   auto pid_of = [&](int64_t pos) -> int64_t {
     return a.order != nullptr ? (int64_t)a.order[pos] : pos;
   };
+  __shared__ long long qpos;
+  auto next_pos = [&](int64_t pos) -> int64_t {
+    if (a.queue == nullptr) return pos + gridDim.x;
+    if (tid == 0) qpos = a.i_begin + (long long)atomicAdd(a.queue, 1ull);
+    __syncthreads();
+    const int64_t v = qpos;
+    __syncthreads();  // read by every thread before the next pop
+    return v;
+  };
   // first valid patch of this CTA, staged before the loop
-  int64_t cur = a.i_begin + blockIdx.x;
+  int64_t cur = a.queue != nullptr ? next_pos(0) : a.i_begin + blockIdx.x;
   int64_t pidc = 0;
   int pc = 0;
   int64_t oc = 0;
-  while (cur < a.i_end && !patch_ok<T, D>(a, pidc = pid_of(cur), pc, oc)) cur += gridDim.x;
+  while (cur < a.i_end && !patch_ok<T, D>(a, pidc = pid_of(cur), pc, oc)) cur = next_pos(cur);
   int s = 0;
   if (cur < a.i_end) {
     face_sources<T, D, GATHER>(a, pidc, pc, oc, fsrc);
@@ -832,10 +846,10 @@ __global__ void __launch_bounds__(NT, (min_blocks<T, NT>()))
 
   while (cur < a.i_end) {
     NextPatch<T> nx;
-    nx.j = cur + gridDim.x;
+    nx.j = next_pos(cur);
     nx.pid = 0;
     while (nx.j < a.i_end && !patch_ok<T, D>(a, nx.pid = pid_of(nx.j), nx.p, nx.off))
-      nx.j += gridDim.x;
+      nx.j = next_pos(nx.j);
     nx.slot = single ? 0 : s ^ 1;
     nx.st = stage_at(nx.slot);
     nx.fs = fsrc + 6 * nx.slot;
@@ -947,6 +961,7 @@ static cudaError_t launch_step_t(const fv_batch* h, const UpdateLaunch& l, int g
   a.prim_out = static_cast<T*>(l.prim_out);
   a.prim_stride = l.prim_stride;
   a.wait_limit = h->wait_limit;
+  a.queue = l.queue;
   const size_t smem = step_smem_bytes<D>((int)sizeof(T), l.pmax, a.nstage);
   cudaError_t e = ensure_smem<T, D, GATHER, FUSED, PRIMIN, NT>(smem);
   if (e != cudaSuccess) return e;

@@ -351,6 +351,7 @@ def fv_get_dt_ptr(h) -> int:
 FV_SCHED_STRIDE = 0
 FV_SCHED_LPT = 1
 FV_SCHED_CLASSES = 2
+FV_SCHED_QUEUE = 3
 
 
 def fv_batch_plan(h, patch_sizes, n_patches: int):

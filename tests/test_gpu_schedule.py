@@ -36,7 +36,7 @@ def test_schedules_bitwise_equal_time_step(fv, prec):
     toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
     dx, cfl = 0.01, 0.4
     outs, lams, dts = [], [], []
-    for sched in (fv.FV_SCHED_STRIDE, fv.FV_SCHED_LPT, fv.FV_SCHED_CLASSES):
+    for sched in (fv.FV_SCHED_STRIDE, fv.FV_SCHED_LPT, fv.FV_SCHED_CLASSES, fv.FV_SCHED_QUEUE):
         b = fv.Batch(3, precision=prec, max_patch_size=7)
         fv.fv_batch_plan(b.h, tsz, n)
         fv.fv_batch_set_schedule(b.h, sched)
@@ -70,7 +70,7 @@ def test_schedules_bitwise_equal_update_mode(fv):
     q, off, sz, _ = uneven(n, 52, 0)
     toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
     res = []
-    for sched in (0, 1, 2):
+    for sched in (0, 1, 2, 3):
         b = fv.Batch(3, max_patch_size=7)
         fv.fv_batch_plan(b.h, tsz, n)
         fv.fv_batch_set_schedule(b.h, sched)
@@ -88,6 +88,32 @@ def test_schedules_bitwise_equal_update_mode(fv):
     mask = fvtest.interior_mask(off, sz, 3, 5, len(q))
     assert np.all(fvtest.per_unknown_rel_err(res[0][0], ref, mask, 5) <= 1e-12)
     assert np.allclose(res[0][1], lam_ref, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_queue_schedule_in_a_graph_of_steps(fv, prec):
+    """The work queue's counter is zeroed by a memset before every launch, a
+    memset node of the captured graph: ten graph-replayed steps under
+    FV_SCHED_QUEUE equal ten eager steps under FV_SCHED_STRIDE, bitwise."""
+    torch = fvtest.torch_cuda()
+    n = 2000
+    q, off, sz, nbr = uneven(n, 57, prec)
+    toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
+    out = []
+    for sched, graph in ((fv.FV_SCHED_STRIDE, False), (fv.FV_SCHED_QUEUE, True)):
+        st = torch.cuda.Stream()  # graph capture needs a stream of its own
+        b = fv.Batch(3, precision=prec, max_patch_size=7, stream=st)
+        fv.fv_batch_plan(b.h, tsz, n)
+        fv.fv_batch_set_schedule(b.h, sched)
+        x, y = fvtest.to_dev(q), fvtest.to_dev(q)
+        torch.cuda.synchronize()
+        b.run_steps(x, y, toff, tsz, tnbr, 0.01, 0.4, 10, use_graph=graph)
+        assert b.status() == fv.FV_OK
+        out.append((x.cpu().numpy(), y.cpu().numpy(), fv.fv_read_dt(b.h)))
+        b.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
 
 
 def test_autotune_keeps_state_and_picks_a_schedule(fv):

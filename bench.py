@@ -763,6 +763,17 @@ def precision_variant(args, N: int = 4095, p: int = 5, steps: int = 100):
                                                    ).tolist()}
         if prec == "f32":
             out[prec]["pairs_kernel_used"] = fv.fv_batch_pairs_launches(b.h) > 0
+            # HBM roofline of the FP32 step (one rows2d launch per step): read
+            # the interior and face-halo cells, write the interior
+            alg = n * ((p * p + 4 * p) * 4 + p * p * 4) * 4
+            peaks, src = _peaks()
+            gbs = alg / (ms / steps / 1e3) / 1e9
+            out[prec]["roofline"] = {
+                "bound": "hbm", "kernel": "rows2d_kernel<5,step>", "achieved": gbs,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                "algorithmic_bytes_per_step": alg,
+                "traffic": _traffic("euler2d_fp32_670761x5") if n == 670761 else None,
+                "peak_source": src}
             # the same steps on the general kernel (no plan)
             bg = fv.Batch(2, precision=fv.FV_FP32, max_patch_size=p, stream=stream)
             x.copy_(x0)

@@ -1,27 +1,12 @@
-// fv_mma.cuh -- BF16 tensor-core building blocks (warp-level mma.sync,
-// m16n8k16, FP32 accumulation) and the activation of the learned face-flux
-// correction network.
+// fv_mma.cuh -- BF16 conversions, the activation of the learned face-flux
+// correction network and the layout of its parameter vector (shared by the
+// tcgen05 training and correction kernels).
 #pragma once
 
 #include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace fv {
-
-// D += A (16x16, row-major bf16) * B (16x8, column-major bf16), FP32 D.
-// Fragment ownership (lane = 4 g + t):
-//   a[0]: A[g][2t, 2t+1]      a[1]: A[g+8][2t, 2t+1]
-//   a[2]: A[g][2t+8, 2t+9]    a[3]: A[g+8][2t+8, 2t+9]
-//   b[0]: B[2t, 2t+1][g]      b[1]: B[2t+8, 2t+9][g]
-//   d[0..1]: D[g][2t, 2t+1]   d[2..3]: D[g+8][2t, 2t+1]
-__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4],
-                                          const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 // Two floats -> two bf16 (round to nearest even) packed low, high.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

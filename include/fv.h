@@ -506,6 +506,13 @@ int64_t fv_corr_stride(const fv_batch* h);
  * fv_halo_fill, two layers deep), into corr (device float, fv_corr_stride(h)
  * per patch).  params: device float[FV_MLP_NPARAM]; norm: device
  * float[FV_MLP_NNORM].  Runs on the tensor cores (BF16, FP32 accumulate).
+ * Each face of the mesh is evaluated once: a face shared by two patches that
+ * name each other as neighbours along its direction takes the stencil of the
+ * upper patch's face b = 0, and its C is written into both patches' slots
+ * (bitwise the same values); a face with no such neighbour (wall, outflow, a
+ * table that is not symmetric) is evaluated by its own patch.  Every slot of
+ * a valid patch of size p is written; slots of sizes below the handle's
+ * maximum are not.  Patches: at most 2^31 - 1 (FV_ERR_UNSUPPORTED above).
  */
 fv_status fv_flux_correction(fv_batch* h, const void* q, const int64_t* patch_offsets,
                              const int32_t* patch_sizes, const int32_t* neighbours,

@@ -1213,6 +1213,8 @@ def main():
                     default=None,
                     help="run one variant on its own")
     ap.add_argument("--small", action="store_true", help="small case of --variant")
+    ap.add_argument("--prec", choices=["f64", "f32"], default="f64",
+                    help="precision of --variant batching")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
@@ -1233,7 +1235,7 @@ def run_variant(args):
     _build.build()
     torch.cuda.set_device(0)
     if args.variant == "batching":
-        res = batching_variant(args, "f64", n=20000 if args.small else 200000)
+        res = batching_variant(args, args.prec, n=20000 if args.small else 200000)
     elif args.variant == "precision":
         res = precision_variant(args, N=1020 if args.small else 4095,
                                 steps=10 if args.small else 100)

@@ -52,6 +52,7 @@ struct fv_batch {
   int cls_only = -1;                         // autotuner: launch only this class (-1: all)
   int cls_real[64] = {0};                    // class c holds one valid size (not the rejects)
   int occ_pairs[3] = {0, 0, 0};              // CTAs per SM of the FP32 pairs kernel, by mode
+  int occ_lines[3] = {0, 0, 0};              // CTAs per SM of the FP32 3^3 lines kernel, by mode
   int64_t pairs_launches = 0;                // launches that used the FP32 pairs kernel
   void* host_stage = nullptr;                // fv_patch_update_host: streams, staging buffers
   int smem_optin = 0;                        // opt-in shared memory per CTA
@@ -160,6 +161,14 @@ bool rows2d_eligible(const fv_batch* h, const UpdateLaunch& l);
 int rows2d_patches_per_cta();
 cudaError_t launch_rows2d(const fv_batch* h, const UpdateLaunch& l, int grid);
 cudaError_t rows2d_occupancy(int mode, int* blocks_per_sm);
+// The same for launches of 3D patches of size p = 3 (fv_lines3d.cu: a lane
+// per line of cells along x, one patch per warp, lines3d_patches_per_cta()
+// patches per CTA and iteration).
+bool lines3d_class(const fv_batch* h, int p);
+bool lines3d_eligible(const fv_batch* h, const UpdateLaunch& l);
+int lines3d_patches_per_cta();
+cudaError_t launch_lines3d(const fv_batch* h, const UpdateLaunch& l, int grid);
+cudaError_t lines3d_occupancy(int mode, int* blocks_per_sm);
 // Launches the update / time-step kernel(s) under the handle's schedule.
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l);
 // Frees the schedule plan of a handle.

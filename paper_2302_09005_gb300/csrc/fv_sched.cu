@@ -47,23 +47,27 @@ static int grid_for(const fv_batch* h, int64_t count, int bps) {
 }
 
 // A launch of patches of one size: the FP32 kernel built for that size (3D
-// or 2D, p = 5) where it applies.
+// p = 5 or p = 3, 2D p = 5) where it applies.
 static cudaError_t launch_one_size(fv_batch* h, const UpdateLaunch& l, int64_t count,
                                    bool* done) {
   *done = false;
   const bool two = rows2d_eligible(h, l);
-  if (!two && !pairs_eligible(h, l)) return cudaSuccess;
+  const bool lines = !two && lines3d_eligible(h, l);
+  if (!two && !lines && !pairs_eligible(h, l)) return cudaSuccess;
   const int f = step_mode(l);
-  int& bps = h->occ_pairs[f];  // a handle has one d
+  int& bps = lines ? h->occ_lines[f] : h->occ_pairs[f];  // a handle has one d
   if (bps == 0) {
-    cudaError_t e = two ? rows2d_occupancy(f, &bps) : pairs_occupancy(f, &bps);
+    cudaError_t e = two     ? rows2d_occupancy(f, &bps)
+                    : lines ? lines3d_occupancy(f, &bps)
+                            : pairs_occupancy(f, &bps);
     if (e != cudaSuccess) return e;
   }
   *done = true;
   ++h->pairs_launches;
-  if (two) {  // a CTA takes rows2d_patches_per_cta() patches at a time
-    const int per = rows2d_patches_per_cta();
-    return launch_rows2d(h, l, grid_for(h, (count + per - 1) / per, bps));
+  if (two || lines) {  // a CTA takes several patches at a time
+    const int per = two ? rows2d_patches_per_cta() : lines3d_patches_per_cta();
+    return two ? launch_rows2d(h, l, grid_for(h, (count + per - 1) / per, bps))
+               : launch_lines3d(h, l, grid_for(h, (count + per - 1) / per, bps));
   }
   return launch_pairs(h, l, grid_for(h, count, bps));
 }
@@ -289,7 +293,8 @@ fv_status fv_batch_autotune(fv_batch* h, const void* in, void* scratch_out, cons
   // 1. the CTA size of each size class (one-class launches)
   h->sched = FV_SCHED_CLASSES;
   for (int c = 0; c < h->ncls && st == FV_OK; ++c) {
-    if (h->cls_real[c] && (fv::pairs_class(h, h->cls_p[c]) || fv::rows2d_class(h, h->cls_p[c])))
+    if (h->cls_real[c] && (fv::pairs_class(h, h->cls_p[c]) || fv::rows2d_class(h, h->cls_p[c]) ||
+                             fv::lines3d_class(h, h->cls_p[c])))
       continue;  // kernels with a fixed CTA size
     const int pi = h->cls_p[c] < 64 ? h->cls_p[c] : 63;
     const int keep = h->cls_nt[pi];

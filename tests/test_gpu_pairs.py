@@ -1,7 +1,7 @@
-"""The FP32 kernel for launches of one 3D patch size (csrc/fv_pairs.cu, 5^3
-patches): it runs (launch counter) for planned batches under every schedule
-and for the 5^3 class of uneven batches, and its results are bitwise those of
-the general kernel -- time steps on periodic, outflow and wall meshes (with
+"""The FP32 kernels for launches of one 3D patch size (csrc/fv_pairs.cu for
+5^3 patches, csrc/fv_lines3d.cu for 3^3): each runs (launch counter) for
+planned batches under every schedule and for its class of uneven batches,
+and its results are bitwise those of the general kernel -- time steps on periodic, outflow and wall meshes (with
 per-patch wave speeds and the primitives of the new state), update mode --
 and within the FP32 tolerance of the FP64 oracle.  Non-physical states are
 flagged as by the general kernel."""
@@ -14,7 +14,10 @@ from tests import fvtest
 
 pytestmark = pytest.mark.gpu
 
-P = 5
+
+@pytest.fixture(params=[5, 3], ids=["pairs5", "lines3"])
+def P(request):
+    return request.param
 
 
 @pytest.fixture(scope="module")
@@ -25,7 +28,7 @@ def fv():
     return fvmod
 
 
-def batch(fv, planned, tsz, n, sched=0, p=P):
+def batch(fv, planned, tsz, n, sched=0, p=5):
     b = fv.Batch(3, precision=fv.FV_FP32, max_patch_size=p)
     if planned:
         fv.fv_batch_plan(b.h, tsz, n)
@@ -47,7 +50,7 @@ def time_steps(fv, b, q, toff, tsz, tnbr, dx, cfl, steps, lam=None):
 @pytest.mark.parametrize("grid,periodic,bnd", [
     ((12, 10, 9), True, -1), ((3, 3, 3), False, -1), ((4, 3, 5), False, -2), ((1, 1, 1), True, -1),
     ((2, 1, 3), False, -2)])
-def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd):
+def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd, P):
     torch = fvtest.torch_cuda()
     n = int(np.prod(grid))
     q, off, sz = fvtest.random_batch(n, P, 3, 71, np.float32)
@@ -56,7 +59,7 @@ def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd)
     dx, cfl, steps = 1.0 / (grid[0] * P), 0.4, 3
     outs, lams, dts, launches = [], [], [], []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n, sched)
+        b = batch(fv, planned, tsz, n, sched, P)
         lam = torch.zeros(n, dtype=torch.float64, device="cuda")
         x = time_steps(fv, b, q, toff, tsz, tnbr, dx, cfl, steps, lam)
         assert b.status() == fv.FV_OK
@@ -72,7 +75,7 @@ def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd)
     assert dts[0] == dts[1]
 
 
-def test_primitives_of_the_new_state_bitwise(fv):
+def test_primitives_of_the_new_state_bitwise(fv, P):
     torch = fvtest.torch_cuda()
     grid = (5, 4, 3)
     n = int(np.prod(grid))
@@ -82,7 +85,7 @@ def test_primitives_of_the_new_state_bitwise(fv):
     dx, cfl = 1.0 / (grid[0] * P), 0.4
     res = []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n)
+        b = batch(fv, planned, tsz, n, 0, P)
         x, y = fvtest.to_dev(q), fvtest.to_dev(q)
         pa = torch.full((n * b.prim_stride(),), float("nan"), dtype=torch.float32, device="cuda")
         b.halo_fill(x, toff, tsz, tnbr)
@@ -100,7 +103,7 @@ def test_primitives_of_the_new_state_bitwise(fv):
 
 
 @pytest.mark.parametrize("device_dt", [False, True])
-def test_update_mode_bitwise_equal_general_kernel(fv, device_dt):
+def test_update_mode_bitwise_equal_general_kernel(fv, device_dt, P):
     torch = fvtest.torch_cuda()
     n = 1500  # more patches than resident CTAs: several per CTA
     q, off, sz = fvtest.random_batch(n, P, 3, 73, np.float32)
@@ -108,7 +111,7 @@ def test_update_mode_bitwise_equal_general_kernel(fv, device_dt):
     dx = 0.01
     res = []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n, 2)
+        b = batch(fv, planned, tsz, n, 2, P)
         x = fvtest.to_dev(q)
         y = x.clone()
         lam = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -125,15 +128,18 @@ def test_update_mode_bitwise_equal_general_kernel(fv, device_dt):
     assert np.array_equal(res[0][1], res[1][1])
 
 
-def test_time_step_matches_oracle(fv):
+def test_time_step_matches_oracle(fv, P):
     grid = (4, 5, 3)
     n = int(np.prod(grid))
-    q, off, sz = fvtest.random_batch(n, P, 3, 74)
+    # the FP32 layout (offsets on 16-byte boundaries), the oracle on the same
+    # FP32 values widened
+    q32, off, sz = fvtest.random_batch(n, P, 3, 74, np.float32)
+    q = q32.astype(np.float64)
     nbr = inputs.grid_neighbours(grid)
     toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
     dx, cfl = 1.0 / (grid[0] * P), 0.4
-    b = batch(fv, True, tsz, n)
-    x = time_steps(fv, b, q.astype(np.float32), toff, tsz, tnbr, dx, cfl, 1)
+    b = batch(fv, True, tsz, n, 0, P)
+    x = time_steps(fv, b, q32, toff, tsz, tnbr, dx, cfl, 1)
     assert b.status() == fv.FV_OK and fv.fv_batch_pairs_launches(b.h) == 1
     ref, dt = oracle.step(q, off, sz, nbr, 3, dx, cfl)
     assert fv.fv_read_dt(b.h) == pytest.approx(dt, rel=1e-6)
@@ -143,7 +149,7 @@ def test_time_step_matches_oracle(fv):
     b.close()
 
 
-def test_uneven_batch_uses_it_for_the_5_cubed_class_only(fv):
+def test_uneven_batch_uses_them_for_the_3_and_5_cubed_classes(fv):
     n = 900
     sizes = inputs.uneven_sizes(n, seed=75)
     q, off, sz = inputs.random_batch(n, sizes, 3, seed=75, dtype=np.float32)
@@ -156,19 +162,19 @@ def test_uneven_batch_uses_it_for_the_5_cubed_class_only(fv):
     b = batch(fv, True, tsz, n, 2, p=7)
     got = time_steps(fv, b, q, toff, tsz, tnbr, dx, cfl, steps).cpu().numpy()
     assert b.status() == fv.FV_OK
-    assert fv.fv_batch_pairs_launches(b.h) == steps
+    assert fv.fv_batch_pairs_launches(b.h) == 2 * steps  # 3^3 and 5^3, not 7^3
     mask = fvtest.interior_mask(off, sz, 3, 5, len(q))
     assert np.array_equal(got[mask], ref[mask])
     b.close()
 
 
-def test_nonphysical_state_is_reported(fv):
+def test_nonphysical_state_is_reported(fv, P):
     n = 8
     q, off, sz = fvtest.random_batch(n, P, 3, 76, np.float32)
     ne = P + 2
     q[off[3] + (2 + ne * (2 + ne * 2)) * 5] = -1.0  # negative density, interior cell
     toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
-    b = batch(fv, True, tsz, n)
+    b = batch(fv, True, tsz, n, 0, P)
     x = fvtest.to_dev(q)
     b.update(x, x.clone(), toff, tsz, 0.01, 0.001)
     assert fv.fv_batch_pairs_launches(b.h) == 1
@@ -176,7 +182,7 @@ def test_nonphysical_state_is_reported(fv):
     b.close()
 
 
-def test_graph_of_steps_on_a_fresh_handle(fv):
+def test_graph_of_steps_on_a_fresh_handle(fv, P):
     """fv_run_steps captured into a CUDA graph on a fresh, planned handle (the
     kernel's first launch happens inside the capture) equals the general
     kernel's eager steps bitwise."""
@@ -187,7 +193,7 @@ def test_graph_of_steps_on_a_fresh_handle(fv):
     nbr = inputs.grid_neighbours(grid)
     toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
     dx, cfl, steps = 1.0 / (grid[0] * P), 0.4, 4
-    b0 = batch(fv, False, tsz, n)
+    b0 = batch(fv, False, tsz, n, 0, P)
     ref = time_steps(fv, b0, q, toff, tsz, tnbr, dx, cfl, steps).cpu().numpy()
     b0.close()
     stream = torch.cuda.Stream()
@@ -204,7 +210,7 @@ def test_graph_of_steps_on_a_fresh_handle(fv):
     b.close()
 
 
-def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv):
+def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv, P):
     """A patch whose box runs past the declared buffer length (n_elems): both
     kernels report FV_ERR_BAD_PATCH, leave it untouched and update the rest
     identically."""
@@ -215,7 +221,7 @@ def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv):
     n_elems = int(off[-1]) + 10  # the last patch does not fit
     res = []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n)
+        b = batch(fv, planned, tsz, n, 0, P)
         x = fvtest.to_dev(q)
         y = x.clone()
         b.update(x, y, toff, tsz, 0.01, 0.001, n_elems=n_elems)

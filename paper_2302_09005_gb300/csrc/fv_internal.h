@@ -161,6 +161,13 @@ bool rows2d_eligible(const fv_batch* h, const UpdateLaunch& l);
 int rows2d_patches_per_cta();
 cudaError_t launch_rows2d(const fv_batch* h, const UpdateLaunch& l, int grid);
 cudaError_t rows2d_occupancy(int mode, int* blocks_per_sm);
+// The plane-sweep kernel for launches of 3D patches of size p = 5
+// (fv_march3d.cu: a lane per row of cells, four patches per warp, the patch
+// advanced plane by plane along z; march3d_patches_per_cta() patches per CTA
+// and iteration); pairs_class / pairs_eligible decide where it runs.
+int march3d_patches_per_cta();
+cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid);
+cudaError_t march3d_occupancy(int mode, int* blocks_per_sm);
 // The same for launches of 3D patches of size p = 3 (fv_lines3d.cu: a lane
 // per line of cells along x, one patch per warp, lines3d_patches_per_cta()
 // patches per CTA and iteration).

@@ -25,6 +25,7 @@
 //  * update: the sum x then y then z, one FMA with -dt / (2 dx), the new state
 //    stored and, in a time step, converted for the next CFL maximum.
 #include "fv_step.cuh"
+#include "fv_cell3.cuh"
 
 // Resident CTAs of 128 threads per SM the register allocation is sized for.
 #ifndef FV_LINES3D_MINBLOCKS
@@ -37,54 +38,6 @@ namespace {
 constexpr int kL3NT = 128;  // threads per CTA: four warps, a patch each
 constexpr int kL3P = 3;     // the patch size
 constexpr int kL3W = kL3P + 2;  // lines per axis of the lane grid
-
-__device__ __forceinline__ unsigned umax_l(unsigned a, unsigned b) { return a > b ? a : b; }
-__device__ __forceinline__ unsigned wbits_l(float u, float c) {
-  return __float_as_uint(add_rn(fabsf(u), c));
-}
-constexpr unsigned kMagL = 0x7FFFFFFFu;
-constexpr unsigned kBadL = 0x7F7FFFFFu;  // bits(x) - 1 < this <=> 0 < x < inf
-
-// State and primitives of one cell: rho, j_x, j_y, j_z, E; u, p, c, E + p.
-struct LCell {
-  float q[5];
-  float u[3], p, c, e;
-};
-
-// Primitives (Eq. 2), the operations of primitives<float, 3>() of the general
-// kernel; `need` keeps non-cells out of the positivity check.
-__device__ __forceinline__ void lprims(LCell& x, float gm1, float gamma, bool need,
-                                       unsigned& chk) {
-  const float inv = recip(x.q[0]);
-  x.u[0] = mul_rn(x.q[1], inv);
-  x.u[1] = mul_rn(x.q[2], inv);
-  x.u[2] = mul_rn(x.q[3], inv);
-  float jj = mul_rn(x.q[1], x.u[0]);
-  jj = fmaf(x.q[2], x.u[1], jj);
-  jj = fmaf(x.q[3], x.u[2], jj);
-  x.p = mul_rn(gm1, fmaf(-0.5f, jj, x.q[4]));
-  x.e = add_rn(x.q[4], x.p);
-  x.c = sqrt_t(mul_rn(mul_rn(gamma, x.p), inv));
-  const unsigned m = need ? ~0u : 0u;
-  chk = umax_l(chk, (__float_as_uint(x.q[0]) - 1u) & m);
-  chk = umax_l(chk, (__float_as_uint(x.p) - 1u) & m);
-}
-
-// G = 2F of one face along k (Eq. 4, 5) in the general kernel's operation
-// order, g[v] for the unknowns v; returns the bits of a.
-template <int K>
-__device__ __forceinline__ unsigned lflux(const LCell& L, const LCell& R, float (&g)[5]) {
-  const unsigned ab = umax_l(wbits_l(L.u[K], L.c), wbits_l(R.u[K], R.c));
-  const float am = __uint_as_float(ab);
-  const float sL = add_rn(L.u[K], am), sR = sub_rn(R.u[K], am), ps = add_rn(L.p, R.p);
-  g[0] = fmaf(L.q[0], sL, mul_rn(R.q[0], sR));
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-    g[1 + m] = m == K ? fmaf(L.q[1 + m], sL, fmaf(R.q[1 + m], sR, ps))
-                      : fmaf(L.q[1 + m], sL, mul_rn(R.q[1 + m], sR));
-  g[4] = fmaf(am, sub_rn(L.q[4], R.q[4]), fmaf(L.e, L.u[K], mul_rn(R.e, R.u[K])));
-  return ab;
-}
 
 __device__ __forceinline__ void lload(LCell& x, const float* src, int negc) {
 #pragma unroll

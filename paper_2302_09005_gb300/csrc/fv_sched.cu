@@ -47,29 +47,31 @@ static int grid_for(const fv_batch* h, int64_t count, int bps) {
 }
 
 // A launch of patches of one size: the FP32 kernel built for that size (3D
-// p = 5 or p = 3, 2D p = 5) where it applies.
+// p = 5: the plane sweep, p = 3: a lane per line; 2D p = 5: a lane per row)
+// where it applies.
 static cudaError_t launch_one_size(fv_batch* h, const UpdateLaunch& l, int64_t count,
                                    bool* done) {
   *done = false;
-  const bool two = rows2d_eligible(h, l);
-  const bool lines = !two && lines3d_eligible(h, l);
-  if (!two && !lines && !pairs_eligible(h, l)) return cudaSuccess;
+  const int kind = rows2d_eligible(h, l) ? 1 : lines3d_eligible(h, l) ? 2 : pairs_eligible(h, l) ? 3 : 0;
+  if (kind == 0) return cudaSuccess;
   const int f = step_mode(l);
-  int& bps = lines ? h->occ_lines[f] : h->occ_pairs[f];  // a handle has one d
+  int& bps = kind == 2 ? h->occ_lines[f] : h->occ_pairs[f];  // a handle has one d
   if (bps == 0) {
-    cudaError_t e = two     ? rows2d_occupancy(f, &bps)
-                    : lines ? lines3d_occupancy(f, &bps)
-                            : pairs_occupancy(f, &bps);
+    cudaError_t e = kind == 1   ? rows2d_occupancy(f, &bps)
+                    : kind == 2 ? lines3d_occupancy(f, &bps)
+                                : march3d_occupancy(f, &bps);
     if (e != cudaSuccess) return e;
   }
   *done = true;
   ++h->pairs_launches;
-  if (two || lines) {  // a CTA takes several patches at a time
-    const int per = two ? rows2d_patches_per_cta() : lines3d_patches_per_cta();
-    return two ? launch_rows2d(h, l, grid_for(h, (count + per - 1) / per, bps))
-               : launch_lines3d(h, l, grid_for(h, (count + per - 1) / per, bps));
-  }
-  return launch_pairs(h, l, grid_for(h, count, bps));
+  // a CTA takes several patches at a time
+  const int per = kind == 1   ? rows2d_patches_per_cta()
+                  : kind == 2 ? lines3d_patches_per_cta()
+                              : march3d_patches_per_cta();
+  const int grid = grid_for(h, (count + per - 1) / per, bps);
+  return kind == 1   ? launch_rows2d(h, l, grid)
+         : kind == 2 ? launch_lines3d(h, l, grid)
+                     : launch_march3d(h, l, grid);
 }
 
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {

@@ -191,7 +191,7 @@ __device__ __forceinline__ void sread(float (&q)[5], const float* p, unsigned nm
 }
 constexpr unsigned kSign = 0x80000000u;
 
-template <int P, bool STEP>
+template <int P, bool STEP, bool LAM>
 __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(StepParams<float> a) {
   using G = MGeom<P>;
   constexpr int S = 5, NE = P + 2;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
         lprims(L, gm1, gam, false, chk);
         float g[S];
         const unsigned ab = lflux<2>(L, cc[i], g);
-        lmax = umax_l(lmax, ab & ((act && inner) ? kMagL : 0u));
+        lmax = umax_l(lmax, ab & ((LAM && act && inner) ? kMagL : 0u));
         if (z >= 2) {
           float qn[S];
 #pragma unroll
@@ -312,32 +312,40 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
             qn[v] = fmaf(mhr, acc, pq[i][v]);
             if (inner) outb[ri * P * S + i * S + v] = qn[v];
           }
+          if constexpr (STEP) {
+            // primitives and wave speeds of the new state (next CFL maximum)
+            LCell w;
+#pragma unroll
+            for (int v = 0; v < S; ++v) w.q[v] = qn[v];
+            lprims(w, gm1, gam, act && inner, chk);
+            if (act && inner) {
+#pragma unroll
+              for (int k = 0; k < 3; ++k) lam_next = umax_l(lam_next, wbits_l(w.u[k], w.c) & kMagL);
+            }
+          }
         }
 #pragma unroll
         for (int v = 0; v < S; ++v) pglo[i][v] = g[v];
       }
       if constexpr (STEP) {
-        if (z >= 2 && act && inner) {
-          // primitives and wave speeds of plane z - 1's new state (next CFL
-          // maximum), read back from the output stage
+        if (z >= 2 && act && inner && a.prim_out != nullptr) {
+          // the primitives of the new state to the carry block: converted
+          // again from the output stage (the same operations, so the same
+          // values), which keeps them out of the registers of the loop above
 #pragma unroll
           for (int i = 0; i < P; ++i) {
             LCell w;
 #pragma unroll
             for (int v = 0; v < S; ++v) w.q[v] = outb[ri * P * S + i * S + v];
-            lprims(w, gm1, gam, true, chk);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) lam_next = umax_l(lam_next, wbits_l(w.u[k], w.c) & kMagL);
-            if (a.prim_out != nullptr) {
-              constexpr int NI = P * P * P;
-              float* po = a.prim_out + pid * a.prim_stride + i + P * (ri + P * (z - 2));
-              po[0] = w.u[0];
-              po[NI] = w.u[1];
-              po[2 * NI] = w.u[2];
-              po[3 * NI] = w.p;
-              po[4 * NI] = w.c;
-              po[5 * NI] = w.e;
-            }
+            lprims(w, gm1, gam, false, chk);
+            constexpr int NI = P * P * P;
+            float* po = a.prim_out + pid * a.prim_stride + i + P * (ri + P * (z - 2));
+            po[0] = w.u[0];
+            po[NI] = w.u[1];
+            po[2 * NI] = w.u[2];
+            po[3 * NI] = w.p;
+            po[4 * NI] = w.c;
+            po[5 * NI] = w.e;
           }
         }
       }
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
       float gp[S];
       {
         const unsigned ab = lflux<0>(h0, cc[0], gp);
-        lmax = umax_l(lmax, ab & ((act && inner) ? kMagL : 0u));
+        lmax = umax_l(lmax, ab & ((LAM && act && inner) ? kMagL : 0u));
       }
 #pragma unroll
       for (int i = 0; i < P; ++i) {
@@ -385,7 +393,7 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
         {
           float g[S];
           const unsigned ab = lflux<0>(cc[i], i + 1 < P ? cc[i + 1] : h1, g);
-          lmax = umax_l(lmax, ab & ((act && inner) ? kMagL : 0u));
+          lmax = umax_l(lmax, ab & ((LAM && act && inner) ? kMagL : 0u));
 #pragma unroll
           for (int v = 0; v < S; ++v) {
             dg[v] = sub_rn(g[v], gp[v]);
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
         up.e = __shfl_down_sync(0xFFFFFFFFu, cc[i].e, 1);
         float g[S];
         const unsigned ab = lflux<1>(cc[i], up, g);
-        lmax = umax_l(lmax, ab & ((act && r <= P) ? kMagL : 0u));
+        lmax = umax_l(lmax, ab & ((LAM && act && r <= P) ? kMagL : 0u));
 #pragma unroll
         for (int v = 0; v < S; ++v) {
           const float below = __shfl_up_sync(0xFFFFFFFFu, g[v], 1);
@@ -412,7 +420,7 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
         }
       }
     }
-    if (a.lam_patch != nullptr) {  // the patch's maximum over its eight lanes
+    if constexpr (LAM) {  // the patch's maximum over its eight lanes
       lmax = umax_l(lmax, __shfl_xor_sync(0xFFFFFFFFu, lmax, 4));
       lmax = umax_l(lmax, __shfl_xor_sync(0xFFFFFFFFu, lmax, 2));
       lmax = umax_l(lmax, __shfl_xor_sync(0xFFFFFFFFu, lmax, 1));
@@ -428,24 +436,24 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
   }
 }
 
-template <int P, bool STEP>
+template <int P, bool STEP, bool LAM>
 cudaError_t march3d_smem_attr() {
   static int set_bytes[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && set_bytes[dev] >= MGeom<P>::BYTES) return cudaSuccess;
-  e = cudaFuncSetAttribute(march3d_kernel<P, STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(march3d_kernel<P, STEP, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            MGeom<P>::BYTES);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(march3d_kernel<P, STEP>,
+    e = cudaFuncSetAttribute(march3d_kernel<P, STEP, LAM>,
                              cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess && dev >= 0 && dev < 64) set_bytes[dev] = MGeom<P>::BYTES;
   return e;
 }
 
-template <int P, bool STEP>
+template <int P, bool STEP, bool LAM>
 cudaError_t launch_march3d_t(const fv_batch* h, const UpdateLaunch& l, int grid) {
   StepParams<float> a{};
   a.in = static_cast<const float*>(l.in);
@@ -476,17 +484,17 @@ cudaError_t launch_march3d_t(const fv_batch* h, const UpdateLaunch& l, int grid)
   a.mzero = -0.0f;
   a.prim_out = static_cast<float*>(l.prim_out);
   a.prim_stride = l.prim_stride;
-  cudaError_t e = march3d_smem_attr<P, STEP>();
+  cudaError_t e = march3d_smem_attr<P, STEP, LAM>();
   if (e != cudaSuccess) return e;
-  march3d_kernel<P, STEP><<<grid, kMNT, MGeom<P>::BYTES, h->stream>>>(a);
+  march3d_kernel<P, STEP, LAM><<<grid, kMNT, MGeom<P>::BYTES, h->stream>>>(a);
   return cudaGetLastError();
 }
 
 template <int P, bool STEP>
-cudaError_t occupancy_march3d_t(int* bps) {
-  cudaError_t e = march3d_smem_attr<P, STEP>();
+cudaError_t occupancy_march3d_t(int* bps) {  // the kernel with per-patch maxima
+  cudaError_t e = march3d_smem_attr<P, STEP, true>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, march3d_kernel<P, STEP>, kMNT,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, march3d_kernel<P, STEP, true>, kMNT,
                                                        MGeom<P>::BYTES);
 }
 
@@ -495,8 +503,12 @@ cudaError_t occupancy_march3d_t(int* bps) {
 int march3d_patches_per_cta() { return kMGroups; }
 
 cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid) {
-  return step_mode(l) == kModeStep ? launch_march3d_t<5, true>(h, l, grid)
-                                   : launch_march3d_t<5, false>(h, l, grid);
+  const bool step = step_mode(l) == kModeStep, lam = l.lam_patch != nullptr;
+  if (step)
+    return lam ? launch_march3d_t<5, true, true>(h, l, grid)
+               : launch_march3d_t<5, true, false>(h, l, grid);
+  return lam ? launch_march3d_t<5, false, true>(h, l, grid)
+             : launch_march3d_t<5, false, false>(h, l, grid);
 }
 
 cudaError_t march3d_occupancy(int mode, int* bps) {

@@ -427,7 +427,7 @@ def run_ours(args, ws, rank, local):
            "unit": "GB/s", "frac": alg_bytes / (kern_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
            "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src}
     if roof is None:
-        kname = ((f"pairs{'2d' if d == 2 else ''}_kernel<5,step>"
+        kname = ((("rows2d_kernel<5,step>" if d == 2 else "march3d_kernel<5,step>")
                   if fv.fv_batch_pairs_launches(b.h) > 0 else
                   f"step_kernel<float,{d},gather,fused>"))
         roof = {"bound": "hbm", "kernel": kname, **hbm,
@@ -762,7 +762,7 @@ def precision_variant(args, N: int = 4095, p: int = 5, steps: int = 100):
                      "conserved_drift_rel_to_l1": (np.abs(a1 - a0) / l1_scale.cpu().numpy()
                                                    ).tolist()}
         if prec == "f32":
-            out[prec]["pairs_kernel_used"] = fv.fv_batch_pairs_launches(b.h) > 0
+            out[prec]["one_size_kernel_used"] = fv.fv_batch_pairs_launches(b.h) > 0
             # HBM roofline of the FP32 step (one rows2d launch per step): read
             # the interior and face-halo cells, write the interior
             alg = n * ((p * p + 4 * p) * 4 + p * p * 4) * 4
@@ -1028,7 +1028,7 @@ def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, s
     ms_general = timed_steps()
     fv.fv_batch_plan(b.h, tsz, n)
     ms = timed_steps()
-    pairs_used = fv.fv_batch_pairs_launches(b.h) > 0
+    one_size_used = fv.fv_batch_pairs_launches(b.h) > 0
     # the same with the primitive carry
     prims = [torch.empty(n * b.prim_stride(), dtype=torch.float32, device="cuda")
              for _ in range(2)]
@@ -1051,8 +1051,9 @@ def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, s
     b.close()
     return {"value": n * p ** d / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "what": "fv_time_step in FP32 (no primitive carry), the batch planned: the "
-                    "kernel for one 3D patch size (pairs_kernel<5>)",
-            "pairs_kernel_used": pairs_used,
+                    "kernel for 5^3 patches (march3d_kernel<5>: a lane per row, the patch "
+                    "swept plane by plane)",
+            "one_size_kernel_used": one_size_used,
             "general_kernel": {"value": n * p ** d / (ms_general / 1e3),
                                "ms_per_step": ms_general,
                                "what": "the same step on the general kernel (no plan)"},
@@ -1062,7 +1063,7 @@ def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, s
             "status_ok": ok,
             "rel_l1_vs_fp64_one_step": rel_l1, "max_rel_err_vs_fp64_one_step":
                 max_rel.tolist(),
-            "roofline": {"bound": "hbm", "kernel": "pairs_kernel<5,step>",
+            "roofline": {"bound": "hbm", "kernel": "march3d_kernel<5,step>",
                          "achieved": alg / (ms / 1e3) / 1e9,
                          "traffic": _traffic("euler3d_fp32_262144x5"),
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",

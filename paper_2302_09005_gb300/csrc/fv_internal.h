@@ -51,9 +51,9 @@ struct fv_batch {
   int cls_nt[64] = {0};                      // CTA size of the size-class launches (0: 128)
   int cls_only = -1;                         // autotuner: launch only this class (-1: all)
   int cls_real[64] = {0};                    // class c holds one valid size (not the rejects)
-  int occ_pairs[3] = {0, 0, 0};              // CTAs per SM of the FP32 pairs kernel, by mode
+  int occ_one[3] = {0, 0, 0};                // CTAs per SM of the FP32 2D or 3D 5^p kernel, by mode
   int occ_lines[3] = {0, 0, 0};              // CTAs per SM of the FP32 3^3 lines kernel, by mode
-  int64_t pairs_launches = 0;                // launches that used the FP32 pairs kernel
+  int64_t pairs_launches = 0;                // launches that used an FP32 one-size kernel
   void* host_stage = nullptr;                // fv_patch_update_host: streams, staging buffers
   int smem_optin = 0;                        // opt-in shared memory per CTA
   long long wait_limit = FV_WAIT_LIMIT;      // step kernel: cycles of a copy wait
@@ -147,12 +147,6 @@ template <typename T, int NT>
 cudaError_t launch_step_nt(const fv_batch* h, const UpdateLaunch& l, int grid);
 template <typename T, int NT>
 cudaError_t occupancy_nt(int d, int mode, int pmax, int nstage, int* bps);
-// The FP32 kernel for launches of one 3D patch size (fv_pairs.cu): whether a
-// size class / a launch can use it, its launch and its occupancy.
-bool pairs_class(const fv_batch* h, int p);
-bool pairs_eligible(const fv_batch* h, const UpdateLaunch& l);
-cudaError_t launch_pairs(const fv_batch* h, const UpdateLaunch& l, int grid);
-cudaError_t pairs_occupancy(int mode, int* blocks_per_sm);
 // The same for launches of one 2D patch size, p = 5 (fv_rows2d.cu: a lane
 // per row of cells, four patches per warp, rows2d_patches_per_cta() patches
 // per CTA and iteration).
@@ -161,10 +155,12 @@ bool rows2d_eligible(const fv_batch* h, const UpdateLaunch& l);
 int rows2d_patches_per_cta();
 cudaError_t launch_rows2d(const fv_batch* h, const UpdateLaunch& l, int grid);
 cudaError_t rows2d_occupancy(int mode, int* blocks_per_sm);
-// The plane-sweep kernel for launches of 3D patches of size p = 5
-// (fv_march3d.cu: a lane per row of cells, four patches per warp, the patch
-// advanced plane by plane along z; march3d_patches_per_cta() patches per CTA
-// and iteration); pairs_class / pairs_eligible decide where it runs.
+// The FP32 kernel for launches of 3D patches of size p = 5 (fv_march3d.cu: a
+// lane per row of cells, four patches per warp, each patch advanced plane by
+// plane along z; march3d_patches_per_cta() patches per CTA and iteration):
+// whether a size class / a launch can use it, its launch and its occupancy.
+bool march3d_class(const fv_batch* h, int p);
+bool march3d_eligible(const fv_batch* h, const UpdateLaunch& l);
 int march3d_patches_per_cta();
 cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid);
 cudaError_t march3d_occupancy(int mode, int* blocks_per_sm);

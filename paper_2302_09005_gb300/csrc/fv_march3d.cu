@@ -504,6 +504,16 @@ cudaError_t occupancy_march3d_t(int* bps) {  // the kernel with per-patch maxima
 
 }  // namespace
 
+bool march3d_class(const fv_batch* h, int p) {
+  return h->prec == FV_FP32 && h->d == 3 && h->s == 5 && p == 5;
+}
+
+bool march3d_eligible(const fv_batch* h, const UpdateLaunch& l) {
+  const int mode = step_mode(l);
+  return march3d_class(h, l.uniform_p) && mode != kModePrim && l.corr == nullptr &&
+         l.dx_patch == nullptr && !l.local_cfl && (mode == kModeStep || l.prim_out == nullptr);
+}
+
 int march3d_patches_per_cta() { return kMGroups; }
 
 cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid) {

@@ -52,10 +52,13 @@ static int grid_for(const fv_batch* h, int64_t count, int bps) {
 static cudaError_t launch_one_size(fv_batch* h, const UpdateLaunch& l, int64_t count,
                                    bool* done) {
   *done = false;
-  const int kind = rows2d_eligible(h, l) ? 1 : lines3d_eligible(h, l) ? 2 : pairs_eligible(h, l) ? 3 : 0;
+  const int kind = rows2d_eligible(h, l)    ? 1
+                   : lines3d_eligible(h, l) ? 2
+                   : march3d_eligible(h, l) ? 3
+                                            : 0;
   if (kind == 0) return cudaSuccess;
   const int f = step_mode(l);
-  int& bps = kind == 2 ? h->occ_lines[f] : h->occ_pairs[f];  // a handle has one d
+  int& bps = kind == 2 ? h->occ_lines[f] : h->occ_one[f];  // a handle has one d
   if (bps == 0) {
     cudaError_t e = kind == 1   ? rows2d_occupancy(f, &bps)
                     : kind == 2 ? lines3d_occupancy(f, &bps)
@@ -295,7 +298,7 @@ fv_status fv_batch_autotune(fv_batch* h, const void* in, void* scratch_out, cons
   // 1. the CTA size of each size class (one-class launches)
   h->sched = FV_SCHED_CLASSES;
   for (int c = 0; c < h->ncls && st == FV_OK; ++c) {
-    if (h->cls_real[c] && (fv::pairs_class(h, h->cls_p[c]) || fv::rows2d_class(h, h->cls_p[c]) ||
+    if (h->cls_real[c] && (fv::march3d_class(h, h->cls_p[c]) || fv::rows2d_class(h, h->cls_p[c]) ||
                              fv::lines3d_class(h, h->cls_p[c])))
       continue;  // kernels with a fixed CTA size
     const int pi = h->cls_p[c] < 64 ? h->cls_p[c] : 63;

@@ -1,4 +1,4 @@
-"""The FP32 kernels for launches of one 3D patch size (csrc/fv_pairs.cu for
+"""The FP32 kernels for launches of one 3D patch size (csrc/fv_march3d.cu for
 5^3 patches, csrc/fv_lines3d.cu for 3^3): each runs (launch counter) for
 planned batches under every schedule and for its class of uneven batches,
 and its results are bitwise those of the general kernel -- time steps on periodic, outflow and wall meshes (with
@@ -15,7 +15,7 @@ from tests import fvtest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=[5, 3], ids=["pairs5", "lines3"])
+@pytest.fixture(params=[5, 3], ids=["march5", "lines3"])
 def P(request):
     return request.param
 

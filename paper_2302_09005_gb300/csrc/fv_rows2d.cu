@@ -6,16 +6,18 @@
 //
 // A warp advances four patches at a time, eight lanes each: lane r of a group
 // holds row y = r of its patch box (r = 0 and r = p + 1 the face-halo rows,
-// lane 7 idle).  Everything stays in registers; no shared memory, no block
-// barrier:
+// lane 7 idle).  The arithmetic stays in registers, with no block barrier:
 //
-//  * loads: an interior row reads its p cells with 16-byte loads, and its two
-//    x-halo cells from their sources (the own halo layer in update mode; in a
-//    time step the neighbour's interior layer next to the face, a wall's
-//    mirror or the outflow copy); a face-halo row reads the p cells of its
-//    source row.  The patch box is read once, in whole rows; where the rows
-//    come from (patch, neighbours) is resolved one iteration ahead;
-//  * primitives of every cell of the row (Eq. 2);
+//  * staging: each group copies its next patch into shared memory while it
+//    computes the current one (cp.async, one 16-byte cell per copy, the eight
+//    lanes taking consecutive cells so the copies coalesce): the rows 1 .. p
+//    of the own box with their x-halo cells as one contiguous span, the two
+//    y-halo rows from the y-face sources and, in a time step, the 2p x-halo
+//    cells from the x-face sources (the neighbour's interior layer next to the
+//    face, a wall's mirror, the outflow copy; the own halo layer in update
+//    mode).  Where a patch's data come from is resolved two patches ahead and
+//    kept in a per-group record;
+//  * primitives of every cell of the lane's row (Eq. 2);
 //  * x faces: an interior row walks its p + 1 faces left to right and keeps
 //    each cell's x flux difference;
 //  * y faces: lane r takes the face between rows r and r + 1 of every column,
@@ -48,6 +50,7 @@ constexpr unsigned kMag = 0x7FFFFFFFu;
 // positivity of rho and p accumulated as max(bits - 1): 0 < x < inf <=>
 // bits(x) - 1 < 0x7F7FFFFF
 constexpr unsigned kBad = 0x7F7FFFFFu;
+constexpr unsigned kSignR = 0x80000000u;  // the sign bit: a wall's mirrored momentum
 
 // State and primitives of one cell: rho, j_x, j_y, E; u_x, u_y, p, c, E + p.
 struct RCell {
@@ -87,23 +90,116 @@ __device__ __forceinline__ unsigned rflux(const RCell& L, const RCell& R, float 
   return ab;
 }
 
-__device__ __forceinline__ void ld_cell(RCell& x, const float* src, int negc) {
-  const float4 v = __ldg(reinterpret_cast<const float4*>(src));
-  x.q[0] = v.x;
-  x.q[1] = negc == 1 ? neg_t(v.y) : v.y;
-  x.q[2] = negc == 2 ? neg_t(v.z) : v.z;
-  x.q[3] = v.w;
+
+// Shared-memory staging (floats) of patch size P, per group and stage: the
+// rows 1 .. P of the own box with their x-halo cells (A, one contiguous
+// span), the 2P x-halo cells from the x-face sources (X, time steps) and the
+// two y-halo rows from the y-face sources (Y).  Cells are 16 bytes and patch
+// offsets multiples of 4, so every cell is one aligned 16-byte chunk.
+template <int P>
+struct RGeom {
+  static constexpr int S = 4, NE = P + 2;
+  static constexpr int OA = 0, OX = OA + P * NE * S, OY = OX + 2 * P * S;
+  static constexpr int SLOT = OY + 2 * P * S;
+  static constexpr int REC = 16;                    // floats per patch record
+  static constexpr int GROUP = 2 * SLOT + 3 * REC;  // two stages, three records
+  static constexpr int BYTES = (kRowsNT / 32) * kRowsPerWarp * GROUP * 4;
+  static_assert(SLOT % 4 == 0 && GROUP % 4 == 0, "16-byte alignment of the stages");
+};
+
+// Where a group's patch comes from (one record per patch, a ring of three:
+// the patch being computed, the one whose copies are in flight, the one
+// resolved last): the four face sources (patch offset, source layer, wall
+// flag) and the patch itself.
+struct RRec {
+  long long fo[4];
+  int fck[4];  // source layer | wall << 8
+  long long off;
+  int pid, act;
+};
+static_assert(sizeof(RRec) <= 16 * 4, "record size");
+
+struct RNext {
+  long long fo, off;
+  int fck, pid, act;
+};
+
+// The patch at position `pos` and the source of face r of it (lanes r = 0 ..
+// 3 of the group; Algorithm 1 step 5: where the face-halo cells come from).
+template <int P, bool STEP>
+__device__ __forceinline__ RNext resolve_patch2d(const StepParams<float>& a, int64_t pos, int r) {
+  constexpr int S = 4, NE = P + 2;
+  RNext n{0, 0, 0, 0, 0};
+  if (pos < a.i_end) {
+    const int64_t pid = a.order != nullptr ? (int64_t)a.order[pos] : pos;
+    const int pj = a.sizes[pid];
+    const int64_t off = a.off[pid];
+    const bool act = pj == P && off >= 0 && (off % 4) == 0 &&
+                     (a.n_elems <= 0 || off + (int64_t)NE * NE * S <= a.n_elems);
+    if (!act && r == 0) atomicOr(a.status, ST_BAD_PATCH);  // other size or bad layout
+    n.pid = (int)pid;
+    n.off = off;
+    n.act = act ? 1 : 0;
+    if (act && r < 4) {
+      const FaceSrc fs = face_source<float, 2, STEP>(a, pid, P, off, r);
+      n.fo = fs.off;
+      n.fck = fs.ck | (fs.neg << 8);
+    }
+  }
+  return n;
 }
 
-// Where one lane's row comes from: the patch, and the sources of its halo
-// cells (an interior row: faces -x, +x; a face-halo row: its face).
-struct RowMeta {
-  int64_t pid, off;
-  long long s0, s1;  // source patch offsets
-  int ck0, ck1;      // source layers along the face normal
-  int neg0, neg1;    // wall: the normal momentum mirrored
-  bool act;          // the patch is valid
-};
+__device__ __forceinline__ void write_rec2d(RRec* rec, const RNext& n, int r) {
+  if (r < 4) {
+    rec->fo[r] = n.fo;
+    rec->fck[r] = n.fck;
+  } else if (r == 4) {
+    rec->off = n.off;
+    rec->pid = n.pid;
+    rec->act = n.act;
+  }
+}
+
+__device__ __forceinline__ void cp_cell(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+
+// Issues the copies of the group's patch into `slot`, 16-byte cells, lane r
+// of the group taking cells r, r + 8, ... of each part, so the eight lanes
+// read consecutive cells.
+template <int P, bool STEP>
+__device__ __forceinline__ void issue_patch2d(const StepParams<float>& a, const RRec* m,
+                                              float* slot, int r) {
+  using G = RGeom<P>;
+  constexpr int S = 4, NE = P + 2;
+  if (!m->act) return;
+  const float* sa = a.in + m->off + NE * S;  // cell (0, 1)
+#pragma unroll
+  for (int k = r; k < P * NE; k += kRowsGroup) cp_cell(slot + G::OA + S * k, sa + S * k);
+#pragma unroll
+  for (int c = r; c < 2 * P; c += kRowsGroup) {
+    const int s = c >= P ? 1 : 0, x = c - s * P;
+    const long long so = m->fo[2 + s] + (long long)(1 + x + NE * (m->fck[2 + s] & 0xFF)) * S;
+    cp_cell(slot + G::OY + S * c, a.in + so);
+  }
+  if constexpr (STEP) {
+#pragma unroll
+    for (int c = r; c < 2 * P; c += kRowsGroup) {
+      const int s = c >= P ? 1 : 0, row = c - s * P + 1;
+      const long long so = m->fo[s] + (long long)((m->fck[s] & 0xFF) + NE * row) * S;
+      cp_cell(slot + G::OX + S * c, a.in + so);
+    }
+  }
+}
+
+__device__ __forceinline__ void st_cell(RCell& x, const float* src, unsigned nm1, unsigned nm2) {
+  const float4 v = *reinterpret_cast<const float4*>(src);
+  x.q[0] = v.x;
+  x.q[1] = __uint_as_float(__float_as_uint(v.y) ^ nm1);
+  x.q[2] = __uint_as_float(__float_as_uint(v.z) ^ nm2);
+  x.q[3] = v.w;
+}
 
 __device__ __forceinline__ float shfl_dn(float v) { return __shfl_down_sync(0xFFFFFFFFu, v, 1); }
 __device__ __forceinline__ float shfl_up(float v) { return __shfl_up_sync(0xFFFFFFFFu, v, 1); }
@@ -132,46 +228,37 @@ __global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(St
   const float gm1 = a.gm1, gam = a.gamma;
   unsigned chk = 0u, lam_next = 0u;
 
-  // the patch of this lane's group at `base` and the sources of this row
-  // (metadata one iteration ahead, so its chain of dependent loads overlaps
-  // the arithmetic of the current patches)
-  auto row_meta = [&](int64_t base) {
-    RowMeta mt{0, 0, 0, 0, 0, 0, 0, 0, false};
-    const int64_t pos = base + grp;
-    if (pos < a.i_end) {
-      mt.pid = a.order != nullptr ? (int64_t)a.order[pos] : pos;
-      const int pj = a.sizes[mt.pid];
-      mt.off = a.off[mt.pid];
-      mt.act = pj == P && mt.off >= 0 && (mt.off % 4) == 0 &&
-               (a.n_elems <= 0 || mt.off + (int64_t)NE * NE * S <= a.n_elems);
-      if (!mt.act && r == 0) atomicOr(a.status, ST_BAD_PATCH);  // other size or bad layout
-      if (mt.act && row_on) {
-        const FaceSrc fa = face_source<float, 2, STEP>(a, mt.pid, P, mt.off,
-                                                       inner ? 0 : (r == 0 ? 2 : 3));
-        mt.s0 = fa.off;
-        mt.ck0 = fa.ck;
-        mt.neg0 = fa.neg;
-        if (inner) {
-          const FaceSrc fb = face_source<float, 2, STEP>(a, mt.pid, P, mt.off, 1);
-          mt.s1 = fb.off;
-          mt.ck1 = fb.ck;
-          mt.neg1 = fb.neg;
-        }
-      }
-    }
-    return mt;
-  };
-
+  using G = RGeom<P>;
+  extern __shared__ __align__(16) float rsm[];
+  float* const gbase = rsm + ((threadIdx.x >> 5) * kRowsPerWarp + grp) * G::GROUP;
+  RRec* const recs = reinterpret_cast<RRec*>(gbase + 2 * G::SLOT);  // ring of three
   const int64_t stride = nwarps * kRowsPerWarp;
-  RowMeta nxt = row_meta(a.i_begin + warp * kRowsPerWarp);
-  for (int64_t base = a.i_begin + warp * kRowsPerWarp; base < a.i_end; base += stride) {
-    const RowMeta mt = nxt;
-    nxt = row_meta(base + stride);
-    const bool act = mt.act;
-    const int64_t pid = mt.pid, off = mt.off;
+  const int64_t base0 = a.i_begin + warp * kRowsPerWarp;
+  if (base0 >= a.i_end) return;  // the whole warp: no patch
+  // the first two patches resolved, the first one's copies issued
+  write_rec2d(recs, resolve_patch2d<P, STEP>(a, base0 + grp, r), r);
+  write_rec2d(recs + 1, resolve_patch2d<P, STEP>(a, base0 + stride + grp, r), r);
+  __syncwarp();
+  issue_patch2d<P, STEP>(a, recs, gbase, r);
+  cp_async_commit();
+  int rc = 0, rn = 1, rl = 2;  // records: computed, in flight, resolved last
+  int st = 0;                  // stage of the patch being computed
+
+  for (int64_t base = base0; base < a.i_end; base += stride) {
+    // the patch two iterations ahead: its sources resolve during this one
+    const RNext nx = resolve_patch2d<P, STEP>(a, base + 2 * stride + grp, r);
+    cp_async_wait_all();
+    __syncwarp();
+    // the next patch's copies land while this one is computed
+    issue_patch2d<P, STEP>(a, recs + rn, gbase + (st ^ 1) * G::SLOT, r);
+    cp_async_commit();
+    const RRec* m = recs + rc;
+    const float* slot = gbase + st * G::SLOT;
+    const bool act = m->act != 0;
+    const int64_t pid = m->pid, off = m->off;
     const bool on = act && row_on;
 
-    // ---- this row's cells x = 0 .. P + 1 and their primitives -------------
+    // ---- this row's cells x = 0 .. P + 1 from the stage -------------------
     RCell c[NE];
 #pragma unroll
     for (int x = 0; x < NE; ++x) {
@@ -182,15 +269,22 @@ __global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(St
     }
     if (on) {
       if (inner) {
-        const float* row = a.in + off + (int64_t)(r * NE) * S;
+        const float* row = slot + G::OA + (r - 1) * NE * S;
 #pragma unroll
-        for (int x = 1; x <= P; ++x) ld_cell(c[x], row + x * S, 0);
-        ld_cell(c[0], a.in + mt.s0 + (int64_t)(r * NE + mt.ck0) * S, mt.neg0 ? 1 : 0);
-        ld_cell(c[P + 1], a.in + mt.s1 + (int64_t)(r * NE + mt.ck1) * S, mt.neg1 ? 1 : 0);
+        for (int x = 1; x <= P; ++x) st_cell(c[x], row + x * S, 0u, 0u);
+        if constexpr (STEP) {
+          st_cell(c[0], slot + G::OX + (r - 1) * S, (m->fck[0] >> 8) ? kSignR : 0u, 0u);
+          st_cell(c[P + 1], slot + G::OX + (P + r - 1) * S, (m->fck[1] >> 8) ? kSignR : 0u, 0u);
+        } else {  // update mode: the own halo cells, in the span
+          st_cell(c[0], row, 0u, 0u);
+          st_cell(c[P + 1], row + (P + 1) * S, 0u, 0u);
+        }
       } else {
-        const float* row = a.in + mt.s0 + (int64_t)(mt.ck0 * NE) * S;
+        const int sy = r == 0 ? 0 : 1;
+        const float* row = slot + G::OY + sy * P * S;
+        const unsigned nm2 = (m->fck[2 + sy] >> 8) ? kSignR : 0u;
 #pragma unroll
-        for (int x = 1; x <= P; ++x) ld_cell(c[x], row + x * S, mt.neg0 ? 2 : 0);
+        for (int x = 1; x <= P; ++x) st_cell(c[x], row + (x - 1) * S, 0u, nm2);
       }
     }
 #pragma unroll
@@ -274,7 +368,14 @@ __global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(St
         }
       }
     }
+    write_rec2d(recs + rl, nx, r);  // read after the next iteration's warp barrier
+    const int t = rc;
+    rc = rn;
+    rn = rl;
+    rl = t;
+    st ^= 1;
   }
+  cp_async_wait_all();
   if (__any_sync(0xFFFFFFFFu, chk >= kBad) && lane == 0) atomicOr(a.status, ST_NONPHYSICAL);
   if constexpr (STEP) {
     const unsigned long long m = warp_max_u64((unsigned long long)lam_next);
@@ -313,13 +414,14 @@ cudaError_t launch_rows2d_t(const fv_batch* h, const UpdateLaunch& l, int grid) 
   a.mzero = -0.0f;
   a.prim_out = static_cast<float*>(l.prim_out);
   a.prim_stride = l.prim_stride;
-  rows2d_kernel<P, STEP><<<grid, kRowsNT, 0, h->stream>>>(a);
+  rows2d_kernel<P, STEP><<<grid, kRowsNT, RGeom<P>::BYTES, h->stream>>>(a);
   return cudaGetLastError();
 }
 
 template <int P, bool STEP>
 cudaError_t occupancy_rows2d_t(int* bps) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, rows2d_kernel<P, STEP>, kRowsNT, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, rows2d_kernel<P, STEP>, kRowsNT,
+                                                       RGeom<P>::BYTES);
 }
 
 }  // namespace

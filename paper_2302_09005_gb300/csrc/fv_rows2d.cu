@@ -24,19 +24,20 @@
 //    the upper cells' state and primitives by warp shuffle from lane r + 1;
 //  * update: an interior row receives the fluxes of the faces below it from
 //    lane r - 1 (shuffle), adds the y differences to its x differences (x then
-//    y), takes one FMA with -dt / (2 dx), stores its p cells with 16-byte
-//    stores and, in a time step, converts them for the next CFL maximum.
+//    y), takes one FMA with -dt / (2 dx) and, in a time step, converts the new
+//    state for the next CFL maximum; the new state goes to the output through
+//    shared memory, the group's lanes storing consecutive 16-byte cells.
 #include "fv_step.cuh"
 
-// Resident CTAs of 128 threads per SM the register allocation is sized for.
+// Resident one-warp CTAs per SM the register allocation is sized for.
 #ifndef FV_ROWS2D_MINBLOCKS
-#define FV_ROWS2D_MINBLOCKS 4
+#define FV_ROWS2D_MINBLOCKS 16
 #endif
 
 namespace fv {
 namespace {
 
-constexpr int kRowsNT = 128;     // threads per CTA: four independent warps
+constexpr int kRowsNT = 32;      // threads per CTA: one warp (independent CTAs schedule best)
 constexpr int kRowsGroup = 8;    // lanes per patch
 constexpr int kRowsPerWarp = 4;  // patches per warp and iteration
 
@@ -102,7 +103,8 @@ struct RGeom {
   static constexpr int OA = 0, OX = OA + P * NE * S, OY = OX + 2 * P * S;
   static constexpr int SLOT = OY + 2 * P * S;
   static constexpr int REC = 16;                    // floats per patch record
-  static constexpr int GROUP = 2 * SLOT + 3 * REC;  // two stages, three records
+  static constexpr int OUT = 2 * SLOT + 3 * REC;    // the new interior state, P * P cells
+  static constexpr int GROUP = OUT + P * P * S;     // two stages, three records, output
   static constexpr int BYTES = (kRowsNT / 32) * kRowsPerWarp * GROUP * 4;
   static_assert(SLOT % 4 == 0 && GROUP % 4 == 0, "16-byte alignment of the stages");
 };
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(St
         qn[v] = fmaf(mhr, acc, c[x].q[v]);
       }
       if (on && inner) {
-        *reinterpret_cast<float4*>(a.out + off + (int64_t)(r * NE + x) * S) =
+        *reinterpret_cast<float4*>(gbase + G::OUT + ((r - 1) * P + x - 1) * S) =
             make_float4(qn[0], qn[1], qn[2], qn[3]);
         if constexpr (STEP) {
           // primitives and wave speeds of the new state (next CFL maximum)
@@ -366,6 +368,17 @@ __global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(St
             po[4 * NI] = w.e;
           }
         }
+      }
+    }
+    // the new state to the output: the group's lanes store consecutive
+    // cells (from the output stage), so the stores coalesce
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int c = r; c < P * P; c += kRowsGroup) {
+        const int yy = c / P, xx = c - yy * P;
+        *reinterpret_cast<float4*>(a.out + off + (int64_t)((yy + 1) * NE + xx + 1) * S) =
+            *reinterpret_cast<const float4*>(gbase + G::OUT + c * S);
       }
     }
     write_rec2d(recs + rl, nx, r);  // read after the next iteration's warp barrier

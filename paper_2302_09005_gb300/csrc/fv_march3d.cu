@@ -57,7 +57,9 @@ constexpr int kMGroups = (kMNT / 32) * kMPW;  // patches per CTA and iteration
 template <int P>
 struct MGeom {
   static constexpr int S = 5, NE = P + 2;
-  static_assert(NE <= kMG, "the rows of a patch box fit a lane group");
+  // rows 0 .. NE - 1 on the group's lanes; for NE = kMG + 1 the last
+  // interior lane also reads the upper y-halo row
+  static_assert(NE <= kMG + 1, "the rows of a patch box fit a lane group");
   static constexpr int SPAN = P * NE * S;         // rows 1 .. P of a plane
   static constexpr int ROW = P * S;               // cells 1 .. P of a row
   static constexpr int NA = (SPAN + 6) / 4;       // chunks of the span, at most
@@ -195,15 +197,23 @@ __device__ __forceinline__ void sread(float (&q)[5], const float* p, unsigned nm
 }
 constexpr unsigned kSign = 0x80000000u;
 
+// Resident CTAs per SM the registers are sized for: P = 5 at 168 registers,
+// P = 7 (seven cells a row in flight) at 255.
+template <int P>
+constexpr int march_blocks() {
+  return P <= 5 ? FV_MARCH3D_MINBLOCKS : 8;
+}
+
 template <int P, bool STEP, bool LAM>
-__global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(StepParams<float> a) {
+__global__ void __launch_bounds__(kMNT, march_blocks<P>()) march3d_kernel(StepParams<float> a) {
   using G = MGeom<P>;
   constexpr int S = 5, NE = P + 2;
+  constexpr bool TOP = NE == kMG + 1;  // lane P also converts the upper y-halo row
   extern __shared__ __align__(16) float msm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int grp = lane >> 3, r = lane & 7;
   const bool inner = r >= 1 && r <= P;      // interior row
-  const bool hrow = r == 0 || r == NE - 1;  // face-halo row
+  const bool hrow = r == 0 || (!TOP && r == NE - 1);  // face-halo row of this lane
   const int ri = inner ? r - 1 : 0;         // span row this lane reads (a valid one)
   float* const stg = msm + G::F_STAGE + wid * (G::STAGES * kMPW * G::GSTR) + grp * G::GSTR;
   float* const outb = msm + G::F_OUT + (wid * kMPW + grp) * G::OSTR;
@@ -383,6 +393,15 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
       }
       lprims(h0, gm1, gam, act && inner, chk);
       lprims(h1, gm1, gam, act && inner, chk);
+      // the upper y-halo row where it has no lane of its own
+      const float* toprow = nullptr;
+      unsigned topm = 0u;
+      if constexpr (TOP) {
+        const int fck = m->fck[3];
+        const long long so = m->fo[3] + (long long)(1 + NE * ((fck & 0xFF) + NE * z)) * S;
+        toprow = slot + G::OY + 4 * G::NY + (int)(so & 3);
+        topm = (fck >> 8) ? kSign : 0u;
+      }
       // ---- cell by cell: its upper x face (dGx), then its y faces: rows
       // r | r + 1 (the upper cells from lane r + 1), the face below from lane
       // r - 1; dGx + dGy carried with the state
@@ -413,6 +432,12 @@ __global__ void __launch_bounds__(kMNT, FV_MARCH3D_MINBLOCKS) march3d_kernel(Ste
         up.p = __shfl_down_sync(0xFFFFFFFFu, cc[i].p, 1);
         up.c = __shfl_down_sync(0xFFFFFFFFu, cc[i].c, 1);
         up.e = __shfl_down_sync(0xFFFFFFFFu, cc[i].e, 1);
+        if constexpr (TOP) {
+          if (r == P) {  // row P + 1: staged by the group, converted here
+            sread(up.q, toprow + i * S, 0u, topm, 0u);
+            lprims(up, gm1, gam, act, chk);
+          }
+        }
         float g[S];
         const unsigned ab = lflux<1>(cc[i], up, g);
         lmax = umax_l(lmax, ab & ((LAM && act && r <= P) ? kMagL : 0u));
@@ -505,7 +530,7 @@ cudaError_t occupancy_march3d_t(int* bps) {  // the kernel with per-patch maxima
 }  // namespace
 
 bool march3d_class(const fv_batch* h, int p) {
-  return h->prec == FV_FP32 && h->d == 3 && h->s == 5 && p == 5;
+  return h->prec == FV_FP32 && h->d == 3 && h->s == 5 && (p == 5 || p == 7);
 }
 
 bool march3d_eligible(const fv_batch* h, const UpdateLaunch& l) {
@@ -516,16 +541,24 @@ bool march3d_eligible(const fv_batch* h, const UpdateLaunch& l) {
 
 int march3d_patches_per_cta() { return kMGroups; }
 
-cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid) {
+template <int P>
+static cudaError_t launch_march3d_p(const fv_batch* h, const UpdateLaunch& l, int grid) {
   const bool step = step_mode(l) == kModeStep, lam = l.lam_patch != nullptr;
   if (step)
-    return lam ? launch_march3d_t<5, true, true>(h, l, grid)
-               : launch_march3d_t<5, true, false>(h, l, grid);
-  return lam ? launch_march3d_t<5, false, true>(h, l, grid)
-             : launch_march3d_t<5, false, false>(h, l, grid);
+    return lam ? launch_march3d_t<P, true, true>(h, l, grid)
+               : launch_march3d_t<P, true, false>(h, l, grid);
+  return lam ? launch_march3d_t<P, false, true>(h, l, grid)
+             : launch_march3d_t<P, false, false>(h, l, grid);
 }
 
-cudaError_t march3d_occupancy(int mode, int* bps) {
+cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid) {
+  return l.uniform_p == 7 ? launch_march3d_p<7>(h, l, grid) : launch_march3d_p<5>(h, l, grid);
+}
+
+cudaError_t march3d_occupancy(int p, int mode, int* bps) {
+  if (p == 7)
+    return mode == kModeStep ? occupancy_march3d_t<7, true>(bps)
+                             : occupancy_march3d_t<7, false>(bps);
   return mode == kModeStep ? occupancy_march3d_t<5, true>(bps) : occupancy_march3d_t<5, false>(bps);
 }
 

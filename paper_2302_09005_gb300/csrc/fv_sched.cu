@@ -47,8 +47,8 @@ static int grid_for(const fv_batch* h, int64_t count, int bps) {
 }
 
 // A launch of patches of one size: the FP32 kernel built for that size (3D
-// p = 5: the plane sweep, p = 3: a lane per line; 2D p = 5: a lane per row)
-// where it applies.
+// p = 5 and 7: the plane sweep, p = 3: a lane per line; 2D p = 5: a lane per
+// row) where it applies.
 static cudaError_t launch_one_size(fv_batch* h, const UpdateLaunch& l, int64_t count,
                                    bool* done) {
   *done = false;
@@ -58,11 +58,11 @@ static cudaError_t launch_one_size(fv_batch* h, const UpdateLaunch& l, int64_t c
                                             : 0;
   if (kind == 0) return cudaSuccess;
   const int f = step_mode(l);
-  int& bps = kind == 2 ? h->occ_lines[f] : h->occ_one[f];  // a handle has one d
+  int& bps = kind == 2 ? h->occ_lines[f] : h->occ_one[l.uniform_p == 7 ? 1 : 0][f];
   if (bps == 0) {
     cudaError_t e = kind == 1   ? rows2d_occupancy(f, &bps)
                     : kind == 2 ? lines3d_occupancy(f, &bps)
-                                : march3d_occupancy(f, &bps);
+                                : march3d_occupancy(l.uniform_p, f, &bps);
     if (e != cudaSuccess) return e;
   }
   *done = true;

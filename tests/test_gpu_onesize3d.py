@@ -1,5 +1,5 @@
 """The FP32 kernels for launches of one 3D patch size (csrc/fv_march3d.cu for
-5^3 patches, csrc/fv_lines3d.cu for 3^3): each runs (launch counter) for
+5^3 and 7^3 patches, csrc/fv_lines3d.cu for 3^3): each runs (launch counter) for
 planned batches under every schedule and for its class of uneven batches,
 and its results are bitwise those of the general kernel -- time steps on periodic, outflow and wall meshes (with
 per-patch wave speeds and the primitives of the new state), update mode --
@@ -15,7 +15,7 @@ from tests import fvtest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=[5, 3], ids=["march5", "lines3"])
+@pytest.fixture(params=[5, 3, 7], ids=["march5", "lines3", "march7"])
 def P(request):
     return request.param
 
@@ -149,7 +149,7 @@ def test_time_step_matches_oracle(fv, P):
     b.close()
 
 
-def test_uneven_batch_uses_them_for_the_3_and_5_cubed_classes(fv):
+def test_uneven_batch_uses_them_for_every_class(fv):
     n = 900
     sizes = inputs.uneven_sizes(n, seed=75)
     q, off, sz = inputs.random_batch(n, sizes, 3, seed=75, dtype=np.float32)
@@ -162,7 +162,7 @@ def test_uneven_batch_uses_them_for_the_3_and_5_cubed_classes(fv):
     b = batch(fv, True, tsz, n, 2, p=7)
     got = time_steps(fv, b, q, toff, tsz, tnbr, dx, cfl, steps).cpu().numpy()
     assert b.status() == fv.FV_OK
-    assert fv.fv_batch_pairs_launches(b.h) == 2 * steps  # 3^3 and 5^3, not 7^3
+    assert fv.fv_batch_pairs_launches(b.h) == 3 * steps  # 3^3, 5^3 and 7^3
     mask = fvtest.interior_mask(off, sz, 3, 5, len(q))
     assert np.array_equal(got[mask], ref[mask])
     b.close()

@@ -98,7 +98,7 @@ def source_hash() -> str:
 # headers it includes); host-side API changes leave its counters valid.
 STEP_KERNEL_SOURCES = ("fv_step.cuh", "fv_device.cuh", "fv_ptx.cuh", "fv_update.cu",
                        "fv_update_f32.cu", "fv_update_nt.cu", "fv_update_nt_f32.cu",
-                       "fv_rows2d.cu", "fv_lines3d.cu", "fv_march3d.cu", "fv_cell3.cuh")
+                       "fv_rows2d.cu", "fv_march3d.cu", "fv_cell3.cuh")
 
 
 def step_kernel_hash() -> str:

@@ -1,5 +1,5 @@
-// fv_cell3.cuh -- one FP32 3D Euler cell in registers for the kernels built
-// for one 3D patch size (fv_lines3d.cu, fv_march3d.cu): its state and
+// fv_cell3.cuh -- one FP32 3D Euler cell in registers for the kernel built
+// for one 3D patch size (fv_march3d.cu): its state and
 // primitives (Eq. 2) and the Rusanov flux G = 2F of a face (Eq. 4, 5), with
 // the operations, in order, of primitives<float, 3>() and of the face flux of
 // the general kernel (fv_step.cuh), so results are bitwise the same.

@@ -51,8 +51,7 @@ struct fv_batch {
   int cls_nt[64] = {0};                      // CTA size of the size-class launches (0: 128)
   int cls_only = -1;                         // autotuner: launch only this class (-1: all)
   int cls_real[64] = {0};                    // class c holds one valid size (not the rejects)
-  int occ_one[2][3] = {};                    // CTAs per SM of the FP32 one-size kernels (p = 5, 7), by mode
-  int occ_lines[3] = {0, 0, 0};              // CTAs per SM of the FP32 3^3 lines kernel, by mode
+  int occ_one[3][3] = {};                    // CTAs per SM of the FP32 one-size kernels (p = 3, 5, 7), by mode
   int64_t pairs_launches = 0;                // launches that used an FP32 one-size kernel
   void* host_stage = nullptr;                // fv_patch_update_host: streams, staging buffers
   int smem_optin = 0;                        // opt-in shared memory per CTA
@@ -155,7 +154,7 @@ bool rows2d_eligible(const fv_batch* h, const UpdateLaunch& l);
 int rows2d_patches_per_cta();
 cudaError_t launch_rows2d(const fv_batch* h, const UpdateLaunch& l, int grid);
 cudaError_t rows2d_occupancy(int mode, int* blocks_per_sm);
-// The FP32 kernel for launches of 3D patches of size p = 5 or 7 (fv_march3d.cu: a
+// The FP32 kernel for launches of 3D patches of size p = 3, 5 or 7 (fv_march3d.cu: a
 // lane per row of cells, four patches per warp, each patch advanced plane by
 // plane along z; march3d_patches_per_cta() patches per CTA and iteration):
 // whether a size class / a launch can use it, its launch and its occupancy.
@@ -164,14 +163,6 @@ bool march3d_eligible(const fv_batch* h, const UpdateLaunch& l);
 int march3d_patches_per_cta();
 cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid);
 cudaError_t march3d_occupancy(int p, int mode, int* blocks_per_sm);
-// The same for launches of 3D patches of size p = 3 (fv_lines3d.cu: a lane
-// per line of cells along x, one patch per warp, lines3d_patches_per_cta()
-// patches per CTA and iteration).
-bool lines3d_class(const fv_batch* h, int p);
-bool lines3d_eligible(const fv_batch* h, const UpdateLaunch& l);
-int lines3d_patches_per_cta();
-cudaError_t launch_lines3d(const fv_batch* h, const UpdateLaunch& l, int grid);
-cudaError_t lines3d_occupancy(int mode, int* blocks_per_sm);
 // Launches the update / time-step kernel(s) under the handle's schedule.
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l);
 // Frees the schedule plan of a handle.

@@ -1,13 +1,14 @@
 // fv_march3d.cu -- the FP32 time step / update of a launch whose patches all
-// have one 3D size P (P + 2 <= 8; P = 5: a size class of the schedule, or a
-// uniform batch after fv_batch_plan): a lane per row of cells along x, the
-// patch swept plane by plane along z.  Same method, same operations in the
+// have one 3D size P = 3, 5 or 7 (a size class of the schedule, or a uniform
+// batch after fv_batch_plan): a lane per row of cells along x, the patch swept
+// plane by plane along z.  Same method, same operations in the
 // same order as the general kernel (fv_step.cuh; Eq. 2-5, Algorithm 1 steps
 // 5-10), so the results are bitwise the same.
 //
 // A warp advances four patches at a time, eight lanes each; lane r of a group
 // holds row y = r of the current plane z (r = 0 and r = P + 1 the face-halo
-// rows, lane 7 idle).  Per plane:
+// rows; lanes past P + 1 idle; for P = 7 lane 7 holds row 7 and also converts
+// the staged row 8).  Per plane:
 //
 //  * staging: the plane's data arrive in shared memory by cp.async copies of
 //    16-byte chunks issued one plane ahead (the next patch's first plane
@@ -197,11 +198,11 @@ __device__ __forceinline__ void sread(float (&q)[5], const float* p, unsigned nm
 }
 constexpr unsigned kSign = 0x80000000u;
 
-// Resident CTAs per SM the registers are sized for: P = 5 at 168 registers,
-// P = 7 (seven cells a row in flight) at 255.
+// Resident CTAs per SM the registers are sized for: P = 3 at 128 registers,
+// P = 5 at 168, P = 7 (seven cells a row in flight) at 255.
 template <int P>
 constexpr int march_blocks() {
-  return P <= 5 ? FV_MARCH3D_MINBLOCKS : 8;
+  return P <= 3 ? 16 : P <= 5 ? FV_MARCH3D_MINBLOCKS : 8;
 }
 
 template <int P, bool STEP, bool LAM>
@@ -530,7 +531,7 @@ cudaError_t occupancy_march3d_t(int* bps) {  // the kernel with per-patch maxima
 }  // namespace
 
 bool march3d_class(const fv_batch* h, int p) {
-  return h->prec == FV_FP32 && h->d == 3 && h->s == 5 && (p == 5 || p == 7);
+  return h->prec == FV_FP32 && h->d == 3 && h->s == 5 && (p == 3 || p == 5 || p == 7);
 }
 
 bool march3d_eligible(const fv_batch* h, const UpdateLaunch& l) {
@@ -552,10 +553,20 @@ static cudaError_t launch_march3d_p(const fv_batch* h, const UpdateLaunch& l, in
 }
 
 cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid) {
-  return l.uniform_p == 7 ? launch_march3d_p<7>(h, l, grid) : launch_march3d_p<5>(h, l, grid);
+  switch (l.uniform_p) {
+    case 3:
+      return launch_march3d_p<3>(h, l, grid);
+    case 7:
+      return launch_march3d_p<7>(h, l, grid);
+    default:
+      return launch_march3d_p<5>(h, l, grid);
+  }
 }
 
 cudaError_t march3d_occupancy(int p, int mode, int* bps) {
+  if (p == 3)
+    return mode == kModeStep ? occupancy_march3d_t<3, true>(bps)
+                             : occupancy_march3d_t<3, false>(bps);
   if (p == 7)
     return mode == kModeStep ? occupancy_march3d_t<7, true>(bps)
                              : occupancy_march3d_t<7, false>(bps);

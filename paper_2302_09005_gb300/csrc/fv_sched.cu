@@ -47,34 +47,24 @@ static int grid_for(const fv_batch* h, int64_t count, int bps) {
 }
 
 // A launch of patches of one size: the FP32 kernel built for that size (3D
-// p = 5 and 7: the plane sweep, p = 3: a lane per line; 2D p = 5: a lane per
-// row) where it applies.
+// p = 3, 5, 7: the plane sweep; 2D p = 5: a lane per row) where it applies.
 static cudaError_t launch_one_size(fv_batch* h, const UpdateLaunch& l, int64_t count,
                                    bool* done) {
   *done = false;
-  const int kind = rows2d_eligible(h, l)    ? 1
-                   : lines3d_eligible(h, l) ? 2
-                   : march3d_eligible(h, l) ? 3
-                                            : 0;
-  if (kind == 0) return cudaSuccess;
+  const bool two = rows2d_eligible(h, l);
+  if (!two && !march3d_eligible(h, l)) return cudaSuccess;
   const int f = step_mode(l);
-  int& bps = kind == 2 ? h->occ_lines[f] : h->occ_one[l.uniform_p == 7 ? 1 : 0][f];
+  int& bps = h->occ_one[l.uniform_p == 3 ? 0 : l.uniform_p == 7 ? 2 : 1][f];
   if (bps == 0) {
-    cudaError_t e = kind == 1   ? rows2d_occupancy(f, &bps)
-                    : kind == 2 ? lines3d_occupancy(f, &bps)
-                                : march3d_occupancy(l.uniform_p, f, &bps);
+    cudaError_t e = two ? rows2d_occupancy(f, &bps) : march3d_occupancy(l.uniform_p, f, &bps);
     if (e != cudaSuccess) return e;
   }
   *done = true;
   ++h->pairs_launches;
   // a CTA takes several patches at a time
-  const int per = kind == 1   ? rows2d_patches_per_cta()
-                  : kind == 2 ? lines3d_patches_per_cta()
-                              : march3d_patches_per_cta();
+  const int per = two ? rows2d_patches_per_cta() : march3d_patches_per_cta();
   const int grid = grid_for(h, (count + per - 1) / per, bps);
-  return kind == 1   ? launch_rows2d(h, l, grid)
-         : kind == 2 ? launch_lines3d(h, l, grid)
-                     : launch_march3d(h, l, grid);
+  return two ? launch_rows2d(h, l, grid) : launch_march3d(h, l, grid);
 }
 
 cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
@@ -298,8 +288,7 @@ fv_status fv_batch_autotune(fv_batch* h, const void* in, void* scratch_out, cons
   // 1. the CTA size of each size class (one-class launches)
   h->sched = FV_SCHED_CLASSES;
   for (int c = 0; c < h->ncls && st == FV_OK; ++c) {
-    if (h->cls_real[c] && (fv::march3d_class(h, h->cls_p[c]) || fv::rows2d_class(h, h->cls_p[c]) ||
-                             fv::lines3d_class(h, h->cls_p[c])))
+    if (h->cls_real[c] && (fv::march3d_class(h, h->cls_p[c]) || fv::rows2d_class(h, h->cls_p[c])))
       continue;  // kernels with a fixed CTA size
     const int pi = h->cls_p[c] < 64 ? h->cls_p[c] : 63;
     const int keep = h->cls_nt[pi];

@@ -1,10 +1,10 @@
-"""The FP32 kernels for launches of one 3D patch size (csrc/fv_march3d.cu for
-5^3 and 7^3 patches, csrc/fv_lines3d.cu for 3^3): each runs (launch counter) for
-planned batches under every schedule and for its class of uneven batches,
-and its results are bitwise those of the general kernel -- time steps on periodic, outflow and wall meshes (with
-per-patch wave speeds and the primitives of the new state), update mode --
-and within the FP32 tolerance of the FP64 oracle.  Non-physical states are
-flagged as by the general kernel."""
+"""The FP32 kernel for launches of one 3D patch size (csrc/fv_march3d.cu, for
+3^3, 5^3 and 7^3 patches): it runs (launch counter) for planned batches under
+every schedule and for every class of uneven batches, and its results are
+bitwise those of the general kernel -- time steps on periodic, outflow and
+wall meshes (with per-patch wave speeds and the primitives of the new state),
+update mode -- and within the FP32 tolerance of the FP64 oracle.
+Non-physical states are flagged as by the general kernel."""
 import numpy as np
 import pytest
 
@@ -15,7 +15,7 @@ from tests import fvtest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=[5, 3, 7], ids=["march5", "lines3", "march7"])
+@pytest.fixture(params=[5, 3, 7], ids=["p5", "p3", "p7"])
 def P(request):
     return request.param
 

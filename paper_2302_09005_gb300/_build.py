@@ -94,18 +94,22 @@ def source_hash() -> str:
     return hsh.hexdigest()[:16]
 
 
-# Sources of the patch update / time-step kernel itself (device code and the
-# headers it includes); host-side API changes leave its counters valid.
-STEP_KERNEL_SOURCES = ("fv_step.cuh", "fv_device.cuh", "fv_ptx.cuh", "fv_update.cu",
-                       "fv_update_f32.cu", "fv_update_nt.cu", "fv_update_nt_f32.cu",
-                       "fv_rows2d.cu", "fv_march3d.cu", "fv_cell3.cuh")
+# Sources of each update / time-step kernel (device code and the headers it
+# includes); host-side API changes leave its counters valid.
+_STEP_CORE = ("fv_step.cuh", "fv_device.cuh", "fv_ptx.cuh")
+KERNEL_SOURCES = {
+    "step": _STEP_CORE + ("fv_update.cu", "fv_update_f32.cu", "fv_update_nt.cu",
+                          "fv_update_nt_f32.cu"),
+    "march3d": _STEP_CORE + ("fv_march3d.cu", "fv_cell3.cuh", "fv_meta.cuh"),
+    "rows2d": _STEP_CORE + ("fv_rows2d.cu", "fv_meta.cuh"),
+}
 
 
-def step_kernel_hash() -> str:
-    """Hash of the step kernel's sources (keys the committed ncu traffic)."""
+def kernel_hash(kind: str = "step") -> str:
+    """Hash of one kernel's sources (keys the committed ncu traffic)."""
     import hashlib
     hsh = hashlib.sha256()
-    for name in STEP_KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[kind]:
         with open(os.path.join(CSRC, name), "rb") as fh:
             hsh.update(name.encode())
             hsh.update(fh.read())

@@ -28,7 +28,7 @@
 //    y), takes one FMA with -dt / (2 dx) and, in a time step, converts the new
 //    state for the next CFL maximum; the new state goes to the output through
 //    shared memory, the group's lanes storing consecutive 16-byte cells.
-#include "fv_step.cuh"
+#include "fv_meta.cuh"
 
 // Resident one-warp CTAs per SM the register allocation is sized for.
 #ifndef FV_ROWS2D_MINBLOCKS
@@ -122,109 +122,7 @@ struct RRec {
 };
 static_assert(sizeof(RRec) <= 16 * 4, "record size");
 
-struct RNext {
-  long long fo, off;
-  int fck, pid, act;
-};
-
-// A patch's metadata is loaded in three steps, one per iteration of the
-// patch loop, so that no load of an iteration waits on another load of the
-// same iteration: the patch index (the schedule's order); the patch's size,
-// offset and its neighbour across face r; the neighbour's size and offset.
-// Every index is clamped to a valid entry (a position past the launch: the
-// launch's first; a neighbour that is not a patch: the patch itself), so
-// each load stays in bounds; finish_patch2d then applies the rules of the
-// general kernel's face_source (Algorithm 1 step 5: where the face-halo cells
-// come from) to the loaded values.
-struct RMeta2 {
-  long long off;
-  int pid, pj, nb;
-};
-struct RMeta3 {
-  long long onb;
-  int snb;
-};
-
-__device__ __forceinline__ int meta_pid(const StepParams<float>& a, int64_t pos) {
-  const int64_t pc = pos < a.i_end ? pos : a.i_begin;
-  return a.order != nullptr ? a.order[pc] : (int)pc;
-}
-
-template <bool STEP>
-__device__ __forceinline__ RMeta2 meta_patch(const StepParams<float>& a, int pid, int r) {
-  RMeta2 m;
-  m.pid = pid;
-  m.pj = a.sizes[pid];
-  m.off = a.off[pid];
-  m.nb = -1;
-  if constexpr (STEP) m.nb = a.nbr[(int64_t)pid * 4 + (r & 3)];
-  return m;
-}
-
-template <bool STEP>
-__device__ __forceinline__ RMeta3 meta_nbr(const StepParams<float>& a, const RMeta2& m) {
-  RMeta3 t{0, 0};
-  if constexpr (STEP) {
-    const int nc = (m.nb >= 0 && m.nb < a.n) ? m.nb : m.pid;
-    t.onb = a.off[nc];
-    t.snb = a.sizes[nc];
-  }
-  return t;
-}
-
-// The record of the patch at `pos` (lanes r = 0 .. 3: the source of face r)
-// from its loaded metadata; flags what face_source and the general kernel
-// flag (a patch of another size or layout, a neighbour that is not a valid
-// patch of the same size, an unknown boundary code).
-template <int P, bool STEP>
-__device__ __forceinline__ RNext finish_patch2d(const StepParams<float>& a, int64_t pos,
-                                                const RMeta2& m, const RMeta3& t, int r) {
-  constexpr int S = 4, NE = P + 2;
-  RNext n{0, 0, 0, 0, 0};
-  if (pos >= a.i_end) return n;
-  const bool act = m.pj == P && m.off >= 0 && (m.off % 4) == 0 &&
-                   (a.n_elems <= 0 || m.off + (int64_t)NE * NE * S <= a.n_elems);
-  if (!act && r == 0) atomicOr(a.status, ST_BAD_PATCH);  // other size or bad layout
-  n.pid = m.pid;
-  n.off = m.off;
-  n.act = act ? 1 : 0;
-  if (act && r < 4) {
-    const int side = r & 1;
-    long long so = m.off;
-    int ck, neg = 0;
-    if constexpr (!STEP) {
-      ck = side ? P + 1 : 0;  // the own halo layer
-    } else {
-      ck = side ? P : 1;  // outflow: the own interior layer next to the face
-      if (m.nb >= 0) {
-        const bool ok = m.nb < a.n && t.snb == P && t.onb >= 0 && (t.onb % 4) == 0 &&
-                        (a.n_elems <= 0 || t.onb + (int64_t)NE * NE * S <= a.n_elems);
-        if (ok) {
-          so = t.onb;
-          ck = side ? 1 : P;  // the neighbour's interior layer next to the face
-        } else {
-          atomicOr(a.status, ST_BAD_PATCH);
-        }
-      } else if (m.nb == -2) {
-        neg = 1;  // wall: mirror of the own interior layer
-      } else if (m.nb != -1) {
-        atomicOr(a.status, ST_BAD_PATCH);
-      }
-    }
-    n.fo = so;
-    n.fck = ck | (neg << 8);
-  }
-  return n;
-}
-
-// All three steps at once (the first patches of a warp).
-template <int P, bool STEP>
-__device__ __forceinline__ RNext resolve_patch2d(const StepParams<float>& a, int64_t pos, int r) {
-  const RMeta2 m = meta_patch<STEP>(a, meta_pid(a, pos), r);
-  return finish_patch2d<P, STEP>(a, pos, m, meta_nbr<STEP>(a, m), r);
-}
-
-__device__ __forceinline__ void write_rec2d(RRec* rec, const RNext& n, int r) {
+__device__ __forceinline__ void write_rec2d(RRec* rec, const PatchSrc& n, int r) {
   if (r < 4) {
     rec->fo[r] = n.fo;
     rec->fck[r] = n.fck;
@@ -311,11 +209,11 @@ __global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(St
   const int64_t base0 = a.i_begin + warp * kRowsPerWarp;
   if (base0 >= a.i_end) return;  // the whole warp: no patch
   // the first two patches resolved, the first one's copies issued
-  write_rec2d(recs, resolve_patch2d<P, STEP>(a, base0 + grp, r), r);
-  write_rec2d(recs + 1, resolve_patch2d<P, STEP>(a, base0 + stride + grp, r), r);
+  write_rec2d(recs, resolve_now<2, P, STEP>(a, base0 + grp, r & 3, r < 4, r == 0), r);
+  write_rec2d(recs + 1, resolve_now<2, P, STEP>(a, base0 + stride + grp, r & 3, r < 4, r == 0), r);
   __syncwarp();
   // the metadata pipeline: patch 2 past its second step, patch 3 past its first
-  RMeta2 q2 = meta_patch<STEP>(a, meta_pid(a, base0 + 2 * stride + grp), r);
+  MetaPatch q2 = meta_patch<2, STEP>(a, meta_pid(a, base0 + 2 * stride + grp), r & 3);
   int q3 = meta_pid(a, base0 + 3 * stride + grp);
   issue_patch2d<P, STEP>(a, recs, gbase, r);
   cp_async_commit();
@@ -325,8 +223,8 @@ __global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(St
   for (int64_t base = base0; base < a.i_end; base += stride) {
     // this iteration's metadata loads (patches two, three and four ahead),
     // consumed at its end or in the next iteration
-    const RMeta3 t2 = meta_nbr<STEP>(a, q2);
-    const RMeta2 n3 = meta_patch<STEP>(a, q3, r);
+    const MetaNbr t2 = meta_nbr<STEP>(a, q2);
+    const MetaPatch n3 = meta_patch<2, STEP>(a, q3, r & 3);
     const int n4 = meta_pid(a, base + 4 * stride + grp);
     cp_async_wait_all();
     __syncwarp();
@@ -462,7 +360,9 @@ __global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(St
     }
     // the record of the patch two ahead, read after the next iteration's
     // warp barrier
-    write_rec2d(recs + rl, finish_patch2d<P, STEP>(a, base + 2 * stride + grp, q2, t2, r), r);
+    write_rec2d(recs + rl,
+                finish_patch<2, P, STEP>(a, base + 2 * stride + grp, q2, t2, r & 3, r < 4, r == 0),
+                r);
     q2 = n3;
     q3 = n4;
     const int t = rc;

@@ -1103,7 +1103,7 @@ def _traffic(workload):
             t = json.load(f)
         from paper_2302_09005_gb300 import _build
         ent = t.get(workload)
-        if ent and ent.get("kernel_hash") == _build.step_kernel_hash():
+        if ent and ent.get("kernel_hash") == _build.kernel_hash(ent.get("kernel", "step")):
             return ent["dram_bytes_per_launch"]
     except Exception:
         return None

@@ -231,3 +231,36 @@ def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv, P):
     assert res[0][2] == 0 and res[1][2] == 1
     assert np.array_equal(res[0][1], res[1][1])
     assert np.array_equal(res[1][1][off[-1]:], q[off[-1]:])  # the last patch untouched
+
+
+def test_bad_neighbour_entries_flagged_like_the_general_kernel(fv, P):
+    """Neighbour-table entries that name no patch (an index past the batch, an
+    unknown boundary code) and a neighbour with a misaligned offset: both
+    kernels report FV_ERR_BAD_PATCH, take those faces as outflow, and agree
+    bitwise on the new state (the face-source rules applied to staged
+    metadata are the general kernel's)."""
+    torch = fvtest.torch_cuda()
+    grid = (9, 8, 7)
+    n = int(np.prod(grid))
+    q, off, sz = fvtest.random_batch(n, P, 3, 79, np.float32)
+    nbr = inputs.grid_neighbours(grid).copy()
+    nbr[5, 0] = n + 5      # past the batch
+    nbr[40, 3] = -3        # no such boundary code
+    nbr[77, 4] = n         # one past the end
+    off = off.copy()
+    mis = 123
+    off[mis] += 1          # misaligned: bad as a patch and as a neighbour
+    toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
+    dx = 1.0 / (grid[0] * P)
+    res = []
+    for planned in (False, True):
+        b = batch(fv, planned, tsz, n, 2, P)
+        x = fvtest.to_dev(q)
+        y = x.clone()
+        b.max_eigenvalue(x, toff, tsz, 0.4, dx)
+        b.time_step(x, y, toff, tsz, tnbr, dx, 0.4)
+        res.append((b.status(), y.cpu().numpy(), fv.fv_batch_pairs_launches(b.h)))
+        b.close()
+    assert res[0][0] == fv.FV_ERR_BAD_PATCH and res[1][0] == fv.FV_ERR_BAD_PATCH
+    assert res[0][2] == 0 and res[1][2] == 1
+    assert np.array_equal(res[0][1], res[1][1])

@@ -255,3 +255,31 @@ def test_invalid_patches_inside_the_sequence(fv, step):
     assert res[0][0] == fv.FV_ERR_BAD_PATCH and res[1][0] == fv.FV_ERR_BAD_PATCH
     assert res[0][2] == 0 and res[1][2] == 1
     assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_bad_neighbour_entries_flagged_like_the_general_kernel(fv):
+    """Neighbour-table entries that name no patch (an index past the batch, an
+    unknown boundary code): both kernels report FV_ERR_BAD_PATCH, take those
+    faces as outflow and agree bitwise on the new state."""
+    torch = fvtest.torch_cuda()
+    grid = (40, 30)
+    n = int(np.prod(grid))
+    q, off, sz = fvtest.random_batch(n, P, D, 98, np.float32)
+    nbr = inputs.grid_neighbours(grid).copy()
+    nbr[7, 1] = n + 2
+    nbr[300, 2] = -7
+    nbr[901, 3] = n
+    toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
+    dx = 1.0 / (grid[0] * P)
+    res = []
+    for planned in (False, True):
+        b = batch(fv, planned, tsz, n, 2)
+        x = fvtest.to_dev(q)
+        y = x.clone()
+        b.max_eigenvalue(x, toff, tsz, 0.4, dx)
+        b.time_step(x, y, toff, tsz, tnbr, dx, 0.4)
+        res.append((b.status(), y.cpu().numpy(), fv.fv_batch_pairs_launches(b.h)))
+        b.close()
+    assert res[0][0] == fv.FV_ERR_BAD_PATCH and res[1][0] == fv.FV_ERR_BAD_PATCH
+    assert res[0][2] == 0 and res[1][2] == 1
+    assert np.array_equal(res[0][1], res[1][1])

@@ -21,20 +21,24 @@
 //    from its 16-byte-aligned start, so the eight lanes of a group read
 //    consecutive chunks and the copies coalesce;
 //  * z faces: the face between plane z - 1 and plane z of every cell of the
-//    row; plane z - 1 (its state, its primitives, the sum of its x and y flux
-//    differences and the z flux of the face below it) stays in registers from
-//    the previous plane, so no lane exchange is needed.  Plane z - 1 is then
+//    row; plane z - 1 (its state, the sum of its x and y flux differences and
+//    the z flux of the face below it) stays in registers from the previous
+//    plane, so no lane exchange is needed (its primitives are converted again
+//    from its state: the same operations, fewer registers).  Plane z - 1 is then
 //    complete: Q - (dt / 2dx)(dGx + dGy + dGz), stored through shared memory
 //    as contiguous row segments and, in a time step, converted for the next
 //    CFL maximum;
 //  * x faces along the lane's row, y faces with the upper row's cells from
 //    lane r + 1 (warp shuffle), the flux of the face below from lane r - 1:
 //    dGx + dGy of plane z, carried to the next plane with its state.
+//
+// Where the next patch's data come from is loaded in the dependent steps of
+// fv_meta.cuh, one per plane over the current patch's first planes.
 #include "fv_cell3.cuh"
 #include "fv_meta.cuh"
 
-// Resident CTAs of one warp per SM the register allocation is sized for
-// (12 x 32 threads x 168 registers: no spills).
+// Resident one-warp CTAs per SM the register allocation of P = 5 is sized
+// for (12 x 32 threads x 168 registers: no spills).
 #ifndef FV_MARCH3D_MINBLOCKS
 #define FV_MARCH3D_MINBLOCKS 12
 #endif

@@ -3,7 +3,8 @@ times, on sampled patches (and faces) the oracle computes one by one.
 
 * 3D Euler FP64, 262,144 patches of 5^3 on a 64^3 periodic patch mesh: the
   time step with the primitive carry, two steps (the second reads carried
-  primitives); each step against an oracle step from the same state.
+  primitives); each step against an oracle step from the same state.  The
+  same mesh in FP32, the batch planned (the one-size 5^3 kernel), two steps.
 * Uneven batch, 200,000 patches (50/30/20 % of 3^3/5^3/7^3, self-periodic),
   FP64 and FP32: per-size-class launches with autotuned CTA sizes, one step
   of the multi-step graph driver.
@@ -100,6 +101,42 @@ def test_config2_fp64_carry_steps_full_size(fv):
         check_sampled(got, ref, off, sz, d, TOL64)
         state = got
         x, y = y, x
+    b.close()
+
+
+def test_config2_fp32_planned_steps_full_size(fv):
+    """The same mesh in FP32 as bench.py's FP32 variant times it: the batch
+    planned, so the one-size kernel for 5^3 runs; two time steps, sampled
+    patches against the oracle (FP64 from the FP32 state) at 1e-5."""
+    torch = fvtest.torch_cuda()
+    d, p, grid = 3, 5, (64, 64, 64)
+    n = int(np.prod(grid))
+    q, off, sz = inputs.random_batch(n, p, d, seed=0, dtype=np.float32)
+    nbr = inputs.grid_neighbours(grid)
+    dx, cfl = 1.0 / (grid[0] * p), 0.4
+    ids = np.sort(np.random.default_rng(2).choice(n, 48, replace=False))
+    stream = torch.cuda.Stream()
+    b = fv.Batch(d, precision=fv.FV_FP32, max_patch_size=p, stream=stream)
+    x = torch.from_numpy(q).cuda()
+    y = x.clone()
+    toff, tsz, tnbr = (torch.from_numpy(a).cuda() for a in (off, sz, nbr))
+    fv.fv_batch_plan(b.h, tsz, n)
+    state = q
+    with torch.cuda.stream(stream):
+        b.halo_fill(x, toff, tsz, tnbr)
+        b.max_eigenvalue(x, toff, tsz, cfl, dx)
+    for step in range(2):
+        with torch.cuda.stream(stream):
+            b.time_step(x, y, toff, tsz, tnbr, dx, cfl)
+        stream.synchronize()
+        assert b.status() == fv.FV_OK
+        got = y.cpu().numpy()
+        ref, dt_ref = oracle_step_sampled(state.astype(np.float64), off, sz, nbr, d, dx, cfl, ids)
+        assert fv.fv_read_dt(b.h) == pytest.approx(dt_ref, rel=1e-6)
+        check_sampled(got.astype(np.float64), ref, off, sz, d, TOL32)
+        state = got
+        x, y = y, x
+    assert fv.fv_batch_pairs_launches(b.h) == 2
     b.close()
 
 

@@ -397,8 +397,8 @@ fv_status fv_batch_class_threads(const fv_batch* h, int p, int* threads);
  * FP32 handles with d = 3 or d = 2 run the launches whose patches all have
  * one of the sizes below (a size class of FV_SCHED_CLASSES, or a planned
  * batch of that one size under any schedule) on a kernel built for that
- * size: 3D p = 3, 5 and 7 (eight lanes a patch, a lane per row of cells,
- * the patch swept plane by plane along z) and 2D p = 5 (eight lanes a
+ * size: 3D p = 3 .. 7 (eight lanes a patch, a lane per row of cells, the
+ * patch swept plane by plane along z) and 2D p = 3 .. 6 (eight lanes a
  * patch, a lane per row of cells).  They perform the same operations in the same order as the
  * general kernel, so results are bitwise identical; class thread settings do
  * not apply to them.  Not used with the primitive carry, flux corrections or

@@ -51,7 +51,7 @@ struct fv_batch {
   int cls_nt[64] = {0};                      // CTA size of the size-class launches (0: 128)
   int cls_only = -1;                         // autotuner: launch only this class (-1: all)
   int cls_real[64] = {0};                    // class c holds one valid size (not the rejects)
-  int occ_one[3][3] = {};                    // CTAs per SM of the FP32 one-size kernels (p = 3, 5, 7), by mode
+  int occ_one[8][3] = {};                    // CTAs per SM of the FP32 one-size kernels, by p and mode
   int64_t pairs_launches = 0;                // launches that used an FP32 one-size kernel
   void* host_stage = nullptr;                // fv_patch_update_host: streams, staging buffers
   int smem_optin = 0;                        // opt-in shared memory per CTA
@@ -146,14 +146,14 @@ template <typename T, int NT>
 cudaError_t launch_step_nt(const fv_batch* h, const UpdateLaunch& l, int grid);
 template <typename T, int NT>
 cudaError_t occupancy_nt(int d, int mode, int pmax, int nstage, int* bps);
-// The same for launches of one 2D patch size, p = 5 (fv_rows2d.cu: a lane
+// The same for launches of one 2D patch size, p = 3 .. 6 (fv_rows2d.cu: a lane
 // per row of cells, four patches per warp, rows2d_patches_per_cta() patches
 // per CTA and iteration).
 bool rows2d_class(const fv_batch* h, int p);
 bool rows2d_eligible(const fv_batch* h, const UpdateLaunch& l);
 int rows2d_patches_per_cta();
 cudaError_t launch_rows2d(const fv_batch* h, const UpdateLaunch& l, int grid);
-cudaError_t rows2d_occupancy(int mode, int* blocks_per_sm);
+cudaError_t rows2d_occupancy(int p, int mode, int* blocks_per_sm);
 // The FP32 kernel for launches of 3D patches of size p = 3, 5 or 7 (fv_march3d.cu: a
 // lane per row of cells, four patches per warp, each patch advanced plane by
 // plane along z; march3d_patches_per_cta() patches per CTA and iteration):

@@ -1,5 +1,5 @@
 // fv_march3d.cu -- the FP32 time step / update of a launch whose patches all
-// have one 3D size P = 3, 5 or 7 (a size class of the schedule, or a uniform
+// have one 3D size P = 3 .. 7 (a size class of the schedule, or a uniform
 // batch after fv_batch_plan): a lane per row of cells along x, the patch swept
 // plane by plane along z.  Same method, same operations in the
 // same order as the general kernel (fv_step.cuh; Eq. 2-5, Algorithm 1 steps
@@ -171,8 +171,9 @@ __device__ __forceinline__ void sread(float (&q)[5], const float* p, unsigned nm
 }
 constexpr unsigned kSign = 0x80000000u;
 
-// Resident CTAs per SM the registers are sized for: P = 3 at 128 registers,
-// P = 5 at 168, P = 7 (seven cells a row in flight) at 255.
+// Resident CTAs per SM the registers are sized for (no spills): P = 3 at 128
+// registers, 4 and 5 at 168, 6 and 7 (six and seven cells a row in
+// flight) at 255.
 template <int P>
 constexpr int march_blocks() {
   return P <= 3 ? 16 : P <= 5 ? FV_MARCH3D_MINBLOCKS : 8;
@@ -525,7 +526,7 @@ cudaError_t occupancy_march3d_t(int* bps) {  // the kernel with per-patch maxima
 }  // namespace
 
 bool march3d_class(const fv_batch* h, int p) {
-  return h->prec == FV_FP32 && h->d == 3 && h->s == 5 && (p == 3 || p == 5 || p == 7);
+  return h->prec == FV_FP32 && h->d == 3 && h->s == 5 && p >= 3 && p <= 7;
 }
 
 bool march3d_eligible(const fv_batch* h, const UpdateLaunch& l) {
@@ -550,6 +551,10 @@ cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid) {
   switch (l.uniform_p) {
     case 3:
       return launch_march3d_p<3>(h, l, grid);
+    case 4:
+      return launch_march3d_p<4>(h, l, grid);
+    case 6:
+      return launch_march3d_p<6>(h, l, grid);
     case 7:
       return launch_march3d_p<7>(h, l, grid);
     default:
@@ -557,14 +562,24 @@ cudaError_t launch_march3d(const fv_batch* h, const UpdateLaunch& l, int grid) {
   }
 }
 
+template <int P>
+static cudaError_t occupancy_march3d_p(int mode, int* bps) {
+  return mode == kModeStep ? occupancy_march3d_t<P, true>(bps) : occupancy_march3d_t<P, false>(bps);
+}
+
 cudaError_t march3d_occupancy(int p, int mode, int* bps) {
-  if (p == 3)
-    return mode == kModeStep ? occupancy_march3d_t<3, true>(bps)
-                             : occupancy_march3d_t<3, false>(bps);
-  if (p == 7)
-    return mode == kModeStep ? occupancy_march3d_t<7, true>(bps)
-                             : occupancy_march3d_t<7, false>(bps);
-  return mode == kModeStep ? occupancy_march3d_t<5, true>(bps) : occupancy_march3d_t<5, false>(bps);
+  switch (p) {
+    case 3:
+      return occupancy_march3d_p<3>(mode, bps);
+    case 4:
+      return occupancy_march3d_p<4>(mode, bps);
+    case 6:
+      return occupancy_march3d_p<6>(mode, bps);
+    case 7:
+      return occupancy_march3d_p<7>(mode, bps);
+    default:
+      return occupancy_march3d_p<5>(mode, bps);
+  }
 }
 
 }  // namespace fv

@@ -177,8 +177,15 @@ __device__ __forceinline__ void st_cell(RCell& x, const float* src, unsigned nm1
 __device__ __forceinline__ float shfl_dn(float v) { return __shfl_down_sync(0xFFFFFFFFu, v, 1); }
 __device__ __forceinline__ float shfl_up(float v) { return __shfl_up_sync(0xFFFFFFFFu, v, 1); }
 
+// Resident CTAs per SM the registers are sized for (no spills): p <= 5 at
+// 128 registers, 6 at 168.
+template <int P>
+constexpr int rows_blocks() {
+  return P <= 5 ? FV_ROWS2D_MINBLOCKS : 12;
+}
+
 template <int P, bool STEP>
-__global__ void __launch_bounds__(kRowsNT, FV_ROWS2D_MINBLOCKS) rows2d_kernel(StepParams<float> a) {
+__global__ void __launch_bounds__(kRowsNT, rows_blocks<P>()) rows2d_kernel(StepParams<float> a) {
   constexpr int S = 4, NE = P + 2;
   static_assert(NE <= kRowsGroup, "a patch's rows fit one lane group");
   const int lane = threadIdx.x & 31;
@@ -423,7 +430,7 @@ cudaError_t occupancy_rows2d_t(int* bps) {
 }  // namespace
 
 bool rows2d_class(const fv_batch* h, int p) {
-  return h->prec == FV_FP32 && h->d == 2 && h->s == 4 && p == 5;
+  return h->prec == FV_FP32 && h->d == 2 && h->s == 4 && p >= 3 && p <= 6;
 }
 
 bool rows2d_eligible(const fv_batch* h, const UpdateLaunch& l) {
@@ -434,13 +441,41 @@ bool rows2d_eligible(const fv_batch* h, const UpdateLaunch& l) {
 
 int rows2d_patches_per_cta() { return (kRowsNT / 32) * kRowsPerWarp; }
 
-cudaError_t launch_rows2d(const fv_batch* h, const UpdateLaunch& l, int grid) {
-  return step_mode(l) == kModeStep ? launch_rows2d_t<5, true>(h, l, grid)
-                                   : launch_rows2d_t<5, false>(h, l, grid);
+template <int P>
+static cudaError_t launch_rows2d_p(const fv_batch* h, const UpdateLaunch& l, int grid) {
+  return step_mode(l) == kModeStep ? launch_rows2d_t<P, true>(h, l, grid)
+                                   : launch_rows2d_t<P, false>(h, l, grid);
 }
 
-cudaError_t rows2d_occupancy(int mode, int* bps) {
-  return mode == kModeStep ? occupancy_rows2d_t<5, true>(bps) : occupancy_rows2d_t<5, false>(bps);
+cudaError_t launch_rows2d(const fv_batch* h, const UpdateLaunch& l, int grid) {
+  switch (l.uniform_p) {
+    case 3:
+      return launch_rows2d_p<3>(h, l, grid);
+    case 4:
+      return launch_rows2d_p<4>(h, l, grid);
+    case 6:
+      return launch_rows2d_p<6>(h, l, grid);
+    default:
+      return launch_rows2d_p<5>(h, l, grid);
+  }
+}
+
+template <int P>
+static cudaError_t occupancy_rows2d_p(int mode, int* bps) {
+  return mode == kModeStep ? occupancy_rows2d_t<P, true>(bps) : occupancy_rows2d_t<P, false>(bps);
+}
+
+cudaError_t rows2d_occupancy(int p, int mode, int* bps) {
+  switch (p) {
+    case 3:
+      return occupancy_rows2d_p<3>(mode, bps);
+    case 4:
+      return occupancy_rows2d_p<4>(mode, bps);
+    case 6:
+      return occupancy_rows2d_p<6>(mode, bps);
+    default:
+      return occupancy_rows2d_p<5>(mode, bps);
+  }
 }
 
 }  // namespace fv

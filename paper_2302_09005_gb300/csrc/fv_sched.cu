@@ -47,16 +47,17 @@ static int grid_for(const fv_batch* h, int64_t count, int bps) {
 }
 
 // A launch of patches of one size: the FP32 kernel built for that size (3D
-// p = 3, 5, 7: the plane sweep; 2D p = 5: a lane per row) where it applies.
+// p = 3 .. 7: the plane sweep; 2D p = 3 .. 6: a lane per row) where it
+// applies.
 static cudaError_t launch_one_size(fv_batch* h, const UpdateLaunch& l, int64_t count,
                                    bool* done) {
   *done = false;
   const bool two = rows2d_eligible(h, l);
   if (!two && !march3d_eligible(h, l)) return cudaSuccess;
   const int f = step_mode(l);
-  int& bps = h->occ_one[l.uniform_p == 3 ? 0 : l.uniform_p == 7 ? 2 : 1][f];
+  int& bps = h->occ_one[l.uniform_p & 7][f];  // p = 3 .. 7 (2D: 3 .. 6)
   if (bps == 0) {
-    cudaError_t e = two ? rows2d_occupancy(f, &bps) : march3d_occupancy(l.uniform_p, f, &bps);
+    cudaError_t e = two ? rows2d_occupancy(l.uniform_p, f, &bps) : march3d_occupancy(l.uniform_p, f, &bps);
     if (e != cudaSuccess) return e;
   }
   *done = true;

@@ -1,5 +1,5 @@
 """The FP32 kernel for launches of one 3D patch size (csrc/fv_march3d.cu, for
-3^3, 5^3 and 7^3 patches): it runs (launch counter) for planned batches under
+p^3 patches, p = 3 .. 7): it runs (launch counter) for planned batches under
 every schedule and for every class of uneven batches, and its results are
 bitwise those of the general kernel -- time steps on periodic, outflow and
 wall meshes (with per-patch wave speeds and the primitives of the new state),
@@ -15,7 +15,7 @@ from tests import fvtest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=[5, 3, 7], ids=["p5", "p3", "p7"])
+@pytest.fixture(params=[5, 3, 7, 4, 6], ids=["p5", "p3", "p7", "p4", "p6"])
 def P(request):
     return request.param
 

@@ -1,6 +1,7 @@
-"""The FP32 kernel for launches of one 2D patch size (csrc/fv_rows2d.cu, 5x5
-patches, a lane per row of cells, four patches a warp): it runs (launch counter) for planned batches
-under every schedule and for the 5x5 class of uneven batches, and its results
+"""The FP32 kernel for launches of one 2D patch size (csrc/fv_rows2d.cu, p x p
+patches for p = 3 .. 6, a lane per row of cells, four patches a warp): it runs
+(launch counter) for planned batches under every schedule and for its classes
+of uneven batches, and its results
 are bitwise those of the general kernel -- time steps on periodic, outflow
 and wall meshes (with per-patch wave speeds, the time step and the
 primitives of the new state), update mode with more patches than resident
@@ -15,7 +16,12 @@ from tests import fvtest
 
 pytestmark = pytest.mark.gpu
 
-P, D = 5, 2
+D = 2
+
+
+@pytest.fixture(params=[5, 3, 4, 6], ids=["p5", "p3", "p4", "p6"])
+def P(request):
+    return request.param
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +32,7 @@ def fv():
     return fvmod
 
 
-def batch(fv, planned, tsz, n, sched=0, p=P):
+def batch(fv, planned, tsz, n, sched=0, p=5):
     b = fv.Batch(D, precision=fv.FV_FP32, max_patch_size=p)
     if planned:
         fv.fv_batch_plan(b.h, tsz, n)
@@ -48,7 +54,7 @@ def time_steps(fv, b, q, toff, tsz, tnbr, dx, cfl, steps, lam=None):
 @pytest.mark.parametrize("grid,periodic,bnd", [
     ((12, 10), True, -1), ((3, 3), False, -1), ((4, 7), False, -2), ((1, 1), True, -1),
     ((80, 60), True, -1), ((200, 100), False, -2)])
-def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd):
+def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd, P):
     torch = fvtest.torch_cuda()
     n = int(np.prod(grid))
     q, off, sz = fvtest.random_batch(n, P, D, 91, np.float32)
@@ -57,7 +63,7 @@ def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd)
     dx, cfl, steps = 1.0 / (grid[0] * P), 0.4, 3
     outs, lams, dts, launches = [], [], [], []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n, sched)
+        b = batch(fv, planned, tsz, n, sched, p=P)
         lam = torch.zeros(n, dtype=torch.float64, device="cuda")
         x = time_steps(fv, b, q, toff, tsz, tnbr, dx, cfl, steps, lam)
         assert b.status() == fv.FV_OK
@@ -73,7 +79,7 @@ def test_time_steps_bitwise_equal_general_kernel(fv, sched, grid, periodic, bnd)
     assert dts[0] == dts[1]
 
 
-def test_primitives_of_the_new_state_bitwise(fv):
+def test_primitives_of_the_new_state_bitwise(fv, P):
     torch = fvtest.torch_cuda()
     grid = (7, 5)
     n = int(np.prod(grid))
@@ -83,7 +89,7 @@ def test_primitives_of_the_new_state_bitwise(fv):
     dx, cfl = 1.0 / (grid[0] * P), 0.4
     res = []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n)
+        b = batch(fv, planned, tsz, n, p=P)
         x, y = fvtest.to_dev(q), fvtest.to_dev(q)
         pa = torch.full((n * b.prim_stride(),), float("nan"), dtype=torch.float32, device="cuda")
         b.halo_fill(x, toff, tsz, tnbr)
@@ -101,7 +107,7 @@ def test_primitives_of_the_new_state_bitwise(fv):
 
 
 @pytest.mark.parametrize("device_dt,n", [(False, 9000), (True, 9000), (False, 40000)])
-def test_update_mode_bitwise_equal_general_kernel(fv, device_dt, n):
+def test_update_mode_bitwise_equal_general_kernel(fv, device_dt, n, P):
     torch = fvtest.torch_cuda()
     # more patches than resident warps: several per CTA (40,000: about 11)
     q, off, sz = fvtest.random_batch(n, P, D, 93, np.float32)
@@ -109,7 +115,7 @@ def test_update_mode_bitwise_equal_general_kernel(fv, device_dt, n):
     dx = 0.01
     res = []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n, 2)
+        b = batch(fv, planned, tsz, n, 2, p=P)
         x = fvtest.to_dev(q)
         y = x.clone()
         lam = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -126,14 +132,14 @@ def test_update_mode_bitwise_equal_general_kernel(fv, device_dt, n):
     assert np.array_equal(res[0][1], res[1][1])
 
 
-def test_time_step_matches_oracle(fv):
+def test_time_step_matches_oracle(fv, P):
     grid = (6, 5)
     n = int(np.prod(grid))
     q, off, sz = fvtest.random_batch(n, P, D, 94)
     nbr = inputs.grid_neighbours(grid)
     toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
     dx, cfl = 1.0 / (grid[0] * P), 0.4
-    b = batch(fv, True, tsz, n)
+    b = batch(fv, True, tsz, n, p=P)
     x = time_steps(fv, b, q.astype(np.float32), toff, tsz, tnbr, dx, cfl, 1)
     assert b.status() == fv.FV_OK and fv.fv_batch_pairs_launches(b.h) == 1
     ref, dt = oracle.step(q, off, sz, nbr, D, dx, cfl)
@@ -144,7 +150,7 @@ def test_time_step_matches_oracle(fv):
     b.close()
 
 
-def test_uneven_batch_uses_it_for_the_5x5_class_only(fv):
+def test_uneven_batch_uses_it_for_its_classes(fv):
     n = 900
     sizes = inputs.uneven_sizes(n, seed=95, mix=((3, 0.4), (5, 0.4), (8, 0.2)))
     q, off, sz = inputs.random_batch(n, sizes, D, seed=95, dtype=np.float32)
@@ -157,19 +163,19 @@ def test_uneven_batch_uses_it_for_the_5x5_class_only(fv):
     b = batch(fv, True, tsz, n, 2, p=8)
     got = time_steps(fv, b, q, toff, tsz, tnbr, dx, cfl, steps).cpu().numpy()
     assert b.status() == fv.FV_OK
-    assert fv.fv_batch_pairs_launches(b.h) == steps
+    assert fv.fv_batch_pairs_launches(b.h) == 2 * steps  # 3x3 and 5x5, not 8x8
     mask = fvtest.interior_mask(off, sz, D, D + 2, len(q))
     assert np.array_equal(got[mask], ref[mask])
     b.close()
 
 
-def test_nonphysical_state_is_reported(fv):
+def test_nonphysical_state_is_reported(fv, P):
     n = 8
     q, off, sz = fvtest.random_batch(n, P, D, 96, np.float32)
     ne = P + 2
     q[off[3] + (2 + ne * 3) * (D + 2)] = -1.0  # negative density, interior cell
     toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
-    b = batch(fv, True, tsz, n)
+    b = batch(fv, True, tsz, n, p=P)
     x = fvtest.to_dev(q)
     b.update(x, x.clone(), toff, tsz, 0.01, 0.001)
     assert fv.fv_batch_pairs_launches(b.h) == 1
@@ -177,7 +183,7 @@ def test_nonphysical_state_is_reported(fv):
     b.close()
 
 
-def test_graph_of_steps_on_a_fresh_handle(fv):
+def test_graph_of_steps_on_a_fresh_handle(fv, P):
     """fv_run_steps captured into a CUDA graph on a fresh, planned handle (the
     kernel's first launch happens inside the capture) equals the general
     kernel's eager steps bitwise."""
@@ -188,7 +194,7 @@ def test_graph_of_steps_on_a_fresh_handle(fv):
     nbr = inputs.grid_neighbours(grid, periodic=False, boundary=-2)
     toff, tsz, tnbr = fvtest.to_dev(off), fvtest.to_dev(sz), fvtest.to_dev(nbr)
     dx, cfl, steps = 1.0 / (grid[0] * P), 0.4, 4
-    b0 = batch(fv, False, tsz, n)
+    b0 = batch(fv, False, tsz, n, p=P)
     ref = time_steps(fv, b0, q, toff, tsz, tnbr, dx, cfl, steps).cpu().numpy()
     b0.close()
     stream = torch.cuda.Stream()
@@ -205,14 +211,14 @@ def test_graph_of_steps_on_a_fresh_handle(fv):
     b.close()
 
 
-def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv):
+def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv, P):
     n = 40
     q, off, sz = fvtest.random_batch(n, P, D, 98, np.float32)
     toff, tsz = fvtest.to_dev(off), fvtest.to_dev(sz)
     n_elems = int(off[-1]) + 10  # the last patch does not fit
     res = []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n)
+        b = batch(fv, planned, tsz, n, p=P)
         x = fvtest.to_dev(q)
         y = x.clone()
         b.update(x, y, toff, tsz, 0.01, 0.001, n_elems=n_elems)
@@ -225,7 +231,7 @@ def test_patch_beyond_the_buffer_is_flagged_and_skipped(fv):
 
 
 @pytest.mark.parametrize("step", [False, True])
-def test_invalid_patches_inside_the_sequence(fv, step):
+def test_invalid_patches_inside_the_sequence(fv, step, P):
     """Patches with a misaligned offset scattered through a long sequence (many
     patches per CTA): both kernels report FV_ERR_BAD_PATCH, skip them (and,
     in a time step, treat them as absent neighbours the same way) and agree
@@ -242,7 +248,7 @@ def test_invalid_patches_inside_the_sequence(fv, step):
     dx = 1.0 / (grid[0] * P)
     res = []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n, 2)
+        b = batch(fv, planned, tsz, n, 2, p=P)
         x = fvtest.to_dev(q)
         y = x.clone()
         if step:
@@ -257,7 +263,7 @@ def test_invalid_patches_inside_the_sequence(fv, step):
     assert np.array_equal(res[0][1], res[1][1])
 
 
-def test_bad_neighbour_entries_flagged_like_the_general_kernel(fv):
+def test_bad_neighbour_entries_flagged_like_the_general_kernel(fv, P):
     """Neighbour-table entries that name no patch (an index past the batch, an
     unknown boundary code): both kernels report FV_ERR_BAD_PATCH, take those
     faces as outflow and agree bitwise on the new state."""
@@ -273,7 +279,7 @@ def test_bad_neighbour_entries_flagged_like_the_general_kernel(fv):
     dx = 1.0 / (grid[0] * P)
     res = []
     for planned in (False, True):
-        b = batch(fv, planned, tsz, n, 2)
+        b = batch(fv, planned, tsz, n, 2, p=P)
         x = fvtest.to_dev(q)
         y = x.clone()
         b.max_eigenvalue(x, toff, tsz, 0.4, dx)

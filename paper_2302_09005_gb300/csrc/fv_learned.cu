@@ -174,6 +174,21 @@ constexpr int kCorrNT = 256;  // consumers + producers
 constexpr int kK1 = 16;       // layer-1 K: the 16 inputs
 constexpr int kK2 = 80;       // layers 2, 3 K: 64 hidden, two ones columns, zeros
 
+// Where a staged tile's patch and its two halo layers come from (the rules
+// of cell_source, resolved once per patch): its size and offset; per side f
+// (-x, +x, -y, +y) the source patch's offset, how the side is filled
+// (0: neighbour, 1: outflow copy, 2: wall mirror) and the neighbour index;
+// per direction whether the low neighbour names the patch back (it then
+// takes the face b = 0 into its high-face slot).
+struct alignas(8) CRec {
+  long long off;
+  long long soff[4];
+  int p;
+  int mode[4];
+  int nb[4];
+  int extok[2];
+};
+
 struct TcSmem {
   alignas(128) unsigned char a1[2][kTcRows * kK1 * 2];
   alignas(128) unsigned char a2[kTcRows * kK2 * 2];
@@ -186,6 +201,7 @@ struct TcSmem {
   int fext[2][kTcRows];  // low neighbour that shares the face (b = 0), or -1
   int fkj[2][kTcRows];   // j | nf1 << 10 | k << 20
   int fany[2];           // whether the tile has an active row
+  CRec prec[2];          // the staged tiles' patch records (this tile, the next)
   alignas(8) uint64_t bar;
   uint32_t tmem;
 };
@@ -344,6 +360,107 @@ __device__ __forceinline__ void stage_patch(const MeshView<T>& m, int64_t pid, i
   }
 }
 
+// A staged tile's patch record in two dependent load steps, one per
+// iteration of the producer loop, by the producer rows f = 0 .. 3 (side f):
+// step 1, the patch's size and offset and its neighbour across side f; step
+// 2, the neighbour's size and offset and its own neighbour back across the
+// shared face.  Indices are clamped to valid entries, so every load is in
+// bounds; corr_rec_finish applies cell_source's rules to the values.
+struct CL1 {
+  long long off;
+  int64_t pid;
+  int p, nb;
+};
+struct CL2 {
+  long long onb;
+  int snb, back;
+};
+template <typename T>
+__device__ __forceinline__ CL1 corr_l1(const MeshView<T>& m, int64_t pid, int f) {
+  CL1 r{0, pid, 0, -1};
+  if (pid >= 0) {
+    r.p = m.sizes[pid];
+    r.off = m.off[pid];
+    r.nb = m.nbr[pid * 4 + f];
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ CL2 corr_l2(const MeshView<T>& m, const CL1& a, int f) {
+  CL2 r{0, 0, -1};
+  if (a.pid >= 0) {
+    const int64_t nc = (a.nb >= 0 && a.nb < m.n) ? (int64_t)a.nb : a.pid;
+    r.snb = m.sizes[nc];
+    r.onb = m.off[nc];
+    r.back = m.nbr[nc * 4 + (f | 1)];
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void corr_rec_finish(const MeshView<T>& m, const CL1& a, const CL2& b,
+                                                int f, int pmax, CRec* rec) {
+  if (a.pid < 0) return;
+  if (f == 0) {
+    rec->p = a.p;
+    rec->off = a.off;
+  }
+  const bool valid = a.nb >= 0 && a.nb < m.n && b.snb == a.p;
+  if (!valid && a.nb != -1 && a.nb != -2 && a.p >= 1 && a.p <= pmax)
+    atomicOr(m.status, ST_BAD_PATCH);
+  rec->soff[f] = valid ? b.onb : a.off;
+  rec->mode[f] = valid ? 0 : (a.nb == -2 ? 2 : 1);
+  rec->nb[f] = a.nb;
+  if ((f & 1) == 0) rec->extok[f >> 1] = (valid && b.back == (int)a.pid) ? 1 : 0;
+}
+
+// stage_patch from a patch record: the same cells, the same values.
+template <typename T>
+__device__ __forceinline__ void stage_patch_rec(const MeshView<T>& m, const CRec& rec,
+                                                float4* stage, int t, int nt) {
+  const int p = rec.p, ns = p + 4;
+  const int total = p * p + 8 * p;  // interior, then 4 sides x 2 layers x p
+  for (; t < total; t += nt) {
+    int x, y, neg = -1;
+    long long so = rec.off;
+    if (t < p * p) {
+      y = t / p;
+      x = 1 + t - y * p;
+      ++y;
+    } else {
+      const int u = t - p * p;
+      const int side4 = u / (2 * p);  // 0: -x, 1: +x, 2: -y, 3: +y
+      const int r = u - side4 * 2 * p;
+      const int layer = r / p;  // 0: next to the face, 1: beyond
+      const int tr = 1 + r - layer * p;
+      const int side = side4 & 1, depth = layer + 1;
+      const int mode = rec.mode[side4];
+      int along;
+      if (mode == 0) {  // the neighbour's interior
+        so = rec.soff[side4];
+        along = side ? depth : p + 1 - depth;
+      } else if (mode == 2) {  // wall: mirror image
+        along = side ? p + 1 - depth : depth;
+        neg = 1 + (side4 >> 1);
+      } else {  // outflow: nearest interior cell
+        along = side ? p : 1;
+      }
+      if (side4 < 2) { x = along; y = tr; } else { x = tr; y = along; }
+      // the staged position: the cell beyond the face
+      const int c = side ? p + 1 + layer : -layer;
+      const T* src = m.q + so + ((int64_t)y * (p + 2) + x) * 4;
+      float v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = (q == neg) ? -narrow(src[q]) : narrow(src[q]);
+      if (side4 < 2) stage[(tr + 1) * ns + (c + 1)] = make_float4(v[0], v[1], v[2], v[3]);
+      else stage[(c + 1) * ns + (tr + 1)] = make_float4(v[0], v[1], v[2], v[3]);
+      continue;
+    }
+    const T* src = m.q + so + ((int64_t)y * (p + 2) + x) * 4;
+    stage[(y + 1) * ns + (x + 1)] =
+        make_float4(narrow(src[0]), narrow(src[1]), narrow(src[2]), narrow(src[3]));
+  }
+}
+
 // Whether patch q is a valid neighbour of size p that names `back` as its
 // neighbour on side `side` of direction k.
 template <typename T>
@@ -428,9 +545,29 @@ __global__ void __launch_bounds__(kCorrNT, 4)
     bool in_b = false;
     int pcur = 0, rp = 0;  // the patch size rp is for: ceil(2^16 / p), x / p = (x rp) >> 16
     int it = 0;
+    // the staged tiles' patch records: this tile's ready, the next one's in
+    // two load steps over this iteration and the one before (rows 0 .. 3)
+    const int64_t gstep = gridDim.x;
+    auto tile_pid = [&](int64_t tl) -> int64_t {  // the patch of a staged tile, else -1
+      return (staged && tl < tilesA) ? tl * kTcRows / perA : -1;
+    };
+    CL1 l1n{0, -1, 0, -1};  // step 1 of the next tile's patch
+    if (row < 4) {
+      const CL1 a0 = corr_l1(m, tile_pid(blockIdx.x), row);
+      corr_rec_finish(m, a0, corr_l2(m, a0, row), row, pmax, &s.prec[0]);
+      l1n = corr_l1(m, tile_pid(blockIdx.x + gstep), row);
+    }
+    nbar_sync(kBarProd, kTcRows);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
       if (it >= 2) nbar_sync(kBarEmpty + b, kCorrNT);
+      CL2 l2n{0, 0, -1};
+      CL1 l1nn{0, -1, 0, -1};
+      if (row < 4) {
+        l2n = corr_l2(m, l1n, row);                          // step 2, the next tile
+        l1nn = corr_l1(m, tile_pid(tile + 2 * gstep), row);  // step 1, the one after
+      }
+      const CRec& rec = s.prec[it & 1];
       if (tile >= tilesA && !in_b) {
         in_b = true;
         wb.init((tile - tilesA) * kTcRows + row, perB, sstep);
@@ -442,7 +579,7 @@ __global__ void __launch_bounds__(kCorrNT, 4)
       int p = 1, nf1 = 2, k = 0, j = 0, bb = 0, tr = 0;
       int ext = -1;
       if (act) {
-        p = m.sizes[pid];
+        p = (staged && !in_b) ? rec.p : m.sizes[pid];
         if (p < 1 || p > pmax) {
           if (lf == 0) atomicOr(m.status, ST_BAD_PATCH);
           act = false;
@@ -471,8 +608,12 @@ __global__ void __launch_bounds__(kCorrNT, 4)
           nf1 = (p + 1) * p;
           j = tr + p * bb;
           if (bb == 0) {  // also the high face of the low neighbour
-            const int64_t nl = m.nbr[pid * 4 + 2 * k];
-            if (links_back(m, nl, p, k, 1, pid)) ext = (int)nl;
+            if (staged && !in_b) {
+              if (rec.extok[k]) ext = rec.nb[2 * k];
+            } else {
+              const int64_t nl = m.nbr[pid * 4 + 2 * k];
+              if (links_back(m, nl, p, k, 1, pid)) ext = (int)nl;
+            }
           }
         }
       }
@@ -481,7 +622,7 @@ __global__ void __launch_bounds__(kCorrNT, 4)
       if (staged && !in_b) {
         // the tile's rows are the low faces of one patch: its cells and
         // halo layers are staged once, every stencil read from there
-        if (p >= 1 && p <= pmax && slot < nA) stage_patch(m, pid, p, stage, row, kTcRows);
+        if (p >= 1 && p <= pmax && slot < nA) stage_patch_rec(m, rec, stage, row, kTcRows);
         nbar_sync(kBarProd, kTcRows);
         const int ns = p + 4;
 #pragma unroll
@@ -538,6 +679,10 @@ __global__ void __launch_bounds__(kCorrNT, 4)
       s.fext[b][row] = ext;
       s.fkj[b][row] = j | (nf1 << 10) | (k << 20) | (p << 21);
       fence_proxy_async_smem();
+      if (row < 4) {  // the next tile's record, read after the barrier below
+        corr_rec_finish(m, l1n, l2n, row, pmax, &s.prec[(it + 1) & 1]);
+        l1n = l1nn;
+      }
       const bool any = nbar_or(kBarProd, kTcRows, act);
       if (row == 0) s.fany[b] = any ? 1 : 0;
       nbar_arrive(kBarFull + b, kCorrNT);

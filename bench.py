@@ -952,6 +952,46 @@ def learned_variant(args, Nc: int = 1024, pc: int = 8, pf: int = 8, r: int = 4, 
     }
 
 
+def correction_variant(args, Nc: int = 1024, pc: int = 8, reps: int = 20):
+    """The correction kernel alone on the learned workload's mesh (the
+    periodic shear layer, Nc^2 cells in pc x pc patches, FP32 state) with a
+    seeded random network: time per call and its rooflines (for profiling
+    the kernel without the training and evaluation around it)."""
+    import torch
+    from paper_2302_09005_gb300 import fv, inputs, learned
+    st = torch.cuda.Stream()
+    m = learned.Mesh2D(Nc, pc, fv.FV_FP32, st, U=inputs.shear_layer(Nc, seed=3))
+    params = torch.from_numpy(learned.init_params(0)).cuda()
+    norm = torch.tensor(np.concatenate([np.full(16, 0.5), np.ones(16), np.full(4, 0.05)]),
+                        dtype=torch.float32, device="cuda")
+    corr = torch.zeros(m.n * fv.fv_corr_stride(m.b.h), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            fv.fv_flux_correction(m.b.h, m.x, m.off, m.sizes, m.nbr, m.n, params, norm, corr)
+        a, b = _events(1)[0]
+        a.record(st)
+        for _ in range(reps):
+            fv.fv_flux_correction(m.b.h, m.x, m.off, m.sizes, m.nbr, m.n, params, norm, corr)
+        b.record(st)
+    st.synchronize()
+    kms = a.elapsed_time(b) / reps
+    ok = m.b.status() == fv.FV_OK
+    faces = m.n * 2 * pc * pc
+    flops = faces * 2 * (16 * 64 + 64 * 64 + 64 * 4)
+    m.close()
+    peaks, src = _peaks()
+    tf = flops / (kms / 1e3) / 1e12
+    tanh_rate = faces * 128 / (kms / 1e3)
+    return {"domain": f"{Nc}x{Nc} periodic shear layer, {pc}x{pc} patches, FP32 state",
+            "ms": kms, "faces": faces, "status_ok": ok,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": tf / peaks["bf16_tflops"],
+                         "peak_source": src + " (BF16 dense, burst)"},
+            "roofline_sfu": {"bound": "sfu", "achieved": tanh_rate / 1e12,
+                             "peak": SFU_TANH_PEAK / 1e12, "unit": "T tanh/s",
+                             "frac": tanh_rate / SFU_TANH_PEAK}}
+
+
 def _equal_cost(cost_n, err_n, target_ms):
     """The resolution N* at which the plain method costs target_ms per coarse
     step and its error there: cost(N) and err(N) interpolated piecewise
@@ -1210,7 +1250,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--variant", choices=["batching", "precision", "learned", "sweep", "amr"],
+    ap.add_argument("--variant", choices=["batching", "precision", "learned", "correction",
+                                          "sweep", "amr"],
                     default=None,
                     help="run one variant on its own")
     ap.add_argument("--small", action="store_true", help="small case of --variant")
@@ -1245,6 +1286,8 @@ def run_variant(args):
                             (1, 4, 16, 64, 256, 1024, 4096, 16384, 65536))
     elif args.variant == "amr":
         res = amr_variant(args, base_level=2 if args.small else 3)
+    elif args.variant == "correction":
+        res = correction_variant(args, Nc=256 if args.small else 1024)
     elif args.variant == "learned":
         res = (learned_variant(args, Nc=256, steps=4, train_steps=200, batch=8192)
                if args.small else learned_variant(args))

@@ -298,7 +298,8 @@ fv_status fv_halo_fill(fv_batch* h, void* q, const int64_t* off, const int32_t* 
   l.n = n;
   l.halo = h->halo;
   l.status = h->d_status;
-  cudaError_t e = fv::launch_halo(h, l, patch_grid(h, n, 8));
+  // 12 CTAs of four warps per SM (a warp per patch; under 40 registers)
+  cudaError_t e = fv::launch_halo(h, l, patch_grid(h, n, 12));
   if (e != cudaSuccess) return cuda_err(h, e, "halo kernel");
   return FV_OK;
 }
@@ -433,7 +434,7 @@ static fv_status time_step_impl(fv_batch* h, const void* in, void* out, const in
   if (prim_in && prim_in == prim_out)
     return set_err(h, FV_ERR_INVALID_ARG, "prim_in and prim_out alias");
   const int nxt = h->lam_cur ^ 1;
-  cudaError_t e = cudaMemsetAsync(&h->d_lam[nxt], 0, sizeof(unsigned long long), h->stream);
+  cudaError_t e = fv::launch_zero_word(&h->d_lam[nxt], h->stream);
   if (e != cudaSuccess) return cuda_err(h, e, "time step: reset wave speed");
   fv::UpdateLaunch l;
   l.in = in;

@@ -1,9 +1,11 @@
 // fv_halo.cu -- face halo fill of every patch from its neighbours (the
 // engine's halo consistency step, Sec. 2 of arXiv 2302.09005).
 //
-// One CTA per patch (grid stride); thread t copies halo cell t of the patch,
-// ordered (face, layer, transverse cell) with x fastest, so a warp walks rows
-// of contiguous cells on the y and z faces.
+// One warp per patch (four per CTA, grid stride over the warps); lane t
+// copies halo cells t, t + 32, ... of the patch, ordered (face, layer,
+// transverse cell) with x fastest, so a warp walks rows of contiguous cells on
+// the y and z faces.  Cells whose size is a multiple of 16 bytes (2D) move as
+// 16-byte words.
 #include "fv_device.cuh"
 #include "fv_internal.h"
 
@@ -21,16 +23,49 @@ struct HaloParams {
   unsigned int* status;
 };
 
+// The S unknowns of one cell (16-byte aligned when S sizeof(T) is a multiple
+// of 16, as patch offsets are multiples of 16 bytes).
+template <typename T, int S>
+__device__ __forceinline__ void copy_cell(const T* src, T (&v)[S]) {
+  if constexpr ((S * sizeof(T)) % 16 == 0) {
+#pragma unroll
+    for (int u = 0; u < (int)(S * sizeof(T) / 16); ++u) {
+      const uint4 w = reinterpret_cast<const uint4*>(src)[u];
+      memcpy(&v[u * (16 / sizeof(T))], &w, 16);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < S; ++u) v[u] = src[u];
+  }
+}
+template <typename T, int S>
+__device__ __forceinline__ void store_cell(T* dst, const T (&v)[S]) {
+  if constexpr ((S * sizeof(T)) % 16 == 0) {
+#pragma unroll
+    for (int u = 0; u < (int)(S * sizeof(T) / 16); ++u) {
+      uint4 w;
+      memcpy(&w, &v[u * (16 / sizeof(T))], 16);
+      reinterpret_cast<uint4*>(dst)[u] = w;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < S; ++u) dst[u] = v[u];
+  }
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(FV_NT) halo_kernel(HaloParams<T> a) {
   constexpr int S = D + 2;
   constexpr int VEC = 16 / sizeof(T);
+  constexpr int NW = FV_NT / 32;
   const int h = a.halo;
-  for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (int64_t)blockIdx.x * NW + (threadIdx.x >> 5); i < a.n;
+       i += (int64_t)gridDim.x * NW) {
     const int p = a.sizes[i];
     const int64_t off = a.off[i];
     if (!(p >= 1 && p <= a.pmax && p >= h && off >= 0 && (off % VEC) == 0)) {
-      if (threadIdx.x == 0) atomicOr(a.status, ST_BAD_PATCH);
+      if (lane == 0) atomicOr(a.status, ST_BAD_PATCH);
       continue;
     }
     const int ne = p + 2 * h;
@@ -38,7 +73,7 @@ __global__ void __launch_bounds__(FV_NT) halo_kernel(HaloParams<T> a) {
     const int per_face = h * ptr;
     const int total = 2 * D * per_face;
     T* Q = a.q + off;
-    for (int t = threadIdx.x; t < total; t += FV_NT) {
+    for (int t = lane; t < total; t += 32) {
       const int f = t / per_face;
       const int rem = t - f * per_face;
       const int l = rem / ptr;  // layer, 0 next to the interior
@@ -88,11 +123,9 @@ __global__ void __launch_bounds__(FV_NT) halo_kernel(HaloParams<T> a) {
       T* dst = Q + id * S;
       const T* src = src_patch + is * S;
       T v[S];
-#pragma unroll
-      for (int u = 0; u < S; ++u) v[u] = src[u];
+      copy_cell<T, S>(src, v);
       if (nb == -2) v[1 + k] = -v[1 + k];
-#pragma unroll
-      for (int u = 0; u < S; ++u) dst[u] = v[u];
+      store_cell<T, S>(dst, v);
     }
   }
 }

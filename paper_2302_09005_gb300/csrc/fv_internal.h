@@ -182,6 +182,8 @@ struct EigLaunch {
   unsigned int* status;
 };
 cudaError_t launch_eig(const fv_batch* h, const EigLaunch& a, int grid);
+// *p = 0 on the stream, by a one-thread kernel.
+cudaError_t launch_zero_word(unsigned long long* p, cudaStream_t stream);
 cudaError_t launch_eig_finish(const fv_batch* h, const unsigned long long* partials, int nparts,
                               double* global_out, unsigned long long* lam_slot, double* dt_slot,
                               double* dt_out, double cfl, double dx);

@@ -10,8 +10,10 @@ namespace fv {
 // Maximum eigenvalue.  The per-patch value is the largest a over the faces
 // that bound interior cells; a face's a is the larger |u_k| + c of its two
 // cells, so the patch value is the maximum of |u_k| + c over the interior
-// cells (every k) and the face-halo cells (their normal k only).  One CTA per
-// patch, grid stride; cells are read straight from HBM.
+// cells (every k) and the face-halo cells (their normal k only).  One warp per
+// patch (four per CTA, grid stride over the warps), the patch maximum by warp
+// shuffles; cells are read straight from HBM, as 16-byte words where a cell's
+// size is a multiple of 16 bytes (2D).
 // ---------------------------------------------------------------------------
 template <typename T>
 struct EigParams {
@@ -36,15 +38,17 @@ template <typename T, int D>
 __global__ void __launch_bounds__(FV_NT) eig_kernel(EigParams<T> a) {
   constexpr int S = D + 2;
   constexpr int VEC = 16 / sizeof(T);
-  __shared__ unsigned long long red[FV_NT / 32];
-  const int tid = threadIdx.x;
-  unsigned long long block_max = 0ull;  // meaningful in thread 0
-  for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x) {
+  constexpr int NW = FV_NT / 32;
+  __shared__ unsigned long long red[NW];
+  const int tid = threadIdx.x, lane = tid & 31;
+  unsigned long long warp_max = 0ull;  // over this warp's patches
+  for (int64_t i = (int64_t)blockIdx.x * NW + (tid >> 5); i < a.n;
+       i += (int64_t)gridDim.x * NW) {
     const int p = a.sizes[i];
     const int64_t off = a.off[i];
     const int h = a.halo;
     if (!(p >= 1 && p <= a.pmax && off >= 0 && (off % VEC) == 0)) {
-      if (tid == 0) atomicOr(a.status, ST_BAD_PATCH);
+      if (lane == 0) atomicOr(a.status, ST_BAD_PATCH);
       continue;
     }
     const int ne = p + 2 * h;
@@ -53,7 +57,7 @@ __global__ void __launch_bounds__(FV_NT) eig_kernel(EigParams<T> a) {
     const T* Q = a.q + off;
     unsigned long long m = 0ull;
     bool bad = false;
-    for (int t = tid; t < nint + 2 * D * ptr; t += FV_NT) {
+    for (int t = lane; t < nint + 2 * D * ptr; t += 32) {
       int c[3] = {0, 0, 0};
       int kdir = -1;
       if (t < nint) {
@@ -80,8 +84,16 @@ __global__ void __launch_bounds__(FV_NT) eig_kernel(EigParams<T> a) {
 #pragma unroll
       for (int k = D - 2; k >= 0; --k) cid = cid * ne + c[k];
       T q[S];
+      if constexpr ((S * sizeof(T)) % 16 == 0) {
 #pragma unroll
-      for (int v = 0; v < S; ++v) q[v] = __ldg(Q + cid * S + v);
+        for (int u = 0; u < (int)(S * sizeof(T) / 16); ++u) {
+          const uint4 w = __ldg(reinterpret_cast<const uint4*>(Q + cid * S) + u);
+          memcpy(&q[u * (16 / sizeof(T))], &w, 16);
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < S; ++v) q[v] = __ldg(Q + cid * S + v);
+      }
       Prim<T, D> w = primitives<T, D>(q, a.gm1, a.gamma, bad);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -93,19 +105,18 @@ __global__ void __launch_bounds__(FV_NT) eig_kernel(EigParams<T> a) {
       }
     }
     if (bad) atomicOr(a.status, ST_NONPHYSICAL);
-    m = warp_max_u64(m);
-    if ((tid & 31) == 0) red[tid >> 5] = m;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned long long mm = red[0];
-#pragma unroll
-      for (int w2 = 1; w2 < FV_NT / 32; ++w2) mm = red[w2] > mm ? red[w2] : mm;
-      if (a.per_patch) a.per_patch[i] = order_value<T>(mm);
-      block_max = mm > block_max ? mm : block_max;
-    }
-    __syncthreads();
+    m = warp_max_u64(m);  // in every lane
+    if (lane == 0 && a.per_patch) a.per_patch[i] = order_value<T>(m);
+    warp_max = m > warp_max ? m : warp_max;
   }
-  if (tid == 0) a.partials[blockIdx.x] = block_max;
+  if (lane == 0) red[tid >> 5] = warp_max;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long mm = red[0];
+#pragma unroll
+    for (int w2 = 1; w2 < NW; ++w2) mm = red[w2] > mm ? red[w2] : mm;
+    a.partials[blockIdx.x] = mm;
+  }
 }
 
 // Reduces the per-CTA maxima (bit patterns of type T), writes the global
@@ -319,6 +330,17 @@ cudaError_t launch_sums_finish(const fv_batch* h, const double* partials, int nc
   if (h->d == 1) sums_finish_kernel<3><<<1, FV_NT, 0, h->stream>>>(partials, nchunks, totals);
   else if (h->d == 2) sums_finish_kernel<4><<<1, FV_NT, 0, h->stream>>>(partials, nchunks, totals);
   else sums_finish_kernel<5><<<1, FV_NT, 0, h->stream>>>(partials, nchunks, totals);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// One 64-bit word set to zero on the stream (the wave-speed slot a time step
+// accumulates into, the work-queue counter), by a one-thread kernel.
+// ---------------------------------------------------------------------------
+__global__ void zero_word_kernel(unsigned long long* p) { *p = 0ull; }
+
+cudaError_t launch_zero_word(unsigned long long* p, cudaStream_t stream) {
+  zero_word_kernel<<<1, 1, 0, stream>>>(p);
   return cudaGetLastError();
 }
 

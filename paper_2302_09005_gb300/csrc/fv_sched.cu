@@ -120,7 +120,7 @@ cudaError_t launch_scheduled(fv_batch* h, UpdateLaunch l) {
     l.i_end = l.n;
     if (h->sched == FV_SCHED_QUEUE) {
       l.queue = h->d_queue;
-      cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned long long), h->stream);
+      cudaError_t e = launch_zero_word(h->d_queue, h->stream);
       if (e != cudaSuccess) return e;
     }
   }

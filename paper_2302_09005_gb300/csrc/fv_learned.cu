@@ -187,6 +187,7 @@ struct alignas(8) CRec {
   int mode[4];
   int nb[4];
   int extok[2];
+  unsigned rp1, rp2;  // ceil(2^16 / p), ceil(2^16 / 2p): x / p = (x rp1) >> 16
 };
 
 struct TcSmem {
@@ -196,7 +197,8 @@ struct TcSmem {
   alignas(128) unsigned char w2[64 * kK2 * 2];
   alignas(128) unsigned char w3[16 * kK2 * 2];
   alignas(16) float b1[64];
-  float mu[16], rsd[16], sdy[4];
+  float2 murs[16];  // per input: mean, 1 / standard deviation
+  float sdy[4];
   int fpid[2][kTcRows];  // patch of each row's face, or -1 (idle row)
   int fext[2][kTcRows];  // low neighbour that shares the face (b = 0), or -1
   int fkj[2][kTcRows];   // j | nf1 << 10 | k << 20
@@ -403,6 +405,9 @@ __device__ __forceinline__ void corr_rec_finish(const MeshView<T>& m, const CL1&
   if (f == 0) {
     rec->p = a.p;
     rec->off = a.off;
+    const unsigned pp = a.p >= 1 ? (unsigned)a.p : 1u;
+    rec->rp1 = (65536u + pp - 1u) / pp;
+    rec->rp2 = (65536u + 2u * pp - 1u) / (2u * pp);
   }
   const bool valid = a.nb >= 0 && a.nb < m.n && b.snb == a.p;
   if (!valid && a.nb != -1 && a.nb != -2 && a.p >= 1 && a.p <= pmax)
@@ -413,24 +418,29 @@ __device__ __forceinline__ void corr_rec_finish(const MeshView<T>& m, const CL1&
   if ((f & 1) == 0) rec->extok[f >> 1] = (valid && b.back == (int)a.pid) ? 1 : 0;
 }
 
-// stage_patch from a patch record: the same cells, the same values.
+// stage_patch from a patch record: the same cells, the same values.  The
+// quotients by p and 2p are products with the record's rounded-up
+// reciprocals, exact for the dividends here (below 8 p + p^2 <= 384): with
+// r = ceil(2^16 / q) = (2^16 + e) / q, e < q <= 32, (x r) >> 16 = floor(x / q)
+// whenever x e < 2^16.
 template <typename T>
 __device__ __forceinline__ void stage_patch_rec(const MeshView<T>& m, const CRec& rec,
                                                 float4* stage, int t, int nt) {
   const int p = rec.p, ns = p + 4;
   const int total = p * p + 8 * p;  // interior, then 4 sides x 2 layers x p
+  const unsigned rp1 = rec.rp1, rp2 = rec.rp2;
   for (; t < total; t += nt) {
     int x, y, neg = -1;
     long long so = rec.off;
     if (t < p * p) {
-      y = t / p;
+      y = (int)(((unsigned)t * rp1) >> 16);  // t / p
       x = 1 + t - y * p;
       ++y;
     } else {
       const int u = t - p * p;
-      const int side4 = u / (2 * p);  // 0: -x, 1: +x, 2: -y, 3: +y
+      const int side4 = (int)(((unsigned)u * rp2) >> 16);  // u / 2p; 0: -x, 1: +x, 2: -y, 3: +y
       const int r = u - side4 * 2 * p;
-      const int layer = r / p;  // 0: next to the face, 1: beyond
+      const int layer = (int)(((unsigned)r * rp1) >> 16);  // r / p; 0: next to the face, 1: beyond
       const int tr = 1 + r - layer * p;
       const int side = side4 & 1, depth = layer + 1;
       const int mode = rec.mode[side4];
@@ -512,10 +522,7 @@ __global__ void __launch_bounds__(kCorrNT, 4)
     *reinterpret_cast<uint4*>(s.a2 + tc_kmajor_offset(r, 72, kK2)) = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid < 4) s.sdy[tid] = norm[32 + tid];
-  if (tid < 16) {
-    s.mu[tid] = norm[tid];
-    s.rsd[tid] = 1.0f / norm[16 + tid];
-  }
+  if (tid < 16) s.murs[tid] = make_float2(norm[tid], 1.0f / norm[16 + tid]);
   if (tid == 0) {
     mbar_init(&s.bar, 1);
     fence_mbar_init();
@@ -632,8 +639,8 @@ __global__ void __launch_bounds__(kCorrNT, 4)
           const float vn4[4] = {q4.x, k ? q4.z : q4.y, k ? q4.y : q4.z, q4.w};
 #pragma unroll
           for (int vn = 0; vn < 4; ++vn) {
-            const int phi = 4 * c + vn;
-            x[phi] = act ? (vn4[vn] - s.mu[phi]) * s.rsd[phi] : 0.f;
+            const float2 mr = s.murs[4 * c + vn];
+            x[4 * c + vn] = act ? (vn4[vn] - mr.x) * mr.y : 0.f;
           }
         }
       } else {
@@ -668,8 +675,8 @@ __global__ void __launch_bounds__(kCorrNT, 4)
         const float vn4[4] = {v[0], k ? v[2] : v[1], k ? v[1] : v[2], v[3]};
 #pragma unroll
         for (int vn = 0; vn < 4; ++vn) {
-          const int phi = 4 * c + vn;
-          x[phi] = act ? (vn4[vn] - s.mu[phi]) * s.rsd[phi] : 0.f;
+          const float2 mr = s.murs[4 * c + vn];
+          x[4 * c + vn] = act ? (vn4[vn] - mr.x) * mr.y : 0.f;
         }
       }
       }

@@ -873,14 +873,13 @@ def learned_variant(args, Nc: int = 1024, pc: int = 8, pf: int = 8, r: int = 4, 
         st.synchronize()
         cost_n[Nr] = a.elapsed_time(b) / 10 * (Nr / Nc)
         mr.close()
-    # the learned step timed as the plain ones: correction + halo fill +
-    # corrected update, ten back to back
+    # the learned step timed as the plain ones: correction (the halo fill on a
+    # second stream beside it) + corrected update, ten back to back
     ml = learned.Mesh2D(Nc, pc, fv.FV_FP64, st, U=refs[0])
     cl = torch.zeros(ml.n * fv.fv_corr_stride(ml.b.h), dtype=torch.float32, device="cuda")
 
     def learned_step():
-        fv.fv_flux_correction(ml.b.h, ml.x, ml.off, ml.sizes, ml.nbr, ml.n, params, norm, cl)
-        ml.step(dts[0], cl)
+        ml.step_learned(dts[0], params, norm, cl)
     with torch.cuda.stream(st):
         for _ in range(3):
             learned_step()

@@ -49,6 +49,7 @@ class Mesh2D:
         self.stream = stream
         self.b = fv.Batch(2, precision=precision, max_patch_size=p, stream=stream)
         self.dx = 1.0 / N
+        self._side = None  # halo fills beside the correction kernel (step_learned)
 
     def halo_fill(self):
         self.b.halo_fill(self.x, self.off, self.sizes, self.nbr)
@@ -64,11 +65,46 @@ class Mesh2D:
         self.b.update(self.x, self.y, self.off, self.sizes, self.dx, dt, corr=corr)
         self.x, self.y = self.y, self.x
 
+    def step_learned(self, dt: float, params, norm, corr):
+        """One learned step: C = net(stencils) on the mesh's stream while the
+        halo fill runs on a second stream, then the update with F + C.  The
+        two overlap safely: the correction kernel reads interior cells only
+        (a patch's and its neighbours'), the halo fill writes halo cells only;
+        the update waits for both."""
+        import torch
+        if self._side is None:
+            side = torch.cuda.Stream()
+            self._side = (side, fv.Batch(2, precision=self.precision, max_patch_size=self.p,
+                                         stream=side),
+                          torch.cuda.Event(), torch.cuda.Event())
+        side, hb, ready, filled = self._side
+        ready.record(self.stream)  # the previous update has written x
+        side.wait_event(ready)
+        hb.halo_fill(self.x, self.off, self.sizes, self.nbr)
+        filled.record(side)
+        fv.fv_flux_correction(self.b.h, self.x, self.off, self.sizes, self.nbr, self.n, params,
+                              norm, corr)
+        self.stream.wait_event(filled)
+        self.b.update(self.x, self.y, self.off, self.sizes, self.dx, dt, corr=corr)
+        self.x, self.y = self.y, self.x
+
+    def status(self) -> int:
+        """The first non-OK status of the mesh's handles (the side handle's
+        halo fills included)."""
+        st = self.b.status()
+        if st == fv.FV_OK and self._side is not None:
+            st = self._side[1].status()
+        return st
+
     def domain(self) -> np.ndarray:
         return inputs.patches_to_domain(self.x.double().cpu().numpy(), self.off_np, self.p,
                                         self.grid, 4)
 
     def close(self):
+        if self._side is not None:
+            self._side[0].synchronize()
+            self._side[1].close()
+            self._side = None
         self.b.close()
 
 
@@ -206,16 +242,16 @@ def evaluate(U_coarse0, refs, dts, pc: int, params, norm, stream, precision=fv.F
             with torch.cuda.stream(stream):
                 e0.record(stream)
                 if learned:
-                    fv.fv_flux_correction(m.b.h, m.x, m.off, m.sizes, m.nbr, m.n, params, norm,
-                                          corr)
-                m.step(dt, corr if learned else None)
+                    m.step_learned(dt, params, norm, corr)
+                else:
+                    m.step(dt)
                 e1.record(stream)
             stream.synchronize()
             ms_total += e0.elapsed_time(e1)
             D = m.domain()
             ref = refs[n + 1]
             errs.append((np.abs(D - ref).sum(axis=(0, 1)) / np.abs(ref).sum(axis=(0, 1))).tolist())
-        if m.b.status() != fv.FV_OK:
+        if m.status() != fv.FV_OK:
             raise RuntimeError("evaluation run failed")
         m.close()
         out[learned] = errs

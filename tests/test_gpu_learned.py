@@ -190,6 +190,41 @@ def test_corrected_update_matches_oracle_and_conserves(fv):
     m.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_learned_step_with_side_stream_halo_fill(fv, prec):
+    """Mesh2D.step_learned (the halo fill on a second stream beside the
+    correction kernel, then the update) gives bitwise the state of the same
+    kernels run in sequence on one stream, over several steps, and its last
+    step is the oracle's update with F + C (the GPU's corrections) to FP64
+    roundoff, or within 1e-5 for an FP32 state."""
+    torch = fvtest.torch_cuda()
+    N, p = 64, 8
+    rng = np.random.default_rng(11)
+    U = inputs.random_cells(rng, N * N, 2).reshape(N, N, 4)
+    a, b = mesh(fv, N, p, prec, U), mesh(fv, N, p, prec, U)
+    theta, norm = random_net(12)
+    pv, nv = net_to_dev(theta, norm)
+    stride = fv.fv_corr_stride(a.b.h)
+    ca = torch.zeros(a.n * stride, dtype=torch.float32, device="cuda")
+    cb = torch.zeros_like(ca)
+    dt = 0.001
+    for _ in range(3):
+        Ua = a.domain()
+        a.step_learned(dt, pv, nv, ca)
+        fv.fv_flux_correction(b.b.h, b.x, b.off, b.sizes, b.nbr, b.n, pv, nv, cb)
+        b.step(dt, cb)
+    torch.cuda.synchronize()
+    assert a.status() == fv.FV_OK and b.status() == fv.FV_OK
+    got = a.domain()
+    assert np.array_equal(got, b.domain())
+    Cx, Cy = gpu_faces_to_domain(ca.cpu().numpy().astype(np.float64), stride, a.grid, p)
+    ref = olearned.step(Ua, dt, 1.0 / N, Cx, Cy)
+    tol = 1e-12 if prec == fv.FV_FP64 else 1e-5
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    a.close()
+    b.close()
+
+
 def test_zero_network_equals_plain_time_step(fv):
     torch = fvtest.torch_cuda()
     N, p = 24, 8

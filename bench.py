@@ -461,7 +461,9 @@ def run_ours(args, ws, rank, local):
                             "span from its first to its last face-halo cell, update, "
                             "device->host copies of each patch's interior span, overlapped; "
                             "wall clock"},
-            "gpu_launches": args.steps,
+            # per step: the one-thread kernel that zeroes the next wave-speed
+            # slot, then the time-step kernel
+            "gpu_launches": 2 * args.steps,
             "step_kernel_ms": kern_ms,
             "roofline": roof,
             "hbm": hbm,

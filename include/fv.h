@@ -336,7 +336,7 @@ fv_status fv_run_steps(fv_batch* h, void* q0, void* q1, const int64_t* patch_off
  *                     pipeline depth and occupancy of its own size.
  *   FV_SCHED_QUEUE    one persistent launch whose CTAs pop the patches, sorted
  *                     by size, largest first, from a work queue (a device
- *                     counter in the handle's workspace, zeroed by a memset
+ *                     counter in the handle's workspace, zeroed by a kernel
  *                     enqueued before the launch): a CTA that finishes early
  *                     takes the next patch.
  * All four give bitwise identical results.  fv_batch_autotune chooses among

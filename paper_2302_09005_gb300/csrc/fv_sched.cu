@@ -11,8 +11,8 @@
 //                     pipeline depth and occupancy of its own size;
 //   FV_SCHED_QUEUE    one persistent launch whose CTAs pop the patches of the
 //                     size-sorted order (largest first) from a work queue, a
-//                     device counter zeroed by a memset before the launch (a
-//                     memset node in a captured graph): dynamic list
+//                     device counter zeroed by a one-thread kernel before
+//                     the launch (a kernel node in a captured graph): dynamic list
 //                     scheduling, a CTA that finishes early takes the next one.
 // fv_batch_plan sorts the patches by size (a stable counting sort);
 // fv_batch_autotune times the three on the caller's batch and keeps the

@@ -92,8 +92,8 @@ def test_schedules_bitwise_equal_update_mode(fv):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_queue_schedule_in_a_graph_of_steps(fv, prec):
-    """The work queue's counter is zeroed by a memset before every launch, a
-    memset node of the captured graph: ten graph-replayed steps under
+    """The work queue's counter is zeroed by a one-thread kernel before every
+    launch, a kernel node of the captured graph: ten graph-replayed steps under
     FV_SCHED_QUEUE equal ten eager steps under FV_SCHED_STRIDE, bitwise."""
     torch = fvtest.torch_cuda()
     n = 2000

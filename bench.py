@@ -21,8 +21,9 @@ Arms:
   default            the CUDA library (value: device-resident timing; e2e: the
                      update through fv_patch_update_host on the pinned host
                      batch, advanced in place: chunked host->device copies of
-                     each patch's face-halo span, the update, device->host
-                     copies of its interior span, overlapped; wall clock)
+                     each patch's span from its first to its last face-halo
+                     cell, the update, device->host copies of each interior
+                     plane, overlapped; wall clock)
   --impl reference   the FP64 CPU oracle on the host cores (a bounded sample
                      of the same workload per step)
 
@@ -333,9 +334,10 @@ def run_ours(args, ws, rank, local):
     # goes through fv_patch_update_host, which overlaps chunked host->device
     # copies, the update and device->host copies.  The batch is advanced in
     # place, step after step, as an engine updates its patch storage: the
-    # copies then take spans (in: first to last face-halo cell of each
-    # patch; back: first to last interior cell).  dt: the CFL step
-    # the device slot holds.  Wall-clock time of the synchronous calls.
+    # copies then take spans of the 5^3 boxes (in: from the first face-halo
+    # cell to the last; back: each interior plane from its first interior cell
+    # to its last).  dt: the CFL step the device slot holds.  Wall-clock time
+    # of the synchronous calls.
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     off_np, sz_np = h_off.numpy(), h_sz.numpy()
     dt_e2e = fv.fv_read_dt(b.h)
@@ -356,8 +358,8 @@ def run_ours(args, ws, rank, local):
         ems = float(tt.item())
     e2e_value = ws * cells_per_step * e2e_steps / (ems / 1e3)
     # one size, equal spacing: the span copies
-    h2d = n * _face_halo_span(d, p, s) * itemsize + h_off.numel() * 8 + h_sz.numel() * 4
-    d2h = n * _interior_span(d, p, s) * itemsize
+    h2d = n * _copied_in(d, p, s) * itemsize + h_off.numel() * 8 + h_sz.numel() * 4
+    d2h = n * _copied_back(d, p, s) * itemsize
     if not args.no_variants:
         # the same pipeline out of place (host_out != host_in): whole boxes back
         fv.fv_patch_update_host(b.h, h_q, h_out, off_np, sz_np, n, dx, dt_e2e)
@@ -458,9 +460,9 @@ def run_ours(args, ws, rank, local):
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                     "what": "fv_patch_update_host in place on the pinned host batch (patches "
                             "with their halos): chunked host->device copies of each patch's "
-                            "span from its first to its last face-halo cell, update, "
-                            "device->host copies of each patch's interior span, overlapped; "
-                            "wall clock"},
+                            "span from its first to its last face-halo cell (327 of 343 "
+                            "cells), update, device->host copies of each interior plane (165 "
+                            "cells), overlapped; wall clock"},
             # per step: the one-thread kernel that zeroes the next wave-speed
             # slot, then the time-step kernel
             "gpu_launches": 2 * args.steps,
@@ -1112,24 +1114,29 @@ def fp32_variant(args, b64, h_q, toff, tsz, tnbr, n, stride, p, d, s, dx, cfl, s
                          "peak_source": peak_src}}
 
 
-def _face_halo_span(d, p, s):
-    """Elements of a patch box from its first to past its last face-halo cell
-    (what the in-place host update copies in)."""
+def _copied_in(d, p, s):
+    """Elements of a patch box the in-place host update copies in: from its
+    first to its last face-halo cell."""
+    ne = p + 2
     tot, top = 0, 1
     for m in range(d):
         tot += top
         if m + 1 < d:
-            top *= p + 2
+            top *= ne
     return s * (p * (tot - top) + (p + 1) * top + 1) - s * (tot - top)
 
 
-def _interior_span(d, p, s):
-    """Elements of a patch box from its first to past its last interior cell
-    (what the in-place host update copies back)."""
+def _copied_back(d, p, s):
+    """Elements of a patch box the in-place host update copies back: 3D, each
+    interior plane's (1, 1, z) .. (p, p, z); else from the first to the last
+    interior cell."""
+    ne = p + 2
+    if d == 3:
+        return s * p * ((p - 1) * ne + p)
     tot, pw = 0, 1
     for _ in range(d):
         tot += pw
-        pw *= p + 2
+        pw *= ne
     return s * (p * tot + 1) - s * tot
 
 

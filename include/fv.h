@@ -178,7 +178,7 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
  * the paper's offload pattern (the engine ships a batch of patches with
  * their halos to the GPU for every update and takes the results back).  The
  * batch is cut into chunks of chunk_patches consecutive patches (<= 0: about
- * 128 MB per chunk); the copy in of a chunk, the update of the previous one
+ * 256 MB per chunk); the copy in of a chunk, the update of the previous one
  * and the copy out of the one before overlap (two copy streams, the
  * handle's stream for the update, three device staging slots the handle keeps
  * until fv_batch_destroy).
@@ -190,8 +190,10 @@ fv_status fv_max_eigenvalue_reduce(fv_batch* h, const void* q_with_halo,
  *                      patches of one size is copied in only from each
  *                      patch's first to its last face-halo cell (what the
  *                      update reads) and back only from its first to its
- *                      last interior cell (a third less for 5^3 boxes), the
- *                      halo cells staying as they are.
+ *                      last interior cell, for 3D patches plane by plane
+ *                      (each z-plane's cells (1, 1, z) .. (p, p, z): 165 of
+ *                      the 343 cells of a 5^3 box), the halo cells staying
+ *                      as they are.
  *   patch_offsets, patch_sizes  HOST arrays; offsets must ascend without
  *                      overlap (FV_ERR_INVALID_ARG), 16-byte multiples
  *                      (FV_ERR_ALIGNMENT); sizes in 1..max_patch_size

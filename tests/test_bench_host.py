@@ -18,23 +18,50 @@ def bench():
     return mod
 
 
-@pytest.mark.parametrize("d,p", [(1, 4), (2, 5), (2, 17), (3, 3), (3, 5), (3, 7)])
-def test_interior_span_is_first_to_last_interior_cell(bench, d, p):
-    s = d + 2
+def _cells(d, p, keep):
+    """Box indices (x fastest) of the cells c of a (p+2)^d box with keep(c)."""
     ne = p + 2
-    idx = [sum(c[m] * ne ** m for m in range(d))
-           for c in itertools.product(range(ne), repeat=d) if all(1 <= x <= p for x in c)]
-    assert bench._interior_span(d, p, s) == (max(idx) - min(idx) + 1) * s
+    return [sum(c[m] * ne ** m for m in range(d))
+            for c in itertools.product(range(ne), repeat=d) if keep(c)]
+
+
+def _span(idx):
+    return max(idx) - min(idx) + 1
+
+
+def _interior(p):
+    return lambda c: all(1 <= x <= p for x in c)
+
+
+def _read(p):  # interior and face-halo cells: at most one coordinate on the halo
+    return lambda c: sum(1 for x in c if x in (0, p + 1)) <= 1
 
 
 @pytest.mark.parametrize("d,p", [(1, 4), (2, 5), (2, 17), (3, 3), (3, 5), (3, 7)])
-def test_face_halo_span_covers_what_the_update_reads(bench, d, p):
+def test_copied_back_covers_the_interior(bench, d, p):
+    """1D/2D: one span from the first to the last interior cell; 3D: one span
+    per interior z-plane (x fastest, z the slowest coordinate)."""
     s = d + 2
-    ne = p + 2
-    idx = [sum(c[m] * ne ** m for m in range(d))
-           for c in itertools.product(range(ne), repeat=d)
-           if sum(1 for x in c if x in (0, p + 1)) <= 1]  # interior and face-halo cells
-    assert bench._face_halo_span(d, p, s) == (max(idx) - min(idx) + 1) * s
+    if d < 3:
+        want = _span(_cells(d, p, _interior(p)))
+    else:
+        want = sum(_span(_cells(d, p, lambda c, z=z: _interior(p)(c) and c[2] == z))
+                   for z in range(1, p + 1))
+    assert bench._copied_back(d, p, s) == want * s
+
+
+@pytest.mark.parametrize("d,p", [(1, 4), (2, 5), (2, 17), (3, 3), (3, 5), (3, 7)])
+def test_copied_in_covers_what_the_update_reads(bench, d, p):
+    """One span from the first to the last face-halo cell."""
+    s = d + 2
+    assert bench._copied_in(d, p, s) == _span(_cells(d, p, _read(p))) * s
+
+
+def test_copied_5cubed_counts(bench):
+    """5^3 boxes (343 cells): 327 cells in, 165 back (one span back would
+    take 229)."""
+    assert bench._copied_in(3, 5, 1) == 327
+    assert bench._copied_back(3, 5, 1) == 165
 
 
 @pytest.mark.parametrize("d,p", [(2, 5), (3, 5), (3, 7)])

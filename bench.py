@@ -78,9 +78,11 @@ def _peaks():
 FP64_LANES_PER_SM = 2
 NUM_SMS = 152
 # Special-function unit: 16 tanh.approx.f32 results per SM per clock (4 per
-# SM sub-partition), the rate that bounds the correction kernel's 128 GELUs
-# per face.
+# SM sub-partition), the rate of the correction kernel's 128 GELUs per face.
 SFU_TANH_PEAK = 16 * NUM_SMS * 2.07e9
+# Instruction issue: one warp instruction per scheduler per clock, four
+# schedulers per SM (the correction kernel's latency-bound chains run into it).
+ISSUE_PEAK = 4 * NUM_SMS * 2.07e9
 
 
 def fp64_ops_per_patch(d: int, p: int, mode: str = "carry") -> int:
@@ -951,7 +953,8 @@ def learned_variant(args, Nc: int = 1024, pc: int = 8, pf: int = 8, r: int = 4, 
                                                "unit": "T tanh/s",
                                                "frac": tanh_rate / SFU_TANH_PEAK,
                                                "peak_source": "derived: 16 tanh per SM per "
-                                                              "cycle x 152 SMs x 2.07 GHz"}},
+                                                              "cycle x 152 SMs x 2.07 GHz"},
+                              "roofline_issue": _issue_roofline(kms, Nc)},
     }
 
 
@@ -992,7 +995,8 @@ def correction_variant(args, Nc: int = 1024, pc: int = 8, reps: int = 20):
                          "peak_source": src + " (BF16 dense, burst)"},
             "roofline_sfu": {"bound": "sfu", "achieved": tanh_rate / 1e12,
                              "peak": SFU_TANH_PEAK / 1e12, "unit": "T tanh/s",
-                             "frac": tanh_rate / SFU_TANH_PEAK}}
+                             "frac": tanh_rate / SFU_TANH_PEAK},
+            "roofline_issue": _issue_roofline(kms, Nc)}
 
 
 def _equal_cost(cost_n, err_n, target_ms):
@@ -1138,6 +1142,37 @@ def _copied_back(d, p, s):
         tot += pw
         pw *= ne
     return s * (p * tot + 1) - s * tot
+
+
+def _warp_instructions(key):
+    """Warp instructions per launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            ent = json.load(f).get(key)
+        from paper_2302_09005_gb300 import _build
+        if ent and ent.get("kernel_hash") == _build.kernel_hash(ent.get("kernel", "step")):
+            return ent.get("warp_instructions_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def _issue_roofline(kms, nc):
+    """The correction kernel's instruction issue against one warp instruction
+    per scheduler per clock (ncu's count of its full launch on the 1024^2
+    mesh; None on another mesh or another source)."""
+    winstr = _warp_instructions("corr_shear_1024") if nc == 1024 else None
+    if winstr is None:
+        return None
+    rate = winstr / (kms / 1e3)
+    return {"bound": "issue", "achieved": rate / 1e12, "peak": ISSUE_PEAK / 1e12,
+            "unit": "T warp instructions/s", "frac": rate / ISSUE_PEAK,
+            "warp_instructions_per_launch": winstr,
+            "peak_source": "derived: 4 schedulers per SM x 152 SMs x 2.07 GHz",
+            "count_source": "ncu smsp__inst_executed.sum of the same launch "
+                            "(profiles/traffic.json)"}
 
 
 def _traffic(workload):

@@ -102,6 +102,8 @@ KERNEL_SOURCES = {
                           "fv_update_nt_f32.cu"),
     "march3d": _STEP_CORE + ("fv_march3d.cu", "fv_cell3.cuh", "fv_meta.cuh"),
     "rows2d": _STEP_CORE + ("fv_rows2d.cu", "fv_meta.cuh"),
+    "corr": ("fv_learned.cu", "fv_device.cuh", "fv_mma.cuh", "fv_ptx.cuh", "fv_tc.cuh",
+             "fv_x2.cuh"),
 }
 
 

@@ -107,11 +107,13 @@ def test_in_place_equals_out_of_place_bitwise(fv, prec, case, chunk):
     b.close()
 
 
-@pytest.mark.parametrize("prec,d,p", [(0, 3, 5), (1, 3, 5), (1, 2, 5), (0, 2, 8)])
+@pytest.mark.parametrize("prec,d,p", [(0, 3, 5), (1, 3, 5), (0, 3, 3), (1, 3, 7), (1, 2, 5),
+                                        (0, 2, 8)])
 def test_in_place_after_poisoned_staging(fv, prec, d, p):
     """In place, the span upload leaves the cells of a box outside the span
     (leading and trailing edge / corner cells) as the staging slot last held
-    them.  Fill every slot with NaN boxes first (an out-of-place call on a
+    them, and 3D boxes come back plane by plane (each z-plane's interior
+    span).  Fill every slot with NaN boxes first (an out-of-place call on a
     NaN batch of the same layout, whose non-physical status is read and
     cleared), then run the in-place call: no NaN may reach the update (status
     FV_OK), the interiors match the oracle, and every halo and gap element of

@@ -86,3 +86,27 @@ def test_equal_cost_interpolation(bench):
     r = bench._equal_cost(cost, err, 0.25)
     assert r["N_at_learned_cost"] == pytest.approx(1000 * 0.5 ** (1 / 3), rel=1e-12)
     assert not r["interpolated"]
+
+
+def test_issue_roofline_uses_the_committed_count_only_for_its_kernel(bench, monkeypatch):
+    """The correction kernel's issue roofline: warp instructions per launch over
+    one warp instruction per scheduler per clock (4 x 152 SMs x 2.07 GHz); no
+    figure on another mesh, or once the kernel's sources differ from those the
+    count was taken on."""
+    monkeypatch.setattr(bench, "_warp_instructions", lambda key: 1.25856e9)
+    r = bench._issue_roofline(1.0, 1024)  # 1.25856e9 instructions in 1 ms: the peak rate
+    assert r["bound"] == "issue"
+    assert r["peak"] == pytest.approx(4 * 152 * 2.07e9 / 1e12)
+    assert r["frac"] == pytest.approx(1.0)
+    assert bench._issue_roofline(1.0, 512) is None
+    monkeypatch.setattr(bench, "_warp_instructions", lambda key: None)
+    assert bench._issue_roofline(1.0, 1024) is None
+
+
+def test_committed_counts_are_keyed_by_kernel_hash(bench, monkeypatch):
+    """A count taken on other sources is not used."""
+    from paper_2302_09005_gb300 import _build
+    assert bench._warp_instructions("corr_shear_1024") == 92208896
+    monkeypatch.setattr(_build, "kernel_hash", lambda kind="step": "0" * 16)
+    assert bench._warp_instructions("corr_shear_1024") is None
+    assert bench._traffic("euler3d_fp32_262144x5") is None
